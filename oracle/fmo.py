@@ -1,0 +1,231 @@
+"""FP64 CPU oracle of FMO1/FMO2/FMO3 with GFN1-xTB fragments.
+
+TEST INFRASTRUCTURE ONLY (see oracle/xtb.py).  It follows Sec. 2.2-2.3 of the
+paper step by step:
+  Eq. 12      FMO2 energy: sum E_I + sum_{I>J} (E_IJ - E_I - E_J + dE^V_IJ)
+  Eqs. 13-14  dimer embedding correction dE^V_IJ from the charge transfer ddq
+  Eq. 15      electrostatic dimer (ES-DIM) approximation for far pairs
+  Eqs. 16-19  FMO3 energy, trimer interaction energy and its embedding term
+  Eqs. 20-21  embedding Fock matrix V^I built from the other fragments'
+              Mulliken shell charges (the ESP)
+  Sec. 2.3    monomer charges iterated to self-consistency in each other's
+              ESP, then dimers and trimers solved in the frozen ESP
+READINGS (listed in the design notes):
+  C-2  E_I, E_IJ, E_IJK are internal energies; the ESP acts only through the
+       density, and dE^V supplies the embedding interaction.
+  C-9  the monomer loop is Jacobi-style (all monomers in the ESP of the
+       previous iterate) unless gauss_seidel=True.
+  C-10 SCC dimer iff the closest inter-fragment atom distance < dimer_cut;
+       SCC trimer iff all three pair distances < trimer_cut.
+  C-11 E^V_{X,Y} sums over fragments K not in the n-mer Y.
+  C-12 only SCC trimers contribute; their sub-pair terms are the FMO2 ones.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import multiprocessing as mp
+
+import numpy as np
+
+from . import xtb
+
+ANGSTROM = 1.0 / 0.529177210903
+
+
+@dataclasses.dataclass
+class FMOOptions:
+    level: int = 2
+    dimer_cut: float = 4.0 * ANGSTROM          # bohr
+    trimer_cut: float = 4.0 * ANGSTROM         # bohr
+    all_dimers_scc: bool = False
+    scc_tol: float = 1e-10
+    e_tol: float = 1e-10
+    outer_tol: float = 1e-10
+    max_iter: int = 300
+    max_outer: int = 200
+    gauss_seidel: bool = False
+    workers: int = 1
+    mixer: str = "broyden"
+
+
+@dataclasses.dataclass
+class FMOResult:
+    e_fmo1: float
+    e_fmo2: float
+    e_fmo3: float | None
+    e_mono: np.ndarray                  # internal monomer energies E'_I
+    dq_mono: list                       # per fragment shell charges
+    outer_iterations: int
+    dimers: np.ndarray                  # (n_pair, 2) all pairs I<J
+    dimer_scc: np.ndarray               # bool: SCC (True) or ES-DIM
+    dE_dimer: np.ndarray                # dE_IJ of Eq. 12
+    e_dimer: np.ndarray                 # E'_IJ (nan for ES-DIM)
+    dEV_dimer: np.ndarray               # dE^V_IJ (0 for ES-DIM)
+    trimers: np.ndarray                 # (n_tri, 2) SCC trimers I<J<K
+    dE_trimer: np.ndarray               # dE_IJK of Eq. 17
+    corr_trimer: np.ndarray             # dE_IJK - dE_IJ - dE_IK - dE_JK
+    mono_iters: np.ndarray
+    dimer_iters: np.ndarray
+
+
+class _Frags:
+    """Per-fragment atoms, shell positions and shell hardnesses."""
+
+    def __init__(self, system, params):
+        self.system = system
+        self.params = params
+        self.atoms = [np.nonzero(system.frag == f)[0] for f in range(system.n_frag)]
+        self.cn = xtb.coordination_numbers(system.Z, system.xyz, params)
+        self.sh_pos, self.sh_eta, self.n_sh = [], [], []
+        for f in range(system.n_frag):
+            Z = system.Z[self.atoms[f]]
+            b = xtb.make_basis(Z, params)
+            self.sh_pos.append(system.xyz[self.atoms[f]][b.sh_atom])
+            self.sh_eta.append(xtb.shell_hardness(Z, b, params))
+            self.n_sh.append(b.n_sh)
+
+    def gamma(self, I, J):
+        return xtb.gamma_between(self.sh_pos[I], self.sh_eta[I], self.sh_pos[J], self.sh_eta[J],
+                                 self.params.k_g)
+
+    def esp(self, nmer, dq_mono):
+        """ESP^{not X}_mu on the shells of n-mer X from the monomer charges of
+        every fragment K outside X (Eq. 21 / READING C-11)."""
+        out = []
+        for I in nmer:
+            v = np.zeros(self.n_sh[I])
+            for K in range(self.system.n_frag):
+                if K in nmer:
+                    continue
+                v += self.gamma(I, K) @ dq_mono[K]
+            out.append(v)
+        return np.concatenate(out)
+
+    def closest(self, I, J):
+        a = self.system.xyz[self.atoms[I]]
+        b = self.system.xyz[self.atoms[J]]
+        return float(np.sqrt(((a[:, None, :] - b[None, :, :]) ** 2).sum(-1)).min())
+
+    def solve(self, nmer, esp, guess, opts):
+        idx = np.concatenate([self.atoms[f] for f in nmer])
+        s = self.system
+        mixer = xtb.Broyden() if opts.mixer == "broyden" else xtb.LinearMixer(0.4)
+        return xtb.scc(s.Z[idx], s.xyz[idx], self.params, self.cn[idx], esp=esp, guess=guess,
+                       charge=float(sum(s.frag_charge[f] for f in nmer)), tol=opts.scc_tol,
+                       e_tol=opts.e_tol, max_iter=opts.max_iter, mixer=mixer)
+
+
+_POOL_STATE = {}
+
+
+def _pool_init(system, params):
+    _POOL_STATE["fr"] = _Frags(system, params)
+
+
+def _pool_solve(args):
+    nmer, esp, guess, opts = args
+    r = _POOL_STATE["fr"].solve(nmer, esp, guess, opts)
+    return r.energy, r.dq, r.iterations, r.converged
+
+
+def fmo(system, params, opts: FMOOptions | None = None) -> FMOResult:
+    opts = FMOOptions() if opts is None else opts
+    fr = _Frags(system, params)
+    nf = system.n_frag
+    pool = None
+    if opts.workers > 1:
+        pool = mp.get_context("spawn").Pool(opts.workers, initializer=_pool_init,
+                                            initargs=(system, params))
+
+    def run_many(jobs):
+        if pool is None:
+            out = []
+            for nmer, esp, guess in jobs:
+                r = fr.solve(nmer, esp, guess, opts)
+                out.append((r.energy, r.dq, r.iterations, r.converged))
+            return out
+        return pool.map(_pool_solve, [(n, e, g, opts) for (n, e, g) in jobs], chunksize=4)
+
+    try:
+        # ---- monomer self-consistency in the ESP (Sec. 2.3)
+        dq_mono = [np.zeros(fr.n_sh[I]) for I in range(nf)]
+        e_mono = np.zeros(nf)
+        mono_iters = np.zeros(nf, dtype=np.int64)
+        outer = 0
+        for outer in range(1, opts.max_outer + 1):
+            change = 0.0
+            if opts.gauss_seidel:
+                for I in range(nf):
+                    (e, dq, it, ok), = run_many([((I,), fr.esp((I,), dq_mono), dq_mono[I])])
+                    change = max(change, float(np.max(np.abs(dq - dq_mono[I]))))
+                    dq_mono[I], e_mono[I], mono_iters[I] = dq, e, mono_iters[I] + it
+            else:
+                jobs = [((I,), fr.esp((I,), dq_mono), dq_mono[I]) for I in range(nf)]
+                res = run_many(jobs)
+                for I, (e, dq, it, ok) in enumerate(res):
+                    change = max(change, float(np.max(np.abs(dq - dq_mono[I]))))
+                    dq_mono[I], e_mono[I], mono_iters[I] = dq, e, mono_iters[I] + it
+            if change < opts.outer_tol:
+                break
+        e_fmo1 = float(np.sum(e_mono))
+
+        # ---- dimers (Eqs. 12-15)
+        pairs = np.array([(I, J) for I in range(nf) for J in range(I + 1, nf)], dtype=np.int64).reshape(-1, 2)
+        rmin = np.array([fr.closest(I, J) for I, J in pairs])
+        scc_pair = np.ones(len(pairs), dtype=bool) if opts.all_dimers_scc else rmin < opts.dimer_cut
+        dE = np.zeros(len(pairs))
+        e_dim = np.full(len(pairs), np.nan)
+        dEV = np.zeros(len(pairs))
+        d_iters = np.zeros(len(pairs), dtype=np.int64)
+        jobs, where = [], []
+        for k, (I, J) in enumerate(pairs):
+            if scc_pair[k]:
+                esp = fr.esp((I, J), dq_mono)
+                jobs.append(((I, J), esp, np.concatenate([dq_mono[I], dq_mono[J]])))
+                where.append(k)
+            else:
+                dE[k] = float(dq_mono[I] @ fr.gamma(I, J) @ dq_mono[J])       # Eq. 15
+        for k, (job, (e, dq, it, ok)) in zip(where, zip(jobs, run_many(jobs))):
+            I, J = pairs[k]
+            esp = job[1]
+            ddq = dq - np.concatenate([dq_mono[I], dq_mono[J]])              # Eq. 14
+            dEV[k] = float(ddq @ esp)                                        # Eq. 13
+            e_dim[k] = e
+            dE[k] = e - e_mono[I] - e_mono[J] + dEV[k]                       # Eq. 12
+            d_iters[k] = it
+        e_fmo2 = e_fmo1 + float(np.sum(dE))
+
+        # ---- trimers (Eqs. 16-19)
+        trimers = np.zeros((0, 3), dtype=np.int64)
+        dE3 = np.zeros(0)
+        corr = np.zeros(0)
+        e_fmo3 = None
+        if opts.level >= 3:
+            pair_index = {(int(I), int(J)): k for k, (I, J) in enumerate(pairs)}
+            near = {(int(I), int(J)) for (I, J), r in zip(pairs, rmin) if r < opts.trimer_cut}
+            tri = [t for t in itertools.combinations(range(nf), 3)
+                   if (t[0], t[1]) in near and (t[0], t[2]) in near and (t[1], t[2]) in near]
+            trimers = np.array(tri, dtype=np.int64).reshape(-1, 3)
+            jobs = [(tuple(t), fr.esp(tuple(t), dq_mono),
+                     np.concatenate([dq_mono[f] for f in t])) for t in tri]
+            res = run_many(jobs)
+            dE3 = np.zeros(len(tri))
+            corr = np.zeros(len(tri))
+            for k, (t, job, (e, dq, it, ok)) in enumerate(zip(tri, jobs, res)):
+                I, J, K = t
+                ddq = dq - np.concatenate([dq_mono[f] for f in t])
+                dEV3 = float(ddq @ job[1])                                   # Eq. 18 / C-11
+                dE3[k] = e - e_mono[I] - e_mono[J] - e_mono[K] + dEV3        # Eq. 17
+                corr[k] = (dE3[k] - dE[pair_index[(I, J)]] - dE[pair_index[(I, K)]]
+                           - dE[pair_index[(J, K)]])                         # Eq. 16
+            e_fmo3 = e_fmo2 + float(np.sum(corr))
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+
+    return FMOResult(e_fmo1=e_fmo1, e_fmo2=e_fmo2, e_fmo3=e_fmo3, e_mono=e_mono, dq_mono=dq_mono,
+                     outer_iterations=outer, dimers=pairs, dimer_scc=scc_pair, dE_dimer=dE,
+                     e_dimer=e_dim, dEV_dimer=dEV, trimers=trimers, dE_trimer=dE3,
+                     corr_trimer=corr, mono_iters=mono_iters, dimer_iters=d_iters)
