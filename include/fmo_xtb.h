@@ -1,0 +1,231 @@
+/*
+ * fmo_xtb.h - C ABI of the batched FMO-xTB self-consistent-charge library.
+ *
+ * The library computes the fragment molecular orbital (FMO) energy of a
+ * molecular system with GFN1-xTB fragments, as stated in Sec. 2.2-2.3 of
+ * Einsele & Mitric, "FMO-xTB: Fragment molecular orbital method with
+ * GFN1-xTB":
+ *   in:  geometry, fragment partition, element parameter table;
+ *   out: monomer energies and shell charges, dimer/trimer interaction
+ *        energies, and the FMO1/FMO2/FMO3 totals.
+ * All arithmetic runs in CUDA kernels on one GPU (sm_103a); the host code
+ * only validates input, plans batches and copies data.
+ *
+ * Conventions
+ *   - Units: bohr and Hartree.  Charges are in electrons, as population
+ *     minus reference occupation (positive = excess electrons).
+ *   - Every function returns fmo_status; FMO_OK is 0.  On error the context
+ *     keeps a message readable through fmo_last_error().  No C++ exception
+ *     crosses the ABI.
+ *   - Ownership: the caller owns every pointer it passes; the library copies
+ *     what it needs during the call and keeps no caller pointer.  Output
+ *     arrays are caller-allocated with the sizes stated per call.
+ *   - Threading: a context may be used by one host thread at a time.
+ */
+#ifndef FMO_XTB_H
+#define FMO_XTB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMO_MAX_Z 87     /* element slots 0..86 */
+#define FMO_MAX_SHELL 3  /* shells per element */
+#define FMO_MAX_PRIM 12  /* Gaussian primitives per shell */
+
+typedef enum {
+  FMO_OK = 0,
+  FMO_ERR_ARG = 1,           /* invalid argument or input */
+  FMO_ERR_CUDA = 2,          /* CUDA runtime error */
+  FMO_ERR_OOM = 3,           /* device allocation failed */
+  FMO_ERR_NOT_CONVERGED = 4, /* an SCC or the monomer loop hit its limit */
+  FMO_ERR_TIMEOUT = 5,       /* deadline passed; kernels stopped early */
+  FMO_ERR_NAN = 6,           /* non-finite value in a result */
+  FMO_ERR_STATE = 7,         /* call out of order (e.g. run before set_system) */
+  FMO_ERR_UNSUPPORTED = 8    /* feature or size not supported */
+} fmo_status;
+
+/* Per-n-mer status words written by the SCC kernel. */
+enum {
+  FMO_SCC_CONVERGED = 0,
+  FMO_SCC_MAX_ITER = 1,
+  FMO_SCC_NAN = 2,
+  FMO_SCC_TIMEOUT = 3,
+  FMO_SCC_JACOBI = 4          /* eigensolver sweep limit reached */
+};
+
+/*
+ * One element of the GFN1-xTB parameter table (Eqs. 2-11 of the paper; the
+ * values themselves are not printed in the paper and are an input).
+ * Shell k has angular momentum l[k] (0 = s, 1 = p) and the contracted
+ * function sum_p coef[k][p] * g(alpha[k][p]) where g is a primitive Gaussian
+ * normalised on its own (s: (2a/pi)^(3/4) e^{-a r^2}; p_x: the same times
+ * 2 sqrt(a) x).  n_shell == 0 marks an absent element.
+ */
+typedef struct fmo_element {
+  int32_t n_shell;
+  int32_t l[FMO_MAX_SHELL];
+  int32_t n_prim[FMO_MAX_SHELL];
+  int32_t pad_;
+  double alpha[FMO_MAX_SHELL][FMO_MAX_PRIM];
+  double coef[FMO_MAX_SHELL][FMO_MAX_PRIM];
+  double h_l[FMO_MAX_SHELL];     /* H_A^l, Eq. 10 (Eh) */
+  double k_cn_l[FMO_MAX_SHELL];  /* k_CN,l, Eq. 10 */
+  double k_poly_l[FMO_MAX_SHELL];/* k^poly_{A,l}, Eq. 9 */
+  double kappa_l[FMO_MAX_SHELL]; /* kappa_A^l, Eq. 5 */
+  double q0_l[FMO_MAX_SHELL];    /* reference shell occupation (e), Eq. 3 */
+  double eta;                    /* eta_A, Eq. 5 (Eh) */
+  double gamma3;                 /* Gamma_A, third-order term of Eq. 2 (Eh) */
+  double en;                     /* electronegativity, Delta EN of Eq. 8 */
+  double r_cov;                  /* covalent radius (bohr), Eq. 9 and CN */
+  double z_eff;                  /* Z^eff_A, Eq. 11 */
+  double alpha_rep;              /* alpha_A, Eq. 11 */
+} fmo_element;
+
+/* The whole table plus the global parameters of Eqs. 4, 8, 11 and the CN. */
+typedef struct fmo_params {
+  fmo_element el[FMO_MAX_Z];
+  double k_l[3];                 /* k_l of Eq. 8 for l = s, p, d */
+  double k_ab[FMO_MAX_Z][FMO_MAX_Z]; /* K_AB of Eq. 8 */
+  double k_en;                   /* k_EN of Eq. 8 */
+  double k_g;                    /* k_g of Eq. 4 */
+  double k_f;                    /* k_f of Eq. 11 */
+  double cn_k1, cn_k2;           /* k_1, k_2 of the CN counting function */
+  double cn_cutoff;              /* pairs at R >= cutoff are not counted (bohr) */
+  double t_el;                   /* electronic temperature of Eq. 6 (K) */
+  double v_hop;                  /* HOP projector strength (Eh) */
+} fmo_params;
+
+enum { FMO_PREC_FP64 = 0, FMO_PREC_MIXED = 1 };
+
+typedef struct fmo_options {
+  int32_t level;            /* 1 = FMO1, 2 = FMO2 (Eq. 12), 3 = FMO3 (Eq. 16) */
+  int32_t precision;        /* FMO_PREC_FP64 or FMO_PREC_MIXED (FP32 loose
+                               iterations, then FP64 to convergence) */
+  int32_t all_dimers_scc;   /* 1: every pair gets an SCC dimer (no ES-DIM) */
+  int32_t max_iter;         /* SCC iterations per n-mer solve */
+  int32_t max_outer;        /* monomer ESP iterations */
+  int32_t guess;            /* 0 neutral charges, 2 user charges (fmo_set_guess) */
+  int32_t schedule;         /* 0 autotuned block size, 1 fixed block size */
+  int32_t reserved_;
+  double dimer_cut;         /* SCC dimer iff closest atom pair < dimer_cut (bohr) */
+  double trimer_cut;        /* SCC trimer iff all three pairs < trimer_cut */
+  double scc_tol;           /* max |dq_out - dq_in| at SCC convergence (e) */
+  double e_tol;             /* |E - E_prev| at SCC convergence (Eh) */
+  double outer_tol;         /* monomer loop: max charge change (e) */
+  double mixed_switch_tol;  /* mixed: FP32 until max |dq_out - dq_in| < this */
+  double deadline_s;        /* wall-clock limit per fmo_run, 0 = none */
+} fmo_options;
+
+/* Counters of the last fmo_run. */
+typedef struct fmo_stats {
+  int64_t n_monomer_solves;   /* monomer SCCs summed over outer iterations */
+  int64_t n_dimer_scc;        /* SCC dimers */
+  int64_t n_dimer_esdim;      /* ES-DIM pairs (Eq. 15) */
+  int64_t n_trimer_scc;       /* SCC trimers */
+  int64_t scc_iterations;     /* all SCC iterations of all solves */
+  int64_t kernel_launches;    /* CUDA kernels launched by the run */
+  int32_t outer_iterations;   /* monomer ESP iterations */
+  int32_t n_failed;           /* n-mers whose status is not CONVERGED */
+  double ms_setup, ms_monomer, ms_select, ms_dimer, ms_trimer, ms_reduce;
+  /* per pass p = 0 monomers (all outer iterations), 1 dimers, 2 trimers */
+  double ms_scc[3];           /* SCC kernel launches alone (CUDA events, same stream) */
+  int64_t scc_launches[3];    /* SCC kernel launches */
+  int64_t iters_fp32[3];      /* SCC iterations run in FP32 (mixed precision) */
+  int64_t iters_fp64[3];      /* SCC iterations run in FP64 */
+  double flops_fp32[3];       /* algorithmic flops: 15 n^3 per SCC iteration of an */
+  double flops_fp64[3];       /* n-AO n-mer (transform 4n^3, density 2n^3, eigen 9n^3) */
+  int64_t h2d_bytes;          /* host -> device bytes copied by the run */
+  int64_t d2h_bytes;          /* device -> host bytes copied by the run */
+} fmo_stats;
+
+typedef struct fmo_ctx fmo_ctx;
+
+/* Fill *o with the defaults: level 2, FP64, ES-DIM on, cut 4.0 A, tolerances
+ * 1e-10, max_iter 300, max_outer 200, switch 1e-5, no deadline. */
+void fmo_options_default(fmo_options *o);
+
+/* Create a context on CUDA device `device` with a copy of the table *p.
+ * Errors: FMO_ERR_ARG (NULL pointers, element with n_prim > FMO_MAX_PRIM or
+ * l > 1), FMO_ERR_CUDA (no such device). */
+fmo_status fmo_create(fmo_ctx **out, const fmo_params *p, int device);
+
+/*
+ * Define the system (Sec. 2.2: N fragments).
+ *   Z[n_atoms]             atomic numbers; each must be present in the table
+ *   xyz[3*n_atoms]         coordinates (bohr), atom-major (x0,y0,z0,x1,...)
+ *   frag_of_atom[n_atoms]  fragment index 0..n_frag-1; every fragment non-empty
+ *   frag_charge[n_frag]    net charge of each fragment (e)
+ *   n_cut, bda_baa[2*n_cut] covalent bonds cut between fragments (BDA, BAA);
+ *                          must be 0 / NULL in this version
+ * Each n-mer must hold an even number of electrons (closed shell).
+ * Errors: FMO_ERR_ARG on any violation, FMO_ERR_UNSUPPORTED for n_cut > 0.
+ */
+fmo_status fmo_set_system(fmo_ctx *ctx, int32_t n_atoms, const int32_t *Z, const double *xyz,
+                          int32_t n_frag, const int32_t *frag_of_atom, const int32_t *frag_charge,
+                          int32_t n_cut, const int32_t *bda_baa);
+
+/* New coordinates for the same atoms and partition: host array xyz[3*n_atoms]
+ * (bohr, input atom order), copied to the device on the context's stream. */
+fmo_status fmo_set_coordinates(fmo_ctx *ctx, const double *xyz);
+
+/* The same, from a device array (3*n_atoms doubles, input atom order) that
+ * is read on `cuda_stream`.  With a stream, the call only enqueues the gather:
+ * run fmo_run on the same stream (or order the two streams).  With NULL the
+ * context's stream is used and the call returns when the copy is done. */
+fmo_status fmo_set_coordinates_device(fmo_ctx *ctx, const double *xyz_dev, void *cuda_stream);
+
+/* User initial monomer shell charges (options.guess = 2), n_shell values in
+ * the output order of fmo_get_monomers. */
+fmo_status fmo_set_guess(fmo_ctx *ctx, const double *shell_dq);
+
+/*
+ * Run the FMO calculation (Sec. 2.3): coordination numbers of the whole
+ * system, monomer SCCs iterated to self-consistency in each other's ESP,
+ * n-mer selection, SCC dimers (and trimers) in the frozen ESP, ES-DIM pairs,
+ * and the FMO sums of Eqs. 12-19.  Work is issued on `cuda_stream` (NULL: the
+ * context's own stream); the call returns after the results are on the host.
+ * Returns FMO_ERR_NOT_CONVERGED if any SCC or the monomer loop hit its limit
+ * (results are still readable), FMO_ERR_TIMEOUT if the deadline passed.
+ */
+fmo_status fmo_run(fmo_ctx *ctx, const fmo_options *opt, void *cuda_stream);
+
+/* Totals of the last run: FMO1 = sum E_I, FMO2 (Eq. 12), FMO3 (Eq. 16; NaN
+ * unless level 3).  Any pointer may be NULL. */
+fmo_status fmo_get_energy(fmo_ctx *ctx, double *e_fmo1, double *e_fmo2, double *e_fmo3);
+
+/* Number of shells of the whole system (length of shell_dq below). */
+fmo_status fmo_get_sizes(fmo_ctx *ctx, int32_t *n_shell, int32_t *n_ao);
+
+/* Monomer results: E_I[n_frag] internal energies, shell_dq[n_shell] (fragments
+ * in index order, atoms in input order within a fragment, shells in table
+ * order), iters[n_frag] SCC iterations of the final outer pass,
+ * status[n_frag] FMO_SCC_* words.  Any pointer may be NULL. */
+fmo_status fmo_get_monomers(fmo_ctx *ctx, double *E_I, double *shell_dq, int32_t *iters,
+                            int32_t *status);
+
+/* Pairs I<J of the last run in lexicographic order; *n receives the count
+ * n_frag(n_frag-1)/2.  ij[2n], dE[n] (dE_IJ of Eq. 12 or Eq. 15), e_dimer[n]
+ * (internal E_IJ, NaN for ES-DIM), dEV[n] (Eq. 13), scc[n] (1 = SCC dimer),
+ * iters[n].  Any array pointer may be NULL. */
+fmo_status fmo_get_dimers(fmo_ctx *ctx, int64_t *n, int32_t *ij, double *dE, double *e_dimer,
+                          double *dEV, uint8_t *scc, int32_t *iters);
+
+/* SCC trimers I<J<K of the last level-3 run: ijk[3n], dE3[n] (Eq. 17),
+ * corr[n] (dE_IJK - dE_IJ - dE_IK - dE_JK). */
+fmo_status fmo_get_trimers(fmo_ctx *ctx, int64_t *n, int32_t *ijk, double *dE3, double *corr);
+
+fmo_status fmo_get_stats(fmo_ctx *ctx, fmo_stats *st);
+
+/* Message of the last error on this context ("" if none). */
+const char *fmo_last_error(const fmo_ctx *ctx);
+
+/* Free the context and its device memory.  NULL is allowed. */
+void fmo_destroy(fmo_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMO_XTB_H */

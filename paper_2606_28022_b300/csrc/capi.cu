@@ -1,0 +1,955 @@
+// Host side of the C ABI declared in include/fmo_xtb.h: validation, the
+// fragment/n-mer bookkeeping, device memory, and the order of the passes of
+// Sec. 2.3 of the paper (monomer loop in the ESP, then dimers and trimers in
+// the frozen ESP, then the FMO sums).  Every arithmetic step of the method
+// runs in the kernels of kernels.cu.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fmo_xtb.h"
+#include "kernels.h"
+
+using namespace fmo;
+
+namespace {
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    cap = want;
+    return cudaSuccess;
+  }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+  void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
+};
+
+struct Pass {
+  std::vector<Nmer> nm;
+  std::vector<int> order;
+  int max_n = 0, max_nsh = 0, max_nat = 0, max_pairs = 0;
+  long long tot_mat = 0, tot_sh = 0, tot_gam = 0, tot_ao = 0, tot_hist = 0, tot_apad = 0;
+  DevBuf d_nm, d_order, S, H0, gam, CTd, W1d, W2d, Agd, CTf, W1f, W2f, Agf, esp, dq, eps, hist;
+  DevBuf energy, e_el, e_rep, dEV, iters, iters32, status;
+  std::vector<int> h_iters, h_iters32;
+  void release() {
+    for (DevBuf* b : {&d_nm, &d_order, &S, &H0, &gam, &CTd, &W1d, &W2d, &Agd, &CTf, &W1f, &W2f, &Agf, &esp, &dq,
+                      &eps, &hist, &energy, &e_el, &e_rep, &dEV, &iters, &iters32, &status})
+      b->release();
+  }
+};
+
+// Pinned staging for every host <-> device copy (no pageable transfers).
+// Regions are handed out from page-locked chunks; device->host results are
+// copied to their destination after the stream is synchronised (flush), and
+// all regions are recycled at that point.
+struct Staging {
+  struct Chunk { char* p; size_t cap; size_t used; };
+  struct Pending { void* dst; const void* src; size_t bytes; };
+  std::vector<Chunk> chunks;
+  std::vector<Pending> pend;
+  void* take(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    for (auto& c : chunks)
+      if (c.cap - c.used >= bytes) { void* r = c.p + c.used; c.used += bytes; return r; }
+    const size_t cap = std::max<size_t>(bytes, size_t(8) << 20);
+    char* p = nullptr;
+    if (cudaMallocHost((void**)&p, cap) != cudaSuccess) return nullptr;
+    chunks.push_back({p, cap, bytes});
+    return p;
+  }
+  void flush() {
+    for (auto& q : pend) std::memcpy(q.dst, q.src, q.bytes);
+    pend.clear();
+    for (auto& c : chunks) c.used = 0;
+  }
+  void release() {
+    for (auto& c : chunks) cudaFreeHost(c.p);
+    chunks.clear();
+    pend.clear();
+  }
+};
+
+}  // namespace
+
+struct fmo_ctx {
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  std::string err;
+  fmo_params params;
+  // compact element table
+  int ne = 0;
+  int z_to_e[FMO_MAX_Z];
+  std::vector<DevElem> h_el;
+  std::vector<double> h_kab;
+  DevBuf d_el, d_kab;
+  GParams g;
+  int smem_optin = 0;
+  // system
+  bool have_system = false;
+  int n_atoms = 0, n_frag = 0, n_sh = 0, n_ao = 0;
+  std::vector<int> perm;                  // internal atom i <- input atom perm[i]
+  std::vector<int> h_elem, h_atom_sh0, h_sh_atom;
+  std::vector<int> f_atom0, f_nat, f_sh0, f_nsh, f_ao0, f_nao;
+  std::vector<double> f_nel, h_sh_inv_eta;
+  DevBuf d_xyz, d_xyz_in, d_perm, d_elem, d_cn, d_atom_sh0, d_sh_atom, d_sh_inv_eta;
+  DevBuf d_f_atom0, d_f_nat, d_f_sh0, d_f_nsh, d_f_ao0, d_f_nao;
+  DevBuf d_dq_mono, d_phi, d_bounds, d_rmin, d_scalar, d_t0;
+  DevBuf d_pair_scc, d_dE_pair, d_esdim_pairs, d_esdim_idx, d_tri_frag, d_dE3, d_corr, d_totals;
+  std::vector<double> guess;
+  bool have_guess = false;
+  Pass mono, dim, tri;
+  // results of the last run
+  bool have_result = false;
+  int last_level = 0;
+  double totals[3] = {0, 0, 0};
+  std::vector<double> r_e_mono, r_dq_mono, r_dE_pair, r_e_dim_pair, r_dEV_pair;
+  std::vector<int> r_mono_iters, r_mono_status, r_pair_iters;
+  std::vector<uint8_t> r_pair_scc;
+  std::vector<int> r_tri;
+  std::vector<double> r_dE3, r_corr;
+  fmo_stats stats;
+  Staging stg;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
+
+  FragTab ftab() const {
+    return FragTab{d_f_atom0.as<int>(), d_f_nat.as<int>(), d_f_sh0.as<int>(),
+                   d_f_nsh.as<int>(), d_f_ao0.as<int>(), d_f_nao.as<int>()};
+  }
+};
+
+namespace {
+
+fmo_status fail(fmo_ctx* c, fmo_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+#define CK(x)                                                                             \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? FMO_ERR_OOM : FMO_ERR_CUDA,     \
+                  std::string(#x) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+// host <-> device copies through pinned staging, counted in the run statistics
+fmo_ctx* g_ctx = nullptr;   // context of the current call (one host thread per context)
+
+cudaError_t h2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  void* s = g_ctx->stg.take(bytes);
+  if (!s) return cudaErrorMemoryAllocation;
+  std::memcpy(s, src, bytes);
+  g_ctx->h2d_bytes += (int64_t)bytes;
+  return cudaMemcpyAsync(dst, s, bytes, cudaMemcpyHostToDevice, st);
+}
+// The host destination is written at the next sync_stream().
+cudaError_t d2h(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  void* s = g_ctx->stg.take(bytes);
+  if (!s) return cudaErrorMemoryAllocation;
+  g_ctx->d2h_bytes += (int64_t)bytes;
+  g_ctx->stg.pend.push_back({dst, s, bytes});
+  return cudaMemcpyAsync(s, src, bytes, cudaMemcpyDeviceToHost, st);
+}
+cudaError_t sync_stream(cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) g_ctx->stg.flush();
+  return e;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+  cudaError_t e = b.ensure(sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  return h2d(b.p, v.data(), sizeof(T) * v.size(), st);
+}
+
+int elem_nao(const DevElem& e) {
+  int n = 0;
+  for (int s = 0; s < e.nsh; ++s) n += 2 * e.l[s] + 1;
+  return n;
+}
+
+// Lay out a pass of n-mers (tuples of fragments) and size its buffers.
+cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3>>& tuples,
+                      const std::vector<int>& nf, bool monomer_layout, int precision, cudaStream_t st) {
+  P.nm.clear();
+  P.max_n = P.max_nsh = P.max_nat = P.max_pairs = 0;
+  long long mat = 0, sh = 0, gam = 0, ao = 0, hist = 0, apad = 0;
+  for (size_t t = 0; t < tuples.size(); ++t) {
+    Nmer m{};
+    m.nfrag = nf[t];
+    int n = 0, ns = 0, na = 0;
+    double nel = 0.0;
+    for (int k = 0; k < 3; ++k) m.frag[k] = (k < m.nfrag) ? tuples[t][k] : -1;
+    for (int k = 0; k < m.nfrag; ++k) {
+      const int f = tuples[t][k];
+      n += ctx->f_nao[f];
+      ns += ctx->f_nsh[f];
+      na += ctx->f_nat[f];
+      nel += ctx->f_nel[f];
+    }
+    m.n = n; m.nsh = ns; m.nat = na; m.npad = n + (n & 1); m.nel = nel;
+    m.mat = mat; m.gam = gam; m.aov = ao; m.hist = hist; m.apad = apad;
+    m.shv = monomer_layout ? ctx->f_sh0[tuples[t][0]] : sh;
+    mat += (long long)n * n;
+    sh += ns;
+    gam += (long long)ns * ns;
+    ao += m.npad;
+    hist += (long long)(2 * kHist + 2) * ns;
+    apad += (long long)m.npad * m.npad;
+    P.max_n = std::max(P.max_n, n);
+    P.max_nsh = std::max(P.max_nsh, ns);
+    P.max_nat = std::max(P.max_nat, na);
+    P.max_pairs = std::max(P.max_pairs, na * (na + 1) / 2);
+    P.nm.push_back(m);
+  }
+  if (monomer_layout) sh = ctx->n_sh;
+  P.tot_mat = mat; P.tot_sh = sh; P.tot_gam = gam; P.tot_ao = ao; P.tot_hist = hist; P.tot_apad = apad;
+  // longest-processing-time-first order of the blocks
+  P.order.resize(P.nm.size());
+  for (size_t i = 0; i < P.order.size(); ++i) P.order[i] = int(i);
+  std::stable_sort(P.order.begin(), P.order.end(), [&](int a, int b) { return P.nm[a].n > P.nm[b].n; });
+  const size_t nn = std::max<size_t>(P.nm.size(), 1);
+  cudaError_t e;
+#define ENS(buf, bytes) if ((e = (buf).ensure(bytes)) != cudaSuccess) return e
+  ENS(P.S, sizeof(double) * mat);
+  ENS(P.H0, sizeof(double) * mat);
+  ENS(P.gam, sizeof(double) * gam);
+  ENS(P.CTd, sizeof(double) * mat);
+  ENS(P.W1d, sizeof(double) * mat);
+  ENS(P.W2d, sizeof(double) * mat);
+  if (precision == FMO_PREC_MIXED) {
+    ENS(P.CTf, sizeof(float) * mat);
+    ENS(P.W1f, sizeof(float) * mat);
+    ENS(P.W2f, sizeof(float) * mat);
+  }
+  ENS(P.esp, sizeof(double) * std::max<long long>(sh, 1));
+  ENS(P.dq, sizeof(double) * std::max<long long>(sh, 1));
+  ENS(P.eps, sizeof(double) * ao);
+  ENS(P.hist, sizeof(double) * hist);
+  ENS(P.energy, sizeof(double) * nn);
+  ENS(P.e_el, sizeof(double) * nn);
+  ENS(P.e_rep, sizeof(double) * nn);
+  ENS(P.dEV, sizeof(double) * nn);
+  ENS(P.iters, sizeof(int) * nn);
+  ENS(P.iters32, sizeof(int) * nn);
+  ENS(P.status, sizeof(int) * nn);
+#undef ENS
+  if ((e = upload(P.d_nm, P.nm, st)) != cudaSuccess) return e;
+  if ((e = upload(P.d_order, P.order, st)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+struct SmemPlan {
+  int a_d, a_f;
+  size_t bytes;
+};
+
+// Limits of the fixed-size index maps of the integral and gamma kernels.
+bool pass_fits(const Pass& P) { return P.max_nat <= 512 && P.max_nsh <= 1024 && P.max_n <= 4000; }
+
+SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision) {
+  const int npad = P.max_n + (P.max_n & 1);
+  SmemPlan sp{0, 0, 0};
+  const size_t lim = (size_t)ctx->smem_optin;
+  const size_t with_d = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 8 * npad * npad);
+  const size_t with_f = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 4 * npad * npad);
+  if (with_d <= lim) { sp.a_d = 1; sp.a_f = (precision == FMO_PREC_MIXED); }
+  else if (precision == FMO_PREC_MIXED && with_f <= lim) { sp.a_f = 1; }
+  sp.bytes = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, (sp.a_d ? 8 : (sp.a_f ? 4 : 0)) * npad * npad);
+  return sp;
+}
+
+// S, H0, gamma and the Loewdin start of every n-mer of a pass.
+fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, cudaStream_t st) {
+  const int nn = int(P.nm.size());
+  if (nn == 0) return FMO_OK;
+  const SmemPlan& s = sp;
+  if (!s.a_d) CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
+  if (precision == FMO_PREC_MIXED && !s.a_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
+  CK(launch_integrals(st, nn, P.max_pairs, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
+                      ctx->d_elem.as<int>(), ctx->d_atom_sh0.as<int>(), ctx->d_cn.as<double>(),
+                      ctx->d_el.as<DevElem>(), ctx->d_kab.as<double>(), ctx->ne, ctx->g, P.S.as<double>(),
+                      P.H0.as<double>()));
+  CK(launch_gamma(st, nn, P.max_nsh, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
+                  ctx->d_elem.as<int>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(), ctx->g,
+                  P.gam.as<double>()));
+  CK(cudaMemsetAsync(P.status.p, 0, sizeof(int) * nn, st));
+  const bool use_f = (precision == FMO_PREC_MIXED);
+  const int npad = P.max_n + (P.max_n & 1);
+  const size_t lim = (size_t)ctx->smem_optin;
+  const int elb = use_f ? 4 : 8;
+  const int a_in = ((size_t)elb * npad * npad + 64 * 1024 <= lim) ? 1 : 0;
+  if (!a_in) {
+    if (use_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
+    else CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
+  }
+  CK(launch_lowdin(st, nn, P.max_n, P.d_nm.as<Nmer>(), P.S.as<double>(),
+                   use_f ? P.CTf.p : P.CTd.p, use_f ? P.W1f.p : P.W1d.p, use_f ? P.Agf.p : P.Agd.p,
+                   use_f ? 1 : 0, a_in, P.status.as<int>()));
+  ctx->stats.kernel_launches += 3;
+  return FMO_OK;
+}
+
+fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& sp, bool with_phi,
+                   int pass_id, cudaStream_t st) {
+  const int nn = int(P.nm.size());
+  if (nn == 0) return FMO_OK;
+  SccLaunch L{};
+  L.nmers = P.d_nm.as<Nmer>(); L.order = P.d_order.as<int>(); L.ft = ctx->ftab();
+  L.xyz = ctx->d_xyz.as<double>(); L.elem = ctx->d_elem.as<int>(); L.atom_sh0 = ctx->d_atom_sh0.as<int>();
+  L.el = ctx->d_el.as<DevElem>(); L.g = ctx->g; L.S = P.S.as<double>(); L.H0 = P.H0.as<double>();
+  L.gam = P.gam.as<double>();
+  L.CTd = P.CTd.as<double>(); L.W1d = P.W1d.as<double>(); L.W2d = P.W2d.as<double>(); L.Agd = P.Agd.as<double>();
+  L.CTf = P.CTf.as<float>(); L.W1f = P.W1f.as<float>(); L.W2f = P.W2f.as<float>(); L.Agf = P.Agf.as<float>();
+  L.phi = with_phi ? ctx->d_phi.as<double>() : nullptr;
+  L.dq_mono = ctx->d_dq_mono.as<double>();
+  L.esp = P.esp.as<double>(); L.dq = P.dq.as<double>(); L.eps = P.eps.as<double>(); L.hist = P.hist.as<double>();
+  L.energy = P.energy.as<double>(); L.e_el = P.e_el.as<double>(); L.e_rep = P.e_rep.as<double>();
+  L.dEV = P.dEV.as<double>(); L.iters = P.iters.as<int>(); L.iters32 = P.iters32.as<int>();
+  L.status = P.status.as<int>();
+  L.guess_from_mono = 1;
+  L.precision = o.precision;
+  L.max_iter = o.max_iter;
+  L.fp32_cap = std::max(4, o.max_iter / 2);
+  L.tol = o.scc_tol; L.etol = o.e_tol; L.switch_tol = o.mixed_switch_tol;
+  L.jacobi_tol_d = 1e-14;
+  L.jacobi_tol_f = 2e-7;
+  L.t0 = ctx->d_t0.as<unsigned long long>();
+  L.budget_ns = o.deadline_s > 0 ? (unsigned long long)(o.deadline_s * 1e9) : 0ULL;
+  L.a_smem_d = sp.a_d; L.a_smem_f = sp.a_f;
+  L.max_n = P.max_n; L.max_nsh = P.max_nsh; L.max_nat = P.max_nat;
+  if (!sp.a_d) CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
+  if (o.precision == FMO_PREC_MIXED && !sp.a_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
+  L.Agd = P.Agd.as<double>(); L.Agf = P.Agf.as<float>();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  CK(launch_scc(st, nn, L));
+  cudaEventRecord(e1, st);
+  ctx->stats.kernel_launches += 1;
+  // iteration counts of this launch -> algorithmic flops of the pass
+  P.h_iters.resize(nn);
+  P.h_iters32.resize(nn);
+  CK(d2h(P.h_iters.data(), P.iters.p, sizeof(int) * nn, st));
+  CK(d2h(P.h_iters32.data(), P.iters32.p, sizeof(int) * nn, st));
+  CK(sync_stream(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->stats.ms_scc[pass_id] += ms;
+  ctx->stats.scc_launches[pass_id] += 1;
+  for (int i = 0; i < nn; ++i) {
+    const double n3 = 15.0 * double(P.nm[i].n) * P.nm[i].n * P.nm[i].n;
+    const int i32 = P.h_iters32[i], i64 = P.h_iters[i] - P.h_iters32[i];
+    ctx->stats.iters_fp32[pass_id] += i32;
+    ctx->stats.iters_fp64[pass_id] += i64;
+    ctx->stats.flops_fp32[pass_id] += n3 * i32;
+    ctx->stats.flops_fp64[pass_id] += n3 * i64;
+  }
+  return FMO_OK;
+}
+
+// FMO_DEBUG=1 in the environment: synchronise after each stage of fmo_run and
+// report it on stderr (diagnostics only; the computation is unchanged).
+bool debug_on() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("FMO_DEBUG"); v = (e && e[0] == '1') ? 1 : 0; }
+  return v == 1;
+}
+void stage(cudaStream_t st, const char* what, int k = -1) {
+  if (!debug_on()) return;
+  cudaError_t e = sync_stream(st);
+  fprintf(stderr, "[fmo] %s %d: %s\n", what, k, cudaGetErrorString(e));
+  fflush(stderr);
+}
+
+double now_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fmo_options_default(fmo_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->level = 2;
+  o->precision = FMO_PREC_FP64;
+  o->all_dimers_scc = 0;
+  o->max_iter = 300;
+  o->max_outer = 200;
+  o->guess = 0;
+  o->schedule = 0;
+  o->dimer_cut = 4.0 / 0.529177210903;
+  o->trimer_cut = 4.0 / 0.529177210903;
+  o->scc_tol = 1e-10;
+  o->e_tol = 1e-10;
+  o->outer_tol = 1e-10;
+  o->mixed_switch_tol = 1e-5;
+  o->deadline_s = 0.0;
+}
+
+fmo_status fmo_create(fmo_ctx** out, const fmo_params* p, int device) {
+  if (!out || !p) return FMO_ERR_ARG;
+  *out = nullptr;
+  for (int z = 0; z < FMO_MAX_Z; ++z) {
+    const fmo_element& e = p->el[z];
+    if (e.n_shell < 0 || e.n_shell > FMO_MAX_SHELL) return FMO_ERR_ARG;
+    for (int s = 0; s < e.n_shell; ++s) {
+      if (e.l[s] < 0 || e.l[s] > 1) return FMO_ERR_ARG;
+      if (e.n_prim[s] < 1 || e.n_prim[s] > FMO_MAX_PRIM) return FMO_ERR_ARG;
+    }
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FMO_ERR_CUDA;
+  fmo_ctx* ctx = new fmo_ctx();
+  ctx->device = device;
+  ctx->params = *p;
+  if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return FMO_ERR_CUDA; }
+  if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete ctx;
+    return FMO_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  for (int z = 0; z < FMO_MAX_Z; ++z) ctx->z_to_e[z] = -1;
+  std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+  *out = ctx;
+  return FMO_OK;
+}
+
+void fmo_destroy(fmo_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
+                    &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
+                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_dq_mono, &ctx->d_phi,
+                    &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_pair_scc, &ctx->d_dE_pair,
+                    &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
+                    &ctx->d_totals})
+    b->release();
+  ctx->stg.release();
+  ctx->mono.release();
+  ctx->dim.release();
+  ctx->tri.release();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+}
+
+const char* fmo_last_error(const fmo_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const double* xyz, int32_t n_frag,
+                          const int32_t* frag_of_atom, const int32_t* frag_charge, int32_t n_cut,
+                          const int32_t* bda_baa) {
+  g_ctx = ctx;
+  if (!ctx) return FMO_ERR_ARG;
+  (void)bda_baa;
+  if (n_atoms <= 0 || n_frag <= 0 || !Z || !xyz || !frag_of_atom || !frag_charge)
+    return fail(ctx, FMO_ERR_ARG, "empty system or NULL input");
+  if (n_cut != 0) return fail(ctx, FMO_ERR_UNSUPPORTED, "covalent boundaries (HOP) are not supported");
+  cudaSetDevice(ctx->device);
+  const fmo_params& p = ctx->params;
+  // elements present -> compact table
+  ctx->ne = 0;
+  for (int z = 0; z < FMO_MAX_Z; ++z) ctx->z_to_e[z] = -1;
+  ctx->h_el.clear();
+  std::vector<int> ez;
+  for (int i = 0; i < n_atoms; ++i) {
+    const int z = Z[i];
+    if (z <= 0 || z >= FMO_MAX_Z || p.el[z].n_shell == 0)
+      return fail(ctx, FMO_ERR_ARG, "atom " + std::to_string(i) + ": element not in the table");
+    if (!std::isfinite(xyz[3 * i]) || !std::isfinite(xyz[3 * i + 1]) || !std::isfinite(xyz[3 * i + 2]))
+      return fail(ctx, FMO_ERR_ARG, "non-finite coordinate");
+    if (frag_of_atom[i] < 0 || frag_of_atom[i] >= n_frag)
+      return fail(ctx, FMO_ERR_ARG, "fragment index out of range");
+    if (ctx->z_to_e[z] < 0) {
+      if (ctx->ne >= kMaxElem) return fail(ctx, FMO_ERR_UNSUPPORTED, "too many distinct elements");
+      ctx->z_to_e[z] = ctx->ne++;
+      ez.push_back(z);
+    }
+  }
+  for (int k = 0; k < ctx->ne; ++k) {
+    const fmo_element& src = p.el[ez[k]];
+    DevElem d{};
+    d.nsh = src.n_shell;
+    for (int s = 0; s < src.n_shell; ++s) {
+      d.l[s] = src.l[s];
+      d.nprim[s] = src.n_prim[s];
+      for (int q = 0; q < src.n_prim[s]; ++q) {
+        const double a = src.alpha[s][q];
+        double norm = std::pow(2.0 * a / M_PI, 0.75);
+        if (src.l[s] == 1) norm *= 2.0 * std::sqrt(a);
+        d.alpha[s][q] = a;
+        d.cn[s][q] = src.coef[s][q] * norm;
+      }
+      d.h[s] = src.h_l[s];
+      d.kcn[s] = src.k_cn_l[s];
+      d.kpoly[s] = src.k_poly_l[s];
+      d.eta_sh[s] = (1.0 + src.kappa_l[s]) * src.eta;
+      d.q0[s] = src.q0_l[s];
+    }
+    d.gamma3 = src.gamma3; d.en = src.en; d.rcov = src.r_cov; d.zeff = src.z_eff; d.arep = src.alpha_rep;
+    ctx->h_el.push_back(d);
+  }
+  ctx->h_kab.assign((size_t)ctx->ne * ctx->ne, 1.0);
+  for (int a = 0; a < ctx->ne; ++a)
+    for (int b = 0; b < ctx->ne; ++b) ctx->h_kab[a * ctx->ne + b] = p.k_ab[ez[a]][ez[b]];
+  for (int l = 0; l < 3; ++l) ctx->g.k_l[l] = p.k_l[l];
+  ctx->g.k_en = p.k_en; ctx->g.k_g = p.k_g; ctx->g.k_f = p.k_f;
+  ctx->g.cn_k1 = p.cn_k1; ctx->g.cn_k2 = p.cn_k2; ctx->g.cn_cutoff = p.cn_cutoff;
+  ctx->g.kT = 3.166811563e-6 * p.t_el;
+  if (!(ctx->g.kT > 0)) return fail(ctx, FMO_ERR_ARG, "electronic temperature must be positive");
+
+  // atoms grouped by fragment (stable)
+  ctx->n_atoms = n_atoms;
+  ctx->n_frag = n_frag;
+  ctx->perm.resize(n_atoms);
+  for (int i = 0; i < n_atoms; ++i) ctx->perm[i] = i;
+  std::stable_sort(ctx->perm.begin(), ctx->perm.end(),
+                   [&](int a, int b) { return frag_of_atom[a] < frag_of_atom[b]; });
+  ctx->f_atom0.assign(n_frag, 0); ctx->f_nat.assign(n_frag, 0); ctx->f_sh0.assign(n_frag, 0);
+  ctx->f_nsh.assign(n_frag, 0); ctx->f_ao0.assign(n_frag, 0); ctx->f_nao.assign(n_frag, 0);
+  ctx->f_nel.assign(n_frag, 0.0);
+  ctx->h_elem.resize(n_atoms);
+  ctx->h_atom_sh0.resize(n_atoms);
+  ctx->h_sh_atom.clear();
+  ctx->h_sh_inv_eta.clear();
+  int sh = 0, ao = 0;
+  std::vector<double> xyz_int(3 * (size_t)n_atoms);
+  for (int i = 0; i < n_atoms; ++i) {
+    const int src = ctx->perm[i];
+    const int f = frag_of_atom[src];
+    if (i == 0 || frag_of_atom[ctx->perm[i - 1]] != f) { ctx->f_atom0[f] = i; ctx->f_sh0[f] = sh; ctx->f_ao0[f] = ao; }
+    const int e = ctx->z_to_e[Z[src]];
+    ctx->h_elem[i] = e;
+    ctx->h_atom_sh0[i] = sh;
+    const DevElem& d = ctx->h_el[e];
+    for (int s = 0; s < d.nsh; ++s) {
+      ctx->h_sh_atom.push_back(i);
+      ctx->h_sh_inv_eta.push_back(1.0 / d.eta_sh[s]);
+      ctx->f_nel[f] += d.q0[s];
+    }
+    ctx->f_nat[f] += 1;
+    ctx->f_nsh[f] += d.nsh;
+    ctx->f_nao[f] += elem_nao(d);
+    sh += d.nsh;
+    ao += elem_nao(d);
+    for (int c = 0; c < 3; ++c) xyz_int[3 * i + c] = xyz[3 * src + c];
+  }
+  for (int f = 0; f < n_frag; ++f) {
+    if (ctx->f_nat[f] == 0) return fail(ctx, FMO_ERR_ARG, "fragment " + std::to_string(f) + " has no atoms");
+    ctx->f_nel[f] -= frag_charge[f];
+    const double ne = ctx->f_nel[f];
+    if (std::fabs(ne - std::round(ne)) > 1e-9 || (long long)std::llround(ne) % 2 != 0 || ne <= 0)
+      return fail(ctx, FMO_ERR_ARG, "fragment " + std::to_string(f) + " is not closed shell");
+    if (ctx->f_nao[f] > 510) return fail(ctx, FMO_ERR_UNSUPPORTED, "fragment larger than 510 basis functions");
+  }
+  ctx->n_sh = sh;
+  ctx->n_ao = ao;
+  cudaStream_t st = ctx->own_stream;
+  CK(upload(ctx->d_el, ctx->h_el, st));
+  CK(upload(ctx->d_kab, ctx->h_kab, st));
+  CK(upload(ctx->d_xyz, xyz_int, st));
+  CK(upload(ctx->d_perm, ctx->perm, st));
+  CK(ctx->d_xyz_in.ensure(sizeof(double) * 3 * n_atoms));
+  CK(upload(ctx->d_elem, ctx->h_elem, st));
+  CK(ctx->d_cn.ensure(sizeof(double) * n_atoms));
+  CK(upload(ctx->d_atom_sh0, ctx->h_atom_sh0, st));
+  CK(upload(ctx->d_sh_atom, ctx->h_sh_atom, st));
+  CK(upload(ctx->d_sh_inv_eta, ctx->h_sh_inv_eta, st));
+  CK(upload(ctx->d_f_atom0, ctx->f_atom0, st));
+  CK(upload(ctx->d_f_nat, ctx->f_nat, st));
+  CK(upload(ctx->d_f_sh0, ctx->f_sh0, st));
+  CK(upload(ctx->d_f_nsh, ctx->f_nsh, st));
+  CK(upload(ctx->d_f_ao0, ctx->f_ao0, st));
+  CK(upload(ctx->d_f_nao, ctx->f_nao, st));
+  CK(ctx->d_dq_mono.ensure(sizeof(double) * sh));
+  CK(ctx->d_phi.ensure(sizeof(double) * sh));
+  CK(ctx->d_bounds.ensure(sizeof(double) * 4 * n_frag));
+  CK(ctx->d_scalar.ensure(sizeof(double) * 8));
+  CK(ctx->d_t0.ensure(sizeof(unsigned long long)));
+  CK(ctx->d_totals.ensure(sizeof(double) * 4));
+  CK(sync_stream(st));
+  ctx->have_system = true;
+  ctx->have_result = false;
+  ctx->have_guess = false;
+  return FMO_OK;
+}
+
+fmo_status fmo_set_coordinates(fmo_ctx* ctx, const double* xyz) {
+  g_ctx = ctx;
+  if (!ctx || !xyz) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  cudaSetDevice(ctx->device);
+  for (int i = 0; i < 3 * ctx->n_atoms; ++i)
+    if (!std::isfinite(xyz[i])) return fail(ctx, FMO_ERR_ARG, "non-finite coordinate");
+  cudaStream_t st = ctx->own_stream;
+  CK(h2d(ctx->d_xyz_in.p, xyz, sizeof(double) * 3 * ctx->n_atoms, st));
+  CK(launch_gather_xyz(st, ctx->n_atoms, ctx->d_perm.as<int>(), ctx->d_xyz_in.as<double>(), ctx->d_xyz.as<double>()));
+  CK(sync_stream(st));   // a later fmo_run may use another stream
+  ctx->have_result = false;
+  return FMO_OK;
+}
+
+fmo_status fmo_set_coordinates_device(fmo_ctx* ctx, const double* xyz_dev, void* cuda_stream) {
+  g_ctx = ctx;
+  if (!ctx || !xyz_dev) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+  CK(launch_gather_xyz(st, ctx->n_atoms, ctx->d_perm.as<int>(), xyz_dev, ctx->d_xyz.as<double>()));
+  if (!cuda_stream) CK(sync_stream(st));
+  ctx->have_result = false;
+  return FMO_OK;
+}
+
+fmo_status fmo_set_guess(fmo_ctx* ctx, const double* shell_dq) {
+  if (!ctx || !shell_dq) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  ctx->guess.assign(shell_dq, shell_dq + ctx->n_sh);
+  ctx->have_guess = true;
+  return FMO_OK;
+}
+
+fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
+  g_ctx = ctx;
+  if (!ctx || !opt) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  const fmo_options o = *opt;
+  if (o.level < 1 || o.level > 3) return fail(ctx, FMO_ERR_ARG, "level must be 1, 2 or 3");
+  if (o.precision != FMO_PREC_FP64 && o.precision != FMO_PREC_MIXED)
+    return fail(ctx, FMO_ERR_ARG, "unknown precision mode");
+  if (o.max_iter < 1 || o.max_outer < 1 || !(o.scc_tol > 0) || !(o.e_tol > 0) || !(o.outer_tol > 0))
+    return fail(ctx, FMO_ERR_ARG, "iteration limits and tolerances must be positive");
+  if (o.guess == 2 && !ctx->have_guess) return fail(ctx, FMO_ERR_STATE, "guess = 2 needs fmo_set_guess");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+  std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+  ctx->have_result = false;
+  const int nf = ctx->n_frag;
+  ctx->d2h_bytes = 0;
+  cudaEvent_t ev[8];
+  for (auto& e : ev) cudaEventCreate(&e);
+  cudaEventRecord(ev[0], st);
+  CK(launch_stamp(st, ctx->d_t0.as<unsigned long long>()));
+  // ---- coordination numbers of the whole system
+  CK(launch_cn(st, ctx->n_atoms, ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(), ctx->d_el.as<DevElem>(), ctx->g,
+               ctx->d_cn.as<double>()));
+  ctx->stats.kernel_launches += 2;
+  stage(st, "cn");
+  // ---- monomer pass
+  {
+    std::vector<std::array<int, 3>> tu(nf);
+    std::vector<int> nfr(nf, 1);
+    for (int f = 0; f < nf; ++f) tu[f] = {f, -1, -1};
+    CK(plan_pass(ctx, ctx->mono, tu, nfr, true, o.precision, st));
+  }
+  const SmemPlan sp_mono = plan_smem(ctx, ctx->mono, o.precision);
+  if (sp_mono.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->mono))
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "monomer too large");
+  fmo_status fs = setup_pass(ctx, ctx->mono, o.precision, sp_mono, st);
+  if (fs != FMO_OK) return fs;
+  stage(st, "monomer setup");
+  if (o.guess == 2) CK(h2d(ctx->d_dq_mono.p, ctx->guess.data(), sizeof(double) * ctx->n_sh, st));
+  else CK(cudaMemsetAsync(ctx->d_dq_mono.p, 0, sizeof(double) * ctx->n_sh, st));
+  cudaEventRecord(ev[1], st);
+  double change = 1e300;
+  int outer = 0;
+  double h_change_v = 0.0;
+  double* h_change = &h_change_v;
+  for (outer = 1; outer <= o.max_outer; ++outer) {
+    CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
+                  ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>()));
+    stage(st, "phi", outer);
+    fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st);
+    if (fs != FMO_OK) return fs;
+    stage(st, "monomer scc", outer);
+    CK(launch_maxdiff(st, ctx->n_sh, ctx->mono.dq.as<double>(), ctx->d_dq_mono.as<double>(),
+                      ctx->d_scalar.as<double>()));
+    CK(cudaMemcpyAsync(ctx->d_dq_mono.p, ctx->mono.dq.p, sizeof(double) * ctx->n_sh, cudaMemcpyDeviceToDevice, st));
+    CK(d2h(h_change, ctx->d_scalar.p, sizeof(double), st));
+    CK(sync_stream(st));
+    ctx->stats.kernel_launches += 2;
+    ctx->stats.n_monomer_solves += nf;
+    change = *h_change;
+    if (!(change == change)) break;
+    if (change < o.outer_tol) break;
+  }
+  if (outer > o.max_outer) outer = o.max_outer;
+  ctx->stats.outer_iterations = outer;
+  // frozen ESP of the final monomer charges
+  CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
+                ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>()));
+  ctx->stats.kernel_launches += 1;
+  cudaEventRecord(ev[2], st);
+  // ---- n-mer selection
+  const long long npair = (long long)nf * (nf - 1) / 2;
+  std::vector<double> rmin(npair);
+  std::vector<int> pair_scc(std::max<long long>(npair, 1), -1);
+  std::vector<std::array<int, 3>> dim_tu, tri_tu;
+  std::vector<int> dim_nf, tri_nf;
+  std::vector<int2> es_pairs;
+  std::vector<long long> es_idx;
+  if (o.level >= 2 && npair > 0) {
+    CK(ctx->d_rmin.ensure(sizeof(double) * npair));
+    CK(launch_frag_bounds(st, nf, ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_bounds.as<double>()));
+    CK(launch_pair_distance(st, nf, ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_bounds.as<double>(),
+                            std::max(o.dimer_cut, o.trimer_cut), ctx->d_rmin.as<double>()));
+    ctx->stats.kernel_launches += 2;
+    CK(d2h(rmin.data(), ctx->d_rmin.p, sizeof(double) * npair, st));
+    CK(sync_stream(st));
+    long long p = 0;
+    for (int I = 0; I < nf; ++I)
+      for (int J = I + 1; J < nf; ++J, ++p) {
+        if (o.all_dimers_scc || rmin[p] < o.dimer_cut) {
+          pair_scc[p] = int(dim_tu.size());
+          dim_tu.push_back({I, J, -1});
+          dim_nf.push_back(2);
+        } else {
+          es_pairs.push_back(make_int2(I, J));
+          es_idx.push_back(p);
+        }
+      }
+    if (o.level >= 3) {
+      // SCC trimer iff all three pair distances < trimer_cut
+      std::vector<std::vector<int>> nb(nf);
+      p = 0;
+      for (int I = 0; I < nf; ++I)
+        for (int J = I + 1; J < nf; ++J, ++p)
+          if (rmin[p] < o.trimer_cut) nb[I].push_back(J);
+      auto near = [&](int a, int b) { return std::binary_search(nb[a].begin(), nb[a].end(), b); };
+      for (int I = 0; I < nf; ++I)
+        for (size_t x = 0; x < nb[I].size(); ++x)
+          for (size_t y = x + 1; y < nb[I].size(); ++y) {
+            const int J = nb[I][x], K = nb[I][y];
+            if (near(J, K)) { tri_tu.push_back({I, J, K}); tri_nf.push_back(3); }
+          }
+      std::sort(tri_tu.begin(), tri_tu.end());
+    }
+  }
+  cudaEventRecord(ev[3], st);
+  stage(st, "selection", int(dim_tu.size()));
+  ctx->stats.n_dimer_scc = (long long)dim_tu.size();
+  ctx->stats.n_dimer_esdim = (long long)es_pairs.size();
+  ctx->stats.n_trimer_scc = (long long)tri_tu.size();
+  // ---- SCC dimers in the frozen ESP
+  CK(plan_pass(ctx, ctx->dim, dim_tu, dim_nf, false, o.precision, st));
+  const SmemPlan sp_dim = plan_smem(ctx, ctx->dim, o.precision);
+  if (sp_dim.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->dim))
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "dimer too large");
+  if (!dim_tu.empty()) {
+    fs = setup_pass(ctx, ctx->dim, o.precision, sp_dim, st);
+    if (fs != FMO_OK) return fs;
+    stage(st, "dimer setup");
+    fs = run_scc(ctx, ctx->dim, o, sp_dim, true, 1, st);
+    if (fs != FMO_OK) return fs;
+    stage(st, "dimer scc");
+  }
+  // ---- ES-DIM pairs (Eq. 15)
+  CK(ctx->d_dE_pair.ensure(sizeof(double) * std::max<long long>(npair, 1)));
+  CK(upload(ctx->d_pair_scc, pair_scc, st));
+  if (!es_pairs.empty()) {
+    CK(upload(ctx->d_esdim_pairs, es_pairs, st));
+    CK(upload(ctx->d_esdim_idx, es_idx, st));
+    CK(launch_esdim(st, int(es_pairs.size()), ctx->d_esdim_pairs.as<int2>(), ctx->d_esdim_idx.as<long long>(),
+                    ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
+                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_dE_pair.as<double>()));
+    ctx->stats.kernel_launches += 1;
+  }
+  cudaEventRecord(ev[4], st);
+  stage(st, "esdim", int(es_pairs.size()));
+  // ---- SCC trimers
+  CK(plan_pass(ctx, ctx->tri, tri_tu, tri_nf, false, o.precision, st));
+  const SmemPlan sp_tri = plan_smem(ctx, ctx->tri, o.precision);
+  if (sp_tri.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->tri))
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "trimer too large");
+  if (!tri_tu.empty()) {
+    fs = setup_pass(ctx, ctx->tri, o.precision, sp_tri, st);
+    if (fs != FMO_OK) return fs;
+    fs = run_scc(ctx, ctx->tri, o, sp_tri, true, 2, st);
+    if (fs != FMO_OK) return fs;
+  }
+  std::vector<int> tri_flat;
+  for (auto& t : tri_tu) { tri_flat.push_back(t[0]); tri_flat.push_back(t[1]); tri_flat.push_back(t[2]); }
+  CK(upload(ctx->d_tri_frag, tri_flat, st));
+  CK(ctx->d_dE3.ensure(sizeof(double) * std::max<size_t>(tri_tu.size(), 1)));
+  CK(ctx->d_corr.ensure(sizeof(double) * std::max<size_t>(tri_tu.size(), 1)));
+  cudaEventRecord(ev[5], st);
+  // ---- FMO sums
+  CK(launch_fmo_sum(st, nf, ctx->mono.energy.as<double>(), o.level >= 2 ? npair : 0, ctx->d_pair_scc.as<int>(),
+                    ctx->dim.energy.as<double>(), ctx->dim.dEV.as<double>(), ctx->d_dE_pair.as<double>(),
+                    int(tri_tu.size()), ctx->d_tri_frag.as<int>(), ctx->tri.energy.as<double>(),
+                    ctx->tri.dEV.as<double>(), ctx->d_dE3.as<double>(), ctx->d_corr.as<double>(),
+                    ctx->d_totals.as<double>()));
+  ctx->stats.kernel_launches += 1;
+  stage(st, "fmo sum");
+  // ---- results to the host
+  ctx->r_e_mono.resize(nf);
+  ctx->r_dq_mono.resize(ctx->n_sh);
+  ctx->r_mono_iters.resize(nf);
+  ctx->r_mono_status.resize(nf);
+  CK(d2h(ctx->totals, ctx->d_totals.p, sizeof(double) * 3, st));
+  CK(d2h(ctx->r_e_mono.data(), ctx->mono.energy.p, sizeof(double) * nf, st));
+  CK(d2h(ctx->r_dq_mono.data(), ctx->d_dq_mono.p, sizeof(double) * ctx->n_sh, st));
+  CK(d2h(ctx->r_mono_iters.data(), ctx->mono.iters.p, sizeof(int) * nf, st));
+  CK(d2h(ctx->r_mono_status.data(), ctx->mono.status.p, sizeof(int) * nf, st));
+  const size_t ndim = dim_tu.size(), ntri = tri_tu.size();
+  std::vector<double> e_dim(ndim), dev_dim(ndim);
+  std::vector<int> it_dim(ndim), st_dim(ndim), st_tri(ntri), it_tri(ntri);
+  if (o.level >= 2) {
+    ctx->r_dE_pair.resize(npair);
+    if (npair) CK(d2h(ctx->r_dE_pair.data(), ctx->d_dE_pair.p, sizeof(double) * npair, st));
+    if (ndim) {
+      CK(d2h(e_dim.data(), ctx->dim.energy.p, sizeof(double) * ndim, st));
+      CK(d2h(dev_dim.data(), ctx->dim.dEV.p, sizeof(double) * ndim, st));
+      CK(d2h(it_dim.data(), ctx->dim.iters.p, sizeof(int) * ndim, st));
+      CK(d2h(st_dim.data(), ctx->dim.status.p, sizeof(int) * ndim, st));
+    }
+  }
+  ctx->r_dE3.resize(ntri);
+  ctx->r_corr.resize(ntri);
+  if (ntri) {
+    CK(d2h(ctx->r_dE3.data(), ctx->d_dE3.p, sizeof(double) * ntri, st));
+    CK(d2h(ctx->r_corr.data(), ctx->d_corr.p, sizeof(double) * ntri, st));
+    CK(d2h(st_tri.data(), ctx->tri.status.p, sizeof(int) * ntri, st));
+    CK(d2h(it_tri.data(), ctx->tri.iters.p, sizeof(int) * ntri, st));
+  }
+  cudaEventRecord(ev[6], st);
+  CK(sync_stream(st));
+  ctx->stats.ms_setup = now_ms(ev[0], ev[1]);
+  ctx->stats.ms_monomer = now_ms(ev[1], ev[2]);
+  ctx->stats.ms_select = now_ms(ev[2], ev[3]);
+  ctx->stats.ms_dimer = now_ms(ev[3], ev[4]);
+  ctx->stats.ms_trimer = now_ms(ev[4], ev[5]);
+  ctx->stats.ms_reduce = now_ms(ev[5], ev[6]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  // per-pair host arrays in lexicographic order
+  ctx->r_pair_scc.assign(npair, 0);
+  ctx->r_e_dim_pair.assign(npair, std::nan(""));
+  ctx->r_dEV_pair.assign(npair, 0.0);
+  ctx->r_pair_iters.assign(npair, 0);
+  int failed = 0;
+  for (long long p = 0; p < npair && o.level >= 2; ++p) {
+    const int k = pair_scc[p];
+    if (k >= 0) {
+      ctx->r_pair_scc[p] = 1;
+      ctx->r_e_dim_pair[p] = e_dim[k];
+      ctx->r_dEV_pair[p] = dev_dim[k];
+      ctx->r_pair_iters[p] = it_dim[k];
+      if (st_dim[k] != FMO_SCC_CONVERGED) ++failed;
+    }
+  }
+  for (int f = 0; f < nf; ++f) if (ctx->r_mono_status[f] != FMO_SCC_CONVERGED) ++failed;
+  for (size_t t = 0; t < ntri; ++t) if (st_tri[t] != FMO_SCC_CONVERGED) ++failed;
+  ctx->r_tri = tri_flat;
+  long long iters = 0;
+  for (int p = 0; p < 3; ++p) iters += ctx->stats.iters_fp32[p] + ctx->stats.iters_fp64[p];
+  ctx->stats.scc_iterations = iters;
+  ctx->stats.n_failed = failed;
+  ctx->stats.h2d_bytes = ctx->h2d_bytes;
+  ctx->stats.d2h_bytes = ctx->d2h_bytes;
+  ctx->h2d_bytes = 0;
+  ctx->last_level = o.level;
+  if (o.level < 2) ctx->totals[1] = std::nan("");
+  if (o.level < 3) ctx->totals[2] = std::nan("");
+  ctx->have_result = true;
+  bool timeout = false;
+  for (int s : ctx->r_mono_status) timeout |= (s == FMO_SCC_TIMEOUT);
+  for (int s : st_dim) timeout |= (s == FMO_SCC_TIMEOUT);
+  for (int s : st_tri) timeout |= (s == FMO_SCC_TIMEOUT);
+  if (timeout) return fail(ctx, FMO_ERR_TIMEOUT, "deadline reached");
+  for (double v : ctx->totals) if (std::isinf(v)) return fail(ctx, FMO_ERR_NAN, "non-finite total");
+  if (o.level >= 2 && !std::isfinite(ctx->totals[1])) return fail(ctx, FMO_ERR_NAN, "non-finite FMO2 energy");
+  if (failed > 0 || change >= o.outer_tol)
+    return fail(ctx, FMO_ERR_NOT_CONVERGED, std::to_string(failed) + " n-mer solves did not converge");
+  ctx->err.clear();
+  return FMO_OK;
+}
+
+fmo_status fmo_get_energy(fmo_ctx* ctx, double* e1, double* e2, double* e3) {
+  if (!ctx) return FMO_ERR_ARG;
+  if (!ctx->have_result) return fail(ctx, FMO_ERR_STATE, "no results: call fmo_run");
+  if (e1) *e1 = ctx->totals[0];
+  if (e2) *e2 = ctx->totals[1];
+  if (e3) *e3 = ctx->totals[2];
+  return FMO_OK;
+}
+
+fmo_status fmo_get_sizes(fmo_ctx* ctx, int32_t* n_shell, int32_t* n_ao) {
+  if (!ctx) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  if (n_shell) *n_shell = ctx->n_sh;
+  if (n_ao) *n_ao = ctx->n_ao;
+  return FMO_OK;
+}
+
+fmo_status fmo_get_monomers(fmo_ctx* ctx, double* E_I, double* shell_dq, int32_t* iters, int32_t* status) {
+  if (!ctx) return FMO_ERR_ARG;
+  if (!ctx->have_result) return fail(ctx, FMO_ERR_STATE, "no results: call fmo_run");
+  if (E_I) std::memcpy(E_I, ctx->r_e_mono.data(), sizeof(double) * ctx->n_frag);
+  if (shell_dq) std::memcpy(shell_dq, ctx->r_dq_mono.data(), sizeof(double) * ctx->n_sh);
+  if (iters) std::memcpy(iters, ctx->r_mono_iters.data(), sizeof(int) * ctx->n_frag);
+  if (status) std::memcpy(status, ctx->r_mono_status.data(), sizeof(int) * ctx->n_frag);
+  return FMO_OK;
+}
+
+fmo_status fmo_get_dimers(fmo_ctx* ctx, int64_t* n, int32_t* ij, double* dE, double* e_dimer, double* dEV,
+                          uint8_t* scc, int32_t* iters) {
+  if (!ctx || !n) return FMO_ERR_ARG;
+  if (!ctx->have_result) return fail(ctx, FMO_ERR_STATE, "no results: call fmo_run");
+  const long long np = ctx->last_level >= 2 ? (long long)ctx->n_frag * (ctx->n_frag - 1) / 2 : 0;
+  *n = np;
+  long long p = 0;
+  if (ij)
+    for (int I = 0; I < ctx->n_frag; ++I)
+      for (int J = I + 1; J < ctx->n_frag && p < np; ++J, ++p) { ij[2 * p] = I; ij[2 * p + 1] = J; }
+  if (np == 0) return FMO_OK;
+  if (dE) std::memcpy(dE, ctx->r_dE_pair.data(), sizeof(double) * np);
+  if (e_dimer) std::memcpy(e_dimer, ctx->r_e_dim_pair.data(), sizeof(double) * np);
+  if (dEV) std::memcpy(dEV, ctx->r_dEV_pair.data(), sizeof(double) * np);
+  if (scc) std::memcpy(scc, ctx->r_pair_scc.data(), np);
+  if (iters) std::memcpy(iters, ctx->r_pair_iters.data(), sizeof(int) * np);
+  return FMO_OK;
+}
+
+fmo_status fmo_get_trimers(fmo_ctx* ctx, int64_t* n, int32_t* ijk, double* dE3, double* corr) {
+  if (!ctx || !n) return FMO_ERR_ARG;
+  if (!ctx->have_result) return fail(ctx, FMO_ERR_STATE, "no results: call fmo_run");
+  const long long nt = (long long)ctx->r_dE3.size();
+  *n = nt;
+  if (ijk && nt) std::memcpy(ijk, ctx->r_tri.data(), sizeof(int) * 3 * nt);
+  if (dE3 && nt) std::memcpy(dE3, ctx->r_dE3.data(), sizeof(double) * nt);
+  if (corr && nt) std::memcpy(corr, ctx->r_corr.data(), sizeof(double) * nt);
+  return FMO_OK;
+}
+
+fmo_status fmo_get_stats(fmo_ctx* ctx, fmo_stats* st) {
+  if (!ctx || !st) return FMO_ERR_ARG;
+  *st = ctx->stats;
+  return FMO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,310 @@
+// Device-side data layouts and block-level building blocks of the batched
+// FMO-xTB SCC path (sm_103a).  Included by every .cu file of the library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fmo {
+
+constexpr int kMaxShell = 3;
+constexpr int kMaxPrim = 12;
+constexpr int kMaxElem = 16;      // distinct elements in one system
+constexpr int kHist = 8;          // Broyden history length
+constexpr int kBlock = 256;       // threads of the SCC kernels
+
+// One element of the table, compacted to the elements present.  cn[][] holds
+// the contraction coefficient times the primitive normalisation.
+struct DevElem {
+  int nsh;
+  int l[kMaxShell];
+  int nprim[kMaxShell];
+  int pad_;
+  double alpha[kMaxShell][kMaxPrim];
+  double cn[kMaxShell][kMaxPrim];
+  double h[kMaxShell];       // H_A^l
+  double kcn[kMaxShell];     // k_CN,l
+  double kpoly[kMaxShell];   // k^poly_l
+  double eta_sh[kMaxShell];  // (1 + kappa_A^l) eta_A
+  double q0[kMaxShell];
+  double gamma3, en, rcov, zeff, arep;
+};
+
+struct GParams {
+  double k_l[3];
+  double k_en, k_g, k_f;
+  double cn_k1, cn_k2, cn_cutoff;
+  double kT;                 // k_B * T_el (Eh)
+};
+
+// Fragment table (atoms are stored fragment by fragment).
+struct FragTab {
+  const int* atom0;   // first atom
+  const int* nat;
+  const int* sh0;     // first global shell
+  const int* nsh;
+  const int* ao0;     // first global AO
+  const int* nao;
+};
+
+// One n-mer (monomer, dimer or trimer) of a pass.
+struct Nmer {
+  int nfrag;
+  int frag[3];
+  int n, nsh, nat;     // AOs, shells, atoms
+  int npad;            // n rounded up to even
+  double nel;          // electrons
+  long long mat;       // offset of its n x n matrices (elements) in the pools
+  long long shv;       // offset of its shell vectors
+  long long gam;       // offset of its nsh x nsh gamma block
+  long long aov;       // offset of its AO vectors
+  long long hist;      // offset of its Broyden history
+  long long apad;      // offset of its npad x npad scratch (eigen-solve matrix)
+};
+
+// Local -> global index maps of an n-mer, held in shared memory.
+struct NmerMaps {
+  int16_t* ao_sh;      // [n]   local shell of each AO
+  int16_t* sh_at;      // [nsh] local atom of each shell
+  int* at_glob;        // [nat] global atom of each local atom
+  int* sh_glob;        // [nsh] global shell of each local shell
+  int16_t* sh_ao0;     // [nsh+1] first local AO of each shell
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Block-level reductions (fixed order: deterministic).
+//
+// Every thread must see the bit-identical result: convergence tests branch on
+// these values, and threads that disagree in the last bit would leave a loop
+// at different iterations and deadlock at the next barrier.  A sum is
+// therefore reduced onto lane 0 and broadcast from there (an XOR butterfly
+// leaves each lane with a differently rounded total).  Max is exact, so its
+// butterfly gives identical values everywhere.
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum over the block; every thread gets the result.  red: >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (lane < nw) ? red[lane] : 0.0;
+  t = warp_sum(t);
+  return t;
+}
+__device__ __forceinline__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (lane < nw) ? red[lane] : -1e300;
+  t = warp_max(t);
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Block-level GEMM: C[m][n] = sum_k a(m,k) * b(n,k) with
+//   a(m,k) = A[m*sam + kk*sak] * (kscale ? kscale[k] : 1),
+//   b(n,k) = B[n*sbn + kk*sbk],   kk = kidx ? kidx[k] : k.
+// 64x64 output tiles, BK = 16, 256 threads with 4x4 outputs each.  Operand
+// tiles are staged in shared memory (smem: 2*16*64 elements of T).
+
+template <typename T>
+__device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long long sam,
+                           long long sak, const T* __restrict__ B, long long sbn, long long sbk,
+                           T* __restrict__ C, long long ldc, const int* __restrict__ kidx,
+                           const double* __restrict__ kscale, T* smem) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  T* As = smem;             // [BK][BM]
+  T* Bs = smem + BK * BM;   // [BK][BN]
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const bool a_k_contig = (sak == 1);
+  const bool b_k_contig = (sbk == 1);
+  for (int m0 = 0; m0 < M; m0 += BM) {
+    for (int n0 = 0; n0 < N; n0 += BN) {
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int r = 0; r < (BM * BK) / kBlock; ++r) {
+          const int e = tid + r * kBlock;
+          int kk, mm;
+          if (a_k_contig) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+          const int gm = m0 + mm, gk = k0 + kk;
+          T v = T(0);
+          if (gm < M && gk < K) {
+            const long long kr = kidx ? kidx[gk] : gk;
+            v = A[gm * sam + kr * sak];
+            if (kscale) v = T(double(v) * kscale[gk]);
+          }
+          As[kk * BM + mm] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < (BN * BK) / kBlock; ++r) {
+          const int e = tid + r * kBlock;
+          int kk, nn;
+          if (b_k_contig) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+          const int gn = n0 + nn, gk = k0 + kk;
+          T v = T(0);
+          if (gn < N && gk < K) {
+            const long long kr = kidx ? kidx[gk] : gk;
+            v = B[gn * sbn + kr * sbk];
+          }
+          Bs[kk * BN + nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+          T a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[kk * BM + ty * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = Bs[kk * BN + tx * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty * 4 + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gn = n0 + tx * 4 + j;
+          if (gn < N) C[gm * ldc + gn] = acc[i][j];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Block-level cyclic Jacobi eigensolver for a symmetric n x n matrix A
+// (row-major, leading dimension lda >= npad, padding row/column zero).
+// Parallel (round-robin) ordering: each round rotates npad/2 disjoint index
+// pairs, applied as independent 2x2 block updates A <- J^T A J.  Pairs with
+// |A_pq| <= thr are skipped; the solve ends after a sweep with no rotation.
+// The rows of CT (ncol entries each, leading dimension ldc) are rotated along
+// (CT <- J^T CT), so rows of CT become the eigenvectors in the basis CT
+// started from.  Rotation angle: Golub & Van Loan, symmetric Schur 2x2.
+// Returns the number of sweeps, or -1 if max_sweeps was reached.
+
+template <typename T>
+struct JacobiScratch {
+  int* p;
+  int* q;
+  T* c;
+  T* s;
+  int* act;
+};
+
+template <typename T>
+__device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol, double tol,
+                            int max_sweeps, JacobiScratch<T> js, double* red) {
+  const int npad = n + (n & 1);
+  const int half = npad / 2;
+  const int tid = threadIdx.x;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double dmax = 0.0;
+    for (int i = tid; i < n; i += blockDim.x) dmax = fmax(dmax, fabs(double(A[i * lda + i])));
+    dmax = block_max(dmax, red);
+    const double thr = tol * fmax(dmax, 1e-30);
+    int rotations = 0;
+    for (int r = 0; r < npad - 1; ++r) {
+      int active = 0;
+      for (int k = tid; k < half; k += blockDim.x) {
+        const int m = npad - 1;
+        int p, q;
+        if (k == 0) { p = 0; q = ((0 + r) % m) + 1; }
+        else { p = ((k + r) % m) + 1; q = ((m - k + r) % m) + 1; }
+        if (p > q) { int t = p; p = q; q = t; }
+        T c = T(1), s = T(0);
+        int a = 0;
+        if (q < n) {
+          const T apq = A[p * lda + q];
+          if (fabs(double(apq)) > thr) {
+            const T app = A[p * lda + p], aqq = A[q * lda + q];
+            const T tau = (aqq - app) / (T(2) * apq);
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
+            s = t * c;
+            a = 1;
+          }
+        }
+        js.p[k] = p; js.q[k] = q; js.c[k] = c; js.s[k] = s; js.act[k] = a;
+        active |= a;
+      }
+      if (!__syncthreads_or(active)) continue;
+      ++rotations;
+      // 2x2 block updates
+      const int nblk = half * half;
+      for (int e = tid; e < nblk; e += blockDim.x) {
+        const int k = e / half, k2 = e % half;
+        if (k2 < k) continue;                      // symmetric: upper blocks only
+        if (!js.act[k] && !js.act[k2]) continue;
+        const int p = js.p[k], q = js.q[k], p2 = js.p[k2], q2 = js.q[k2];
+        const T c = js.c[k], s = js.s[k], c2 = js.c[k2], s2 = js.s[k2];
+        const T b00 = A[p * lda + p2], b01 = A[p * lda + q2];
+        const T b10 = A[q * lda + p2], b11 = A[q * lda + q2];
+        const T t00 = b00 * c2 - b01 * s2, t01 = b00 * s2 + b01 * c2;
+        const T t10 = b10 * c2 - b11 * s2, t11 = b10 * s2 + b11 * c2;
+        const T x00 = c * t00 - s * t10, x01 = c * t01 - s * t11;
+        const T x10 = s * t00 + c * t10, x11 = s * t01 + c * t11;
+        if (k == k2) {
+          A[p * lda + p] = x00;
+          A[q * lda + q] = x11;
+          A[p * lda + q] = T(0);
+          A[q * lda + p] = T(0);
+        } else {
+          A[p * lda + p2] = x00; A[p * lda + q2] = x01;
+          A[q * lda + p2] = x10; A[q * lda + q2] = x11;
+          A[p2 * lda + p] = x00; A[q2 * lda + p] = x01;
+          A[p2 * lda + q] = x10; A[q2 * lda + q] = x11;
+        }
+      }
+      // rotate the rows p, q of CT
+      const long long work = (long long)half * ncol;
+      for (long long e = tid; e < work; e += blockDim.x) {
+        const int k = int(e / ncol), j = int(e % ncol);
+        if (!js.act[k]) continue;
+        const int p = js.p[k], q = js.q[k];
+        const T c = js.c[k], s = js.s[k];
+        const T vp = CT[p * ldc + j], vq = CT[q * ldc + j];
+        CT[p * ldc + j] = c * vp - s * vq;
+        CT[q * ldc + j] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    if (rotations == 0) return sweep;
+  }
+  return -1;
+}
+
+}  // namespace fmo

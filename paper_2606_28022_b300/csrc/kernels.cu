@@ -1,0 +1,1176 @@
+// CUDA kernels of the batched FMO-xTB SCC path (sm_103a).
+//
+// Paper references (Einsele & Mitric, FMO-xTB):
+//   Eq. 2        electronic energy        Eq. 3      Mulliken shell charges
+//   Eqs. 4-5     gamma kernel, eta        Eq. 6      Fermi occupations
+//   Eq. 7        Fock matrix              Eqs. 8-10  H0, Pi, CN-dependent levels
+//   Eq. 11       repulsion                CN definition in the gradient section
+//   Eqs. 12-15   FMO2, dE^V, ddq, ES-DIM  Eqs. 16-19 FMO3
+//   Eqs. 20-21   embedding Fock matrix V^I from the other fragments' charges
+#include <cstdio>
+
+#include "fmo_device.cuh"
+#include "kernels.h"
+
+namespace fmo {
+
+// ---------------------------------------------------------------------------
+// Coordination numbers of the whole system (CN definition; pairs beyond the
+// cutoff are not counted).
+
+__global__ void cn_kernel(int n_atoms, const double* __restrict__ xyz, const int* __restrict__ elem,
+                          const DevElem* __restrict__ el, GParams g, double* __restrict__ cn) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_atoms) return;
+  const double xa = xyz[3 * a], ya = xyz[3 * a + 1], za = xyz[3 * a + 2];
+  const double ra = el[elem[a]].rcov;
+  double s = 0.0;
+  for (int b = 0; b < n_atoms; ++b) {
+    if (b == a) continue;
+    const double dx = xyz[3 * b] - xa, dy = xyz[3 * b + 1] - ya, dz = xyz[3 * b + 2] - za;
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (r >= g.cn_cutoff) continue;
+    const double arg = -g.cn_k1 * (g.cn_k2 * (ra + el[elem[b]].rcov) / r - 1.0);
+    s += 1.0 / (1.0 + exp(arg));
+  }
+  cn[a] = s;
+}
+
+// ---------------------------------------------------------------------------
+// n-mer index maps (built by thread 0 of a block into shared memory).
+
+struct MapCounts {
+  int nat, nsh, n;
+};
+
+__device__ void build_maps(const Nmer& nm, const FragTab ft, const int* __restrict__ elem,
+                           const int* __restrict__ atom_sh0, const DevElem* __restrict__ el,
+                           NmerMaps mp) {
+  if (threadIdx.x == 0) {
+    int la = 0, ls = 0, lao = 0;
+    for (int k = 0; k < nm.nfrag; ++k) {
+      const int f = nm.frag[k];
+      const int a0 = ft.atom0[f], na = ft.nat[f];
+      for (int i = 0; i < na; ++i) {
+        const int ga = a0 + i;
+        mp.at_glob[la] = ga;
+        const DevElem& e = el[elem[ga]];
+        for (int s = 0; s < e.nsh; ++s) {
+          mp.sh_at[ls] = (int16_t)la;
+          mp.sh_glob[ls] = atom_sh0[ga] + s;
+          mp.sh_ao0[ls] = (int16_t)lao;
+          for (int m = 0; m < 2 * e.l[s] + 1; ++m) mp.ao_sh[lao++] = (int16_t)ls;
+          ++ls;
+        }
+        ++la;
+      }
+    }
+    mp.sh_ao0[ls] = (int16_t)lao;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Overlap and H0 of an n-mer (Eqs. 8-10), one thread per atom pair A <= B.
+// Contracted s/p Gaussians: two primitives combine into one of exponent
+// p = a + b at P = (aA + bB)/p; s-s overlap (pi/p)^{3/2} exp(-ab/p R^2); a p
+// factor contributes (P - A)_i, a pair of p factors (P-A)_i (P-B)_j + d_ij/2p.
+
+__global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
+                                 const double* __restrict__ xyz, const int* __restrict__ elem,
+                                 const int* __restrict__ atom_sh0, const double* __restrict__ cn,
+                                 const DevElem* __restrict__ el, const double* __restrict__ kab,
+                                 int ne, GParams g, double* __restrict__ S,
+                                 double* __restrict__ H0) {
+  const Nmer nm = nmers[blockIdx.y];
+  __shared__ int s_glob[512];
+  __shared__ int s_ao0[512];
+  if (threadIdx.x == 0) {
+    int la = 0, lao = 0;
+    for (int k = 0; k < nm.nfrag; ++k) {
+      const int f = nm.frag[k];
+      for (int i = 0; i < ft.nat[f]; ++i) {
+        const int ga = ft.atom0[f] + i;
+        s_glob[la] = ga;
+        s_ao0[la] = lao;
+        const DevElem& e = el[elem[ga]];
+        for (int s = 0; s < e.nsh; ++s) lao += 2 * e.l[s] + 1;
+        ++la;
+      }
+    }
+  }
+  __syncthreads();
+  const long long npairs = (long long)nm.nat * (nm.nat + 1) / 2;
+  const int n = nm.n;
+  double* Sm = S + nm.mat;
+  double* Hm = H0 + nm.mat;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < npairs;
+       e += (long long)gridDim.x * blockDim.x) {
+    // triangular index -> (i, j), j <= i
+    long long i = (long long)((sqrt(8.0 * double(e) + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > e) --i;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    const int ai = int(i), bj = int(e - i * (i + 1) / 2);
+    const int ga = s_glob[ai], gb = s_glob[bj];
+    const DevElem& EA = el[elem[ga]];
+    const DevElem& EB = el[elem[gb]];
+    const double Ax = xyz[3 * ga], Ay = xyz[3 * ga + 1], Az = xyz[3 * ga + 2];
+    const double dx = xyz[3 * gb] - Ax, dy = xyz[3 * gb + 1] - Ay, dz = xyz[3 * gb + 2] - Az;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double R = sqrt(r2);
+    const bool same = (ai == bj);
+    // pair prefactors of Eq. 8
+    const double den = EA.en - EB.en;
+    const double fen = 1.0 + g.k_en * den * den;
+    const double kAB = kab[elem[ga] * ne + elem[gb]];
+    const double rcov = EA.rcov + EB.rcov;
+    const double ratio = same ? 0.0 : sqrt(R / rcov);
+    int aoA = s_ao0[ai];
+    for (int sa = 0; sa < EA.nsh; ++sa) {
+      const int la = EA.l[sa];
+      const double hA = EA.h[sa] * (1.0 + EA.kcn[sa] * cn[ga]);
+      int aoB = s_ao0[bj];
+      for (int sb = 0; sb < EB.nsh; ++sb) {
+        const int lb = EB.l[sb];
+        double blk[3][3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int v = 0; v < 3; ++v) blk[u][v] = 0.0;
+        for (int pa = 0; pa < EA.nprim[sa]; ++pa) {
+          const double a = EA.alpha[sa][pa], ca = EA.cn[sa][pa];
+          for (int pb = 0; pb < EB.nprim[sb]; ++pb) {
+            const double b = EB.alpha[sb][pb], cb = EB.cn[sb][pb];
+            const double p = a + b, ip = 1.0 / p;
+            const double s00 = ca * cb * pow(M_PI * ip, 1.5) * exp(-a * b * ip * r2);
+            const double PA[3] = {b * ip * dx, b * ip * dy, b * ip * dz};
+            const double PB[3] = {-a * ip * dx, -a * ip * dy, -a * ip * dz};
+            if (la == 0 && lb == 0) {
+              blk[0][0] += s00;
+            } else if (la == 1 && lb == 0) {
+#pragma unroll
+              for (int u = 0; u < 3; ++u) blk[u][0] += PA[u] * s00;
+            } else if (la == 0 && lb == 1) {
+#pragma unroll
+              for (int v = 0; v < 3; ++v) blk[0][v] += PB[v] * s00;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 3; ++u)
+#pragma unroll
+                for (int v = 0; v < 3; ++v)
+                  blk[u][v] += (PA[u] * PB[v] + (u == v ? 0.5 * ip : 0.0)) * s00;
+            }
+          }
+        }
+        const int nu = 2 * la + 1, nv = 2 * lb + 1;
+        double fac = 0.0;
+        const double hB = EB.h[sb] * (1.0 + EB.kcn[sb] * cn[gb]);
+        if (!same) {
+          const double pi = (1.0 + EA.kpoly[sa] * ratio) * (1.0 + EB.kpoly[sb] * ratio);  // Eq. 9
+          fac = kAB * 0.5 * (g.k_l[la] + g.k_l[lb]) * 0.5 * (hA + hB) * fen * pi;          // Eq. 8
+        }
+        for (int u = 0; u < nu; ++u) {
+          for (int v = 0; v < nv; ++v) {
+            const int mu = aoA + u, nu2 = aoB + v;
+            const double sv = blk[u][v];
+            double hv = fac * sv;
+            if (same) hv = (mu == nu2) ? hA : 0.0;   // on-site: levels of Eq. 10
+            Sm[(long long)mu * n + nu2] = sv;
+            Sm[(long long)nu2 * n + mu] = sv;
+            Hm[(long long)mu * n + nu2] = hv;
+            Hm[(long long)nu2 * n + mu] = hv;
+          }
+        }
+        aoB += nv;
+      }
+      aoA += 2 * la + 1;
+    }
+  }
+}
+
+// gamma of Eqs. 4-5 from the distance and the two shell hardnesses.
+__device__ __forceinline__ double gamma_fn(double r2, double inv_eta_a, double inv_eta_b, double kg) {
+  const double ie = 0.5 * (inv_eta_a + inv_eta_b);   // 1/eta, eta = harmonic mean
+  if (kg == 2.0) return 1.0 / sqrt(r2 + ie * ie);
+  return pow(pow(sqrt(r2), kg) + pow(ie, kg), -1.0 / kg);
+}
+
+// Shell-resolved gamma block of an n-mer.
+__global__ void gamma_kernel(const Nmer* __restrict__ nmers, FragTab ft, const double* __restrict__ xyz,
+                             const int* __restrict__ elem, const int* __restrict__ sh_atom,
+                             const double* __restrict__ sh_inv_eta, GParams g,
+                             double* __restrict__ gam) {
+  const Nmer nm = nmers[blockIdx.y];
+  __shared__ int s_sh[1024];
+  if (threadIdx.x == 0) {
+    int ls = 0;
+    for (int k = 0; k < nm.nfrag; ++k) {
+      const int f = nm.frag[k];
+      for (int i = 0; i < ft.nsh[f]; ++i) s_sh[ls++] = ft.sh0[f] + i;
+    }
+  }
+  __syncthreads();
+  const long long tot = (long long)nm.nsh * nm.nsh;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = int(e / nm.nsh), j = int(e % nm.nsh);
+    const int gi = s_sh[i], gj = s_sh[j];
+    const int a = sh_atom[gi], b = sh_atom[gj];
+    const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
+                 dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+    gam[nm.gam + e] = gamma_fn(dx * dx + dy * dy + dz * dz, sh_inv_eta[gi], sh_inv_eta[gj], g.k_g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Loewdin orthogonaliser X = S^{-1/2} of each n-mer (Jacobi eigensolve of S),
+// written as the starting eigenvector rows CT = X (X is symmetric).
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) lowdin_kernel(const Nmer* __restrict__ nmers,
+                                                        const double* __restrict__ S, T* __restrict__ CT,
+                                                        T* __restrict__ W, T* __restrict__ Ag,
+                                                        int a_in_smem, double tol, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Nmer nm = nmers[blockIdx.x];
+  const int n = nm.n, npad = nm.npad;
+  unsigned char* sp = smem_raw;
+  T* A;
+  if (a_in_smem) { A = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)npad * npad; }
+  else A = Ag + nm.apad;  // global scratch, npad*npad per n-mer
+  T* gemm = reinterpret_cast<T*>(sp); sp += sizeof(T) * 2 * 16 * 64;
+  double* red = reinterpret_cast<double*>(sp); sp += sizeof(double) * 32;
+  double* scale = reinterpret_cast<double*>(sp); sp += sizeof(double) * npad;
+  JacobiScratch<T> js;
+  js.p = reinterpret_cast<int*>(sp); sp += sizeof(int) * npad;
+  js.q = reinterpret_cast<int*>(sp); sp += sizeof(int) * npad;
+  js.act = reinterpret_cast<int*>(sp); sp += sizeof(int) * npad;
+  sp = (unsigned char*)(((uintptr_t)sp + 15) & ~uintptr_t(15));
+  js.c = reinterpret_cast<T*>(sp); sp += sizeof(T) * npad;
+  js.s = reinterpret_cast<T*>(sp); sp += sizeof(T) * npad;
+
+  const double* Sm = S + nm.mat;
+  T* CTm = CT + nm.mat;
+  T* Wm = W + nm.mat;
+  for (int e = threadIdx.x; e < npad * npad; e += blockDim.x) {
+    const int i = e / npad, j = e % npad;
+    A[e] = (i < n && j < n) ? T(Sm[(long long)i * n + j]) : T(0);
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) CTm[e] = T((e / n) == (e % n) ? 1.0 : 0.0);
+  __syncthreads();
+  const int sw = block_jacobi<T>(A, npad, n, CTm, n, n, tol, 60, js, red);
+  if (sw < 0 && threadIdx.x == 0) status[blockIdx.x] = FMO_SCC_JACOBI_CODE;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) scale[i] = 1.0 / sqrt(double(A[i * npad + i]));
+  __syncthreads();
+  // X = V diag(s^-1/2) V^T with V^T = CT rows
+  block_gemm<T>(n, n, n, CTm, 1, n, CTm, 1, n, Wm, n, nullptr, scale, gemm);
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) CTm[e] = Wm[e];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched SCC kernel: one block per n-mer iterates the SCC loop of
+// Eqs. 2-7 to self-consistency in its embedding potential (Eqs. 20-21).
+
+struct SccArgs {
+  const Nmer* nmers;
+  const int* order;
+  FragTab ft;
+  const double* xyz;
+  const int* elem;
+  const int* atom_sh0;
+  const DevElem* el;
+  GParams g;
+  const double* S;
+  const double* H0;
+  const double* gam;
+  double* CTd;
+  double* W1d;
+  double* W2d;
+  double* Agd;
+  float* CTf;
+  float* W1f;
+  float* W2f;
+  float* Agf;
+  const double* phi;       // supersystem potential sum_lambda gamma dq_mono (or null)
+  const double* dq_mono;   // monomer charges, global shell order
+  double* esp;             // out: the n-mer's embedding potential
+  double* dq;              // in: guess (if !guess_from_mono), out: charges
+  double* eps;             // out: orbital energies
+  double* hist;            // Broyden history scratch
+  double* energy;          // out per n-mer (index = n-mer index)
+  double* e_el;
+  double* e_rep;
+  double* dEV;
+  int* iters;
+  int* iters32;
+  int* status;
+  int guess_from_mono;
+  int precision;
+  int max_iter;
+  int fp32_cap;
+  double tol, etol, switch_tol;
+  double jacobi_tol_d, jacobi_tol_f;
+  const unsigned long long* t0;
+  unsigned long long budget_ns;
+  int a_smem_d, a_smem_f;
+  int max_n, max_nsh, max_nat;
+};
+
+// Shared-memory layout of the SCC kernel (sizes from the launch maxima).
+struct SccSmem {
+  void* A;
+  void* gemm;
+  double* red;
+  double* sig;
+  double* dqin;
+  double* dqout;
+  double* esp;
+  double* q0;
+  double* dqat;
+  double* g3;
+  double* eps;
+  double* focc;
+  int* occ;
+  double* bro;   // Broyden small matrix (kHist*kHist + 2*kHist)
+  NmerMaps mp;
+  int* jsp;
+  int* jsq;
+  int* jsact;
+  void* jsc;
+  void* jss;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t scc_smem_bytes(int max_n, int max_nsh, int max_nat, int a_bytes) {
+  const int npad = max_n + (max_n & 1);
+  size_t b = 0;
+  b += align16((size_t)a_bytes);
+  b += align16(sizeof(double) * 2 * 16 * 64);
+  b += align16(sizeof(double) * 32);
+  b += 7 * align16(sizeof(double) * max_nsh);          // sig dqin dqout esp q0 + spare
+  b += 2 * align16(sizeof(double) * max_nat);          // dqat g3
+  b += 2 * align16(sizeof(double) * npad);             // eps focc
+  b += align16(sizeof(int) * npad);                    // occ
+  b += align16(sizeof(double) * (kHist * kHist + 4 * kHist + 8));
+  b += align16(sizeof(int16_t) * npad);                // ao_sh
+  b += align16(sizeof(int16_t) * max_nsh);             // sh_at
+  b += align16(sizeof(int) * max_nat);                 // at_glob
+  b += align16(sizeof(int) * max_nsh);                 // sh_glob
+  b += align16(sizeof(int16_t) * (max_nsh + 1));       // sh_ao0
+  b += 3 * align16(sizeof(int) * npad);                // js p q act
+  b += 2 * align16(sizeof(double) * npad);             // js c s
+  return b;
+}
+
+__device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, int max_nat, int a_bytes) {
+  const int npad = max_n + (max_n & 1);
+  SccSmem s;
+  unsigned char* p = base;
+  auto take = [&](size_t bytes) { unsigned char* r = p; p += align16(bytes); return (void*)r; };
+  s.A = take(a_bytes);
+  s.gemm = take(sizeof(double) * 2 * 16 * 64);
+  s.red = (double*)take(sizeof(double) * 32);
+  s.sig = (double*)take(sizeof(double) * max_nsh);
+  s.dqin = (double*)take(sizeof(double) * max_nsh);
+  s.dqout = (double*)take(sizeof(double) * max_nsh);
+  s.esp = (double*)take(sizeof(double) * max_nsh);
+  s.q0 = (double*)take(sizeof(double) * max_nsh);
+  take(sizeof(double) * max_nsh);
+  take(sizeof(double) * max_nsh);
+  s.dqat = (double*)take(sizeof(double) * max_nat);
+  s.g3 = (double*)take(sizeof(double) * max_nat);
+  s.eps = (double*)take(sizeof(double) * npad);
+  s.focc = (double*)take(sizeof(double) * npad);
+  s.occ = (int*)take(sizeof(int) * npad);
+  s.bro = (double*)take(sizeof(double) * (kHist * kHist + 4 * kHist + 8));
+  s.mp.ao_sh = (int16_t*)take(sizeof(int16_t) * npad);
+  s.mp.sh_at = (int16_t*)take(sizeof(int16_t) * max_nsh);
+  s.mp.at_glob = (int*)take(sizeof(int) * max_nat);
+  s.mp.sh_glob = (int*)take(sizeof(int) * max_nsh);
+  s.mp.sh_ao0 = (int16_t*)take(sizeof(int16_t) * (max_nsh + 1));
+  s.jsp = (int*)take(sizeof(int) * npad);
+  s.jsq = (int*)take(sizeof(int) * npad);
+  s.jsact = (int*)take(sizeof(int) * npad);
+  s.jsc = take(sizeof(double) * npad);
+  s.jss = take(sizeof(double) * npad);
+  return s;
+}
+
+// Fermi level by bisection (warp 0), occupations, -T S_el, occupied list.
+__device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_occ_out) {
+  __shared__ double s_mts;
+  __shared__ int s_nocc;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double lo = 1e300, hi = -1e300;
+    for (int i = lane; i < n; i += 32) { lo = fmin(lo, sm.eps[i]); hi = fmax(hi, sm.eps[i]); }
+    lo = -warp_max(-lo);
+    hi = warp_max(hi);
+    lo -= 50.0 * kT + 1.0;
+    hi += 50.0 * kT + 1.0;
+    double ef = 0.5 * (lo + hi);
+    for (int it = 0; it < 400; ++it) {
+      ef = 0.5 * (lo + hi);
+      double tot = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        const double x = fmin(fmax((sm.eps[i] - ef) / kT, -700.0), 700.0);
+        tot += 2.0 / (exp(x) + 1.0);
+      }
+      tot = warp_sum(tot);
+      if (fabs(tot - nel) < 1e-13 || hi - lo < 1e-15) break;
+      if (tot > nel) hi = ef; else lo = ef;
+    }
+    double mts = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double x = fmin(fmax((sm.eps[i] - ef) / kT, -700.0), 700.0);
+      const double f = 2.0 / (exp(x) + 1.0);
+      sm.focc[i] = f;
+      const double h = 0.5 * f;
+      double t = 0.0;
+      if (h > 1e-300) t += h * log(h);
+      if (1.0 - h > 1e-300) t += (1.0 - h) * log(1.0 - h);
+      mts += t;
+    }
+    mts = warp_sum(mts);
+    if (lane == 0) s_mts = 2.0 * kT * mts;
+    __syncwarp();
+    if (lane == 0) {
+      int k = 0;
+      for (int i = 0; i < n; ++i) {
+        const double f = sm.focc[i];
+        if (f > 1e-30) sm.occ[k++] = i;
+      }
+      s_nocc = k;
+    }
+  }
+  __syncthreads();
+  *n_occ_out = s_nocc;
+  return s_mts;
+}
+
+// Modified Broyden mixing (Johnson 1988) of the shell-charge vector, FP64.
+// x_new = x_in + a F - sum_n g_n u_n, F = x_out - x_in, dF/dx normalised
+// differences, u = a dF + dx, (w0^2 I + dF dF^T) g = dF F.
+__device__ void broyden_step(int nsh, int it, double* hist, SccSmem& sm, int& hcount, int& hhead,
+                             double alpha, double w0) {
+  double* dF = hist;                          // [kHist][nsh]
+  double* U = hist + (size_t)kHist * nsh;     // [kHist][nsh]
+  double* px = hist + (size_t)2 * kHist * nsh;
+  double* pF = px + nsh;
+  double* red = sm.red;
+  __shared__ double s_norm;
+  if (it > 1) {
+    double nn = 0.0;
+    for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
+      const double F = sm.dqout[i] - sm.dqin[i];
+      const double d = F - pF[i];
+      nn += d * d;
+    }
+    nn = block_sum(nn, red);
+    if (threadIdx.x == 0) s_norm = sqrt(nn);
+    __syncthreads();
+    const double norm = s_norm;
+    if (norm > 0.0) {
+      const int slot = (hhead + hcount) % kHist;
+      for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
+        const double F = sm.dqout[i] - sm.dqin[i];
+        const double d = (F - pF[i]) / norm;
+        const double dx = (sm.dqin[i] - px[i]) / norm;
+        dF[(size_t)slot * nsh + i] = d;
+        U[(size_t)slot * nsh + i] = alpha * d + dx;
+      }
+      if (hcount < kHist) ++hcount; else hhead = (hhead + 1) % kHist;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
+    px[i] = sm.dqin[i];
+    pF[i] = sm.dqout[i] - sm.dqin[i];
+  }
+  __syncthreads();
+  const int m = hcount;
+  double* a = sm.bro;                 // m x m
+  double* c = sm.bro + kHist * kHist; // m
+  double* gv = c + kHist;             // m
+  if (m > 0) {
+    // a_kn = dF_k . dF_n, c_k = dF_k . F  (one warp per entry)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int e = wid; e < m * m + m; e += nw) {
+      double s = 0.0;
+      if (e < m * m) {
+        const int k = (hhead + e / m) % kHist, l = (hhead + e % m) % kHist;
+        for (int i = lane; i < nsh; i += 32) s += dF[(size_t)k * nsh + i] * dF[(size_t)l * nsh + i];
+      } else {
+        const int k = (hhead + (e - m * m)) % kHist;
+        for (int i = lane; i < nsh; i += 32) s += dF[(size_t)k * nsh + i] * pF[i];
+      }
+      s = warp_sum(s);
+      if (lane == 0) { if (e < m * m) a[e] = s; else c[e - m * m] = s; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // solve (w0^2 I + a) g = c, Gaussian elimination with partial pivoting
+      double M[kHist][kHist + 1];
+      for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) M[i][j] = a[i * m + j] + (i == j ? w0 * w0 : 0.0);
+        M[i][m] = c[i];
+      }
+      for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r) if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (piv != col) for (int j = 0; j <= m; ++j) { double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
+        const double d = M[col][col];
+        for (int r = 0; r < m; ++r) {
+          if (r == col) continue;
+          const double f = M[r][col] / d;
+          for (int j = col; j <= m; ++j) M[r][j] -= f * M[col][j];
+        }
+      }
+      for (int i = 0; i < m; ++i) gv[i] = M[i][m] / M[i][i];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
+    const double F = sm.dqout[i] - sm.dqin[i];
+    double x = sm.dqin[i] + alpha * F;
+    for (int k = 0; k < m; ++k) x -= gv[k] * U[(size_t)((hhead + k) % kHist) * nsh + i];
+    sm.dqin[i] = x;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+struct PrecPtrs {
+  T* CT;
+  T* W1;
+  T* W2;
+  T* A;
+  int lda;
+};
+
+// One SCC iteration in precision T.  Returns E_el; writes dq_out, eps.
+template <typename T>
+__device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<T> pp,
+                                double jac_tol, int* jac_fail, double* diff_out) {
+  const int n = nm.n, nsh = nm.nsh, nat = nm.nat, npad = nm.npad;
+  const double* Sm = ar.S + nm.mat;
+  const double* Hm = ar.H0 + nm.mat;
+  const double* G = ar.gam + nm.gam;
+  // atomic charges and shell shifts (Eq. 7 and the ESP of Eq. 21)
+  for (int a = threadIdx.x; a < nat; a += blockDim.x) sm.dqat[a] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nsh; ++s) sm.dqat[sm.mp.sh_at[s]] += sm.dqin[s];
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = wid; s < nsh; s += nw) {
+      double v = 0.0;
+      for (int t = lane; t < nsh; t += 32) v += G[(size_t)s * nsh + t] * sm.dqin[t];
+      v = warp_sum(v);
+      if (lane == 0) {
+        const int a = sm.mp.sh_at[s];
+        sm.sig[s] = v - sm.g3[a] * sm.dqat[a] * sm.dqat[a] + sm.esp[s];
+      }
+    }
+  }
+  __syncthreads();
+  // Fock matrix F = H0 + 1/2 S (sig_mu + sig_nu), into W1
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int i = int(e / n), j = int(e % n);
+    const double f = Hm[e] + 0.5 * Sm[e] * (sm.sig[sm.mp.ao_sh[i]] + sm.sig[sm.mp.ao_sh[j]]);
+    pp.W1[e] = T(f);
+  }
+  // zero the padding row/column of A
+  if (n != npad) {
+    for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+      pp.A[(long long)i * pp.lda + n] = T(0);
+      pp.A[(long long)n * pp.lda + i] = T(0);
+    }
+  }
+  __syncthreads();
+  T* gemm = reinterpret_cast<T*>(sm.gemm);
+  // U = CT F  (W2), then A = U CT^T: the Fock matrix in the current MO basis
+  block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, gemm);
+  block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, gemm);
+  JacobiScratch<T> js{sm.jsp, sm.jsq, reinterpret_cast<T*>(sm.jsc), reinterpret_cast<T*>(sm.jss), sm.jsact};
+  const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
+  if (sw < 0) *jac_fail = 1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
+  __syncthreads();
+  int nocc = 0;
+  const double mts = fermi_step(n, nm.nel, ar.g.kT, sm, &nocc);
+  // compacted occupations
+  double* fc = reinterpret_cast<double*>(sm.jsc);   // js scratch is free here (npad doubles)
+  for (int k = threadIdx.x; k < nocc; k += blockDim.x) fc[k] = sm.focc[sm.occ[k]];
+  __syncthreads();
+  // density P = sum_occ f_i c_i c_i^T  (W1)
+  block_gemm<T>(n, n, nocc, pp.CT, 1, n, pp.CT, 1, n, pp.W1, n, sm.occ, fc, gemm);
+  // Mulliken shell populations (Eq. 3) and the band energy sum P H0, one warp per shell
+  double eb_local = 0.0;
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = wid; s < nsh; s += nw) {
+      double pop = 0.0, eb = 0.0;
+      for (int k = sm.mp.sh_ao0[s]; k < sm.mp.sh_ao0[s + 1]; ++k) {
+        for (int j = lane; j < n; j += 32) {
+          const double pv = double(pp.W1[(long long)k * n + j]);
+          pop += pv * Sm[(long long)k * n + j];
+          eb += pv * Hm[(long long)k * n + j];
+        }
+      }
+      pop = warp_sum(pop);
+      eb = warp_sum(eb);
+      if (lane == 0) {
+        sm.dqout[s] = pop - sm.q0[s];
+        sm.sig[s] = eb;   // per-shell band energy (sig is free now)
+      }
+    }
+  }
+  __syncthreads();
+  // energy of Eq. 2 from the output density
+  for (int a = threadIdx.x; a < nat; a += blockDim.x) sm.dqat[a] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nsh; ++s) sm.dqat[sm.mp.sh_at[s]] += sm.dqout[s];
+  }
+  __syncthreads();
+  double part = 0.0, dmax = 0.0;
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = wid; s < nsh; s += nw) {
+      double v = 0.0;
+      for (int t = lane; t < nsh; t += 32) v += G[(size_t)s * nsh + t] * sm.dqout[t];
+      v = warp_sum(v);
+      if (lane == 0) {
+        part += sm.sig[s] + 0.5 * sm.dqout[s] * v;
+        dmax = fmax(dmax, fabs(sm.dqout[s] - sm.dqin[s]));
+      }
+    }
+  }
+  for (int a = threadIdx.x; a < nat; a += blockDim.x)
+    part -= sm.g3[a] * sm.dqat[a] * sm.dqat[a] * sm.dqat[a] / 3.0;
+  (void)eb_local;
+  const double e_sum = block_sum(part, sm.red);
+  const double dm = block_max(dmax, sm.red);
+  *diff_out = dm;
+  return e_sum + mts;
+}
+
+// CT <- (M^{-1/2}) CT with M = CT S CT^T, by Newton-Schulz steps
+// CT <- 1.5 CT - 0.5 M CT (each squares the error of M - I), FP64, until
+// max |M - I| < 1e-14: restores the S-orthonormality of eigenvectors carried
+// over from FP32, whose rotations drift it by up to ~1e-4.
+__device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<double> pp) {
+  const int n = nm.n;
+  double* gemm = reinterpret_cast<double*>(sm.gemm);
+  const double* Sm = ar.S + nm.mat;
+  for (int step = 0; step < 4; ++step) {
+    block_gemm<double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, gemm);   // V = CT S
+    block_gemm<double>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.W1, n, nullptr, nullptr, gemm);  // M = V CT^T
+    double err = 0.0;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
+      err = fmax(err, fabs(pp.W1[e] - ((e / n) == (e % n) ? 1.0 : 0.0)));
+    err = block_max(err, sm.red);
+    if (err < 1e-14) break;
+    block_gemm<double>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, gemm);  // M CT
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
+      pp.CT[e] = 1.5 * pp.CT[e] - 0.5 * pp.W2[e];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int idx = ar.order[blockIdx.x];
+  const Nmer nm = ar.nmers[idx];
+  const int n = nm.n, nsh = nm.nsh, nat = nm.nat, npad = nm.npad;
+  const int a_bytes = (ar.a_smem_d ? int(sizeof(double)) : (ar.a_smem_f ? int(sizeof(float)) : 0)) *
+                      ((ar.max_n + (ar.max_n & 1)) * (ar.max_n + (ar.max_n & 1)));
+  SccSmem sm = carve_scc_smem(smem_raw, ar.max_n, ar.max_nsh, ar.max_nat, a_bytes);
+  build_maps(nm, ar.ft, ar.elem, ar.atom_sh0, ar.el, sm.mp);
+  // per-shell / per-atom constants
+  for (int s = threadIdx.x; s < nsh; s += blockDim.x) {
+    const int ga = sm.mp.at_glob[sm.mp.sh_at[s]];
+    const DevElem& e = ar.el[ar.elem[ga]];
+    const int k = sm.mp.sh_glob[s] - ar.atom_sh0[ga];
+    sm.q0[s] = e.q0[k];
+  }
+  for (int a = threadIdx.x; a < nat; a += blockDim.x) sm.g3[a] = ar.el[ar.elem[sm.mp.at_glob[a]]].gamma3;
+  __syncthreads();
+  // repulsion energy inside the n-mer (Eq. 11), unordered atom pairs
+  double er = 0.0;
+  for (long long e = threadIdx.x; e < (long long)nat * nat; e += blockDim.x) {
+    const int i = int(e / nat), j = int(e % nat);
+    if (j >= i) continue;
+    const int ga = sm.mp.at_glob[i], gb = sm.mp.at_glob[j];
+    const DevElem& EA = ar.el[ar.elem[ga]];
+    const DevElem& EB = ar.el[ar.elem[gb]];
+    const double dx = ar.xyz[3 * ga] - ar.xyz[3 * gb], dy = ar.xyz[3 * ga + 1] - ar.xyz[3 * gb + 1],
+                 dz = ar.xyz[3 * ga + 2] - ar.xyz[3 * gb + 2];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    er += EA.zeff * EB.zeff / r * exp(-sqrt(EA.arep * EB.arep) * pow(r, ar.g.k_f));
+  }
+  const double e_rep = block_sum(er, sm.red);
+  // embedding potential of this n-mer: ESP_mu = phi_mu - sum_{lambda in X} gamma dq_mono
+  const double* G = ar.gam + nm.gam;
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = wid; s < nsh; s += nw) {
+      double v = 0.0;
+      if (ar.phi) {
+        for (int t = lane; t < nsh; t += 32) v += G[(size_t)s * nsh + t] * ar.dq_mono[sm.mp.sh_glob[t]];
+        v = warp_sum(v);
+        v = ar.phi[sm.mp.sh_glob[s]] - v;
+      }
+      if (lane == 0) {
+        sm.esp[s] = v;
+        ar.esp[nm.shv + s] = v;
+        sm.dqin[s] = ar.guess_from_mono ? ar.dq_mono[sm.mp.sh_glob[s]] : ar.dq[nm.shv + s];
+      }
+    }
+  }
+  __syncthreads();
+
+  const int lda_d = npad;
+  PrecPtrs<double> pd{ar.CTd + nm.mat, ar.W1d + nm.mat, ar.W2d + nm.mat,
+                      ar.a_smem_d ? reinterpret_cast<double*>(sm.A) : ar.Agd + nm.apad,
+                      lda_d};
+  PrecPtrs<float> pf{nullptr, nullptr, nullptr, nullptr, npad};
+  if (ar.precision == 1) {
+    pf.CT = ar.CTf + nm.mat;
+    pf.W1 = ar.W1f + nm.mat;
+    pf.W2 = ar.W2f + nm.mat;
+    pf.A = ar.a_smem_f ? reinterpret_cast<float*>(sm.A) : ar.Agf + nm.apad;
+  }
+  double* hist = ar.hist + nm.hist;
+  int hcount = 0, hhead = 0;
+  int phase = (ar.precision == 1) ? 0 : 1;   // 0: FP32 loose, 1: FP64
+  double e_prev = 0.0;
+  bool have_prev = false;
+  int status = FMO_SCC_MAX_ITER_CODE;
+  int it = 0, it32 = 0, jac_fail = 0;
+  double e_el = 0.0;
+  for (it = 1; it <= ar.max_iter; ++it) {
+    double diff = 0.0;
+    if (phase == 0) {
+      e_el = scc_iteration<float>(nm, ar, sm, pf, ar.jacobi_tol_f, &jac_fail, &diff);
+      ++it32;
+    } else {
+      e_el = scc_iteration<double>(nm, ar, sm, pd, ar.jacobi_tol_d, &jac_fail, &diff);
+    }
+    // loop decisions are made block-uniform with barrier votes (thread 0's
+    // timer read decides the deadline)
+    if (__syncthreads_or(!isfinite(e_el) || !isfinite(diff))) { status = FMO_SCC_NAN_CODE; break; }
+    if (__syncthreads_and(phase == 1 && have_prev && diff < ar.tol && fabs(e_el - e_prev) < ar.etol)) {
+      status = FMO_SCC_CONVERGED_CODE;
+      break;
+    }
+    e_prev = e_el;
+    have_prev = true;
+    if (__syncthreads_or(threadIdx.x == 0 && ar.budget_ns && globaltimer_ns() > *ar.t0 + ar.budget_ns)) {
+      status = FMO_SCC_TIMEOUT_CODE;
+      break;
+    }
+    broyden_step(nsh, it, hist, sm, hcount, hhead, 0.4, 0.01);
+    if (__syncthreads_and(phase == 0 && (diff < ar.switch_tol || it32 >= ar.fp32_cap))) {
+      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
+      __syncthreads();
+      reorthonormalise(nm, ar, sm, pd);
+      phase = 1;
+      have_prev = false;
+    }
+  }
+  if (it > ar.max_iter) it = ar.max_iter;
+  if (jac_fail && status == FMO_SCC_CONVERGED_CODE) status = FMO_SCC_JACOBI_CODE;
+  // keep a float copy of the eigenvectors for a later warm start
+  if (ar.precision == 1) {
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pf.CT[e] = float(pd.CT[e]);
+  }
+  // results
+  double dev = 0.0;
+  for (int s = threadIdx.x; s < nsh; s += blockDim.x) {
+    ar.dq[nm.shv + s] = sm.dqout[s];
+    if (ar.phi) dev += (sm.dqout[s] - ar.dq_mono[sm.mp.sh_glob[s]]) * sm.esp[s];   // Eq. 13
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ar.eps[nm.aov + i] = sm.eps[i];
+  dev = block_sum(dev, sm.red);
+  if (threadIdx.x == 0) {
+    ar.energy[idx] = e_el + e_rep;
+    ar.e_el[idx] = e_el;
+    ar.e_rep[idx] = e_rep;
+    ar.dEV[idx] = dev;
+    ar.iters[idx] = it;
+    ar.iters32[idx] = it32;
+    ar.status[idx] = status;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Supersystem potential phi_mu = sum_lambda gamma_mu,lambda dq_lambda over all
+// shells (the ESP of Eq. 21 before the fragment's own shells are removed).
+
+__global__ void phi_kernel(int n_sh, const double* __restrict__ xyz, const int* __restrict__ sh_atom,
+                           const double* __restrict__ sh_inv_eta, const double* __restrict__ dq,
+                           GParams g, double* __restrict__ phi) {
+  __shared__ double tx[256], ty[256], tz[256], te[256], tq[256];
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  double x = 0, y = 0, z = 0, ie = 0;
+  if (mu < n_sh) {
+    const int a = sh_atom[mu];
+    x = xyz[3 * a]; y = xyz[3 * a + 1]; z = xyz[3 * a + 2];
+    ie = sh_inv_eta[mu];
+  }
+  double acc = 0.0;
+  for (int t0 = 0; t0 < n_sh; t0 += 256) {
+    const int l = t0 + threadIdx.x;
+    if (l < n_sh) {
+      const int b = sh_atom[l];
+      tx[threadIdx.x] = xyz[3 * b]; ty[threadIdx.x] = xyz[3 * b + 1]; tz[threadIdx.x] = xyz[3 * b + 2];
+      te[threadIdx.x] = sh_inv_eta[l];
+      tq[threadIdx.x] = dq[l];
+    } else {
+      tx[threadIdx.x] = ty[threadIdx.x] = tz[threadIdx.x] = 0.0;
+      te[threadIdx.x] = 1.0;
+      tq[threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    const int m = min(256, n_sh - t0);
+    for (int k = 0; k < m; ++k) {
+      const double dx = x - tx[k], dy = y - ty[k], dz = z - tz[k];
+      acc += gamma_fn(dx * dx + dy * dy + dz * dz, ie, te[k], g.k_g) * tq[k];
+    }
+    __syncthreads();
+  }
+  if (mu < n_sh) phi[mu] = acc;
+}
+
+// Fragment centroids and bounding radii (for pruning the pair search).
+__global__ void frag_bounds_kernel(int n_frag, FragTab ft, const double* __restrict__ xyz,
+                                   double* __restrict__ bounds) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_frag) return;
+  const int a0 = ft.atom0[f], na = ft.nat[f];
+  double cx = 0, cy = 0, cz = 0;
+  for (int i = 0; i < na; ++i) { cx += xyz[3 * (a0 + i)]; cy += xyz[3 * (a0 + i) + 1]; cz += xyz[3 * (a0 + i) + 2]; }
+  cx /= na; cy /= na; cz /= na;
+  double r = 0;
+  for (int i = 0; i < na; ++i) {
+    const double dx = xyz[3 * (a0 + i)] - cx, dy = xyz[3 * (a0 + i) + 1] - cy, dz = xyz[3 * (a0 + i) + 2] - cz;
+    r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+  }
+  bounds[4 * f] = cx; bounds[4 * f + 1] = cy; bounds[4 * f + 2] = cz; bounds[4 * f + 3] = r;
+}
+
+// Closest inter-fragment atom distance of every pair I<J (lexicographic pair
+// index); pairs whose bounding spheres are farther apart than `cut` get the
+// sphere gap, a lower bound that already decides the (strict <) test.
+__global__ void pair_distance_kernel(int n_frag, FragTab ft, const double* __restrict__ xyz,
+                                     const double* __restrict__ bounds, double cut,
+                                     double* __restrict__ rmin) {
+  const long long npair = (long long)n_frag * (n_frag - 1) / 2;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long e = warp; e < npair; e += nwarps) {
+    // pair index -> (I, J): rows I hold n-1-I entries
+    long long I = 0, base = 0;
+    {
+      // solve base(I) = I*(2n - I - 1)/2 <= e
+      double nn = double(n_frag);
+      double disc = (2 * nn - 1) * (2 * nn - 1) - 8.0 * double(e);
+      I = (long long)((2 * nn - 1 - sqrt(fmax(disc, 0.0))) * 0.5);
+      if (I < 0) I = 0;
+      while (I > 0 && I * (2 * n_frag - I - 1) / 2 > e) --I;
+      while ((I + 1) * (2 * n_frag - I - 2) / 2 <= e) ++I;
+      base = I * (2 * n_frag - I - 1) / 2;
+    }
+    const int J = int(I + 1 + (e - base));
+    const double cdx = bounds[4 * I] - bounds[4 * J], cdy = bounds[4 * I + 1] - bounds[4 * J + 1],
+                 cdz = bounds[4 * I + 2] - bounds[4 * J + 2];
+    const double gap = sqrt(cdx * cdx + cdy * cdy + cdz * cdz) - bounds[4 * I + 3] - bounds[4 * J + 3];
+    if (gap >= cut) {
+      if (lane == 0) rmin[e] = gap;
+      continue;
+    }
+    const int a0 = ft.atom0[I], na = ft.nat[I], b0 = ft.atom0[J], nb = ft.nat[J];
+    double best = 1e300;
+    for (int k = lane; k < na * nb; k += 32) {
+      const int a = a0 + k / nb, b = b0 + k % nb;
+      const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
+                   dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+      best = fmin(best, dx * dx + dy * dy + dz * dz);
+    }
+    best = -warp_max(-best);
+    if (lane == 0) rmin[e] = sqrt(best);
+  }
+}
+
+// ES-DIM pair energies (Eq. 15): sum_{mu in I, nu in J} gamma dq_I dq_J.
+__global__ void esdim_kernel(int n_pairs, const int2* __restrict__ pairs, const long long* __restrict__ out_idx,
+                             FragTab ft, const double* __restrict__ xyz, const int* __restrict__ sh_atom,
+                             const double* __restrict__ sh_inv_eta, const double* __restrict__ dq,
+                             GParams g, double* __restrict__ out) {
+  __shared__ double red[32];
+  for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+    const int I = pairs[p].x, J = pairs[p].y;
+    const int s0 = ft.sh0[I], ns = ft.nsh[I], t0 = ft.sh0[J], nt = ft.nsh[J];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < ns * nt; k += blockDim.x) {
+      const int mu = s0 + k / nt, nu = t0 + k % nt;
+      const int a = sh_atom[mu], b = sh_atom[nu];
+      const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
+                   dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+      acc += gamma_fn(dx * dx + dy * dy + dz * dz, sh_inv_eta[mu], sh_inv_eta[nu], g.k_g) * dq[mu] * dq[nu];
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) out[out_idx[p]] = acc;
+    __syncthreads();
+  }
+}
+
+// max |a - b| over a vector (single block).
+__global__ void maxdiff_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
+                               double* __restrict__ out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(a[i] - b[i]));
+  m = block_max(m, red);
+  if (threadIdx.x == 0) *out = m;
+}
+
+// Neumaier-compensated sum of one thread's strided subset, then a fixed tree.
+__device__ void neumaier_add(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+  s = t;
+}
+
+__device__ double block_sum_compensated(double s, double c, double* red) {
+  // combine (s + c) pairs with a fixed-shape tree
+  const double v = s + c;
+  return block_sum(v, red);
+}
+
+// FMO sums (Eqs. 12-19).  One block; fixed summation order.
+//   dE_pair[p]      in: ES-DIM values for ES-DIM pairs; out: dE_IJ for all pairs
+//   pair_scc[p]     index of the pair in the SCC-dimer pass or -1
+__global__ void fmo_sum_kernel(int n_frag, const double* __restrict__ e_mono, long long n_pair,
+                               const int* __restrict__ pair_scc, const double* __restrict__ e_dim,
+                               const double* __restrict__ dEV_dim, double* __restrict__ dE_pair,
+                               int n_tri, const int* __restrict__ tri_frag, const double* __restrict__ e_tri,
+                               const double* __restrict__ dEV_tri, double* __restrict__ dE3,
+                               double* __restrict__ corr, double* __restrict__ totals) {
+  __shared__ double red[32];
+  double s = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < n_frag; i += blockDim.x) neumaier_add(s, c, e_mono[i]);
+  const double e1 = block_sum_compensated(s, c, red);
+  s = 0.0; c = 0.0;
+  for (long long p = threadIdx.x; p < n_pair; p += blockDim.x) {
+    // (I, J) of the lexicographic pair index
+    double nn = double(n_frag);
+    long long I = (long long)((2 * nn - 1 - sqrt(fmax((2 * nn - 1) * (2 * nn - 1) - 8.0 * double(p), 0.0))) * 0.5);
+    if (I < 0) I = 0;
+    while (I > 0 && I * (2 * n_frag - I - 1) / 2 > p) --I;
+    while ((I + 1) * (2 * n_frag - I - 2) / 2 <= p) ++I;
+    const long long J = I + 1 + (p - I * (2 * n_frag - I - 1) / 2);
+    const int k = pair_scc[p];
+    double d;
+    if (k >= 0) d = e_dim[k] - e_mono[I] - e_mono[J] + dEV_dim[k];   // Eq. 12
+    else d = dE_pair[p];                                             // Eq. 15
+    dE_pair[p] = d;
+    neumaier_add(s, c, d);
+  }
+  const double e2 = e1 + block_sum_compensated(s, c, red);
+  __syncthreads();
+  s = 0.0; c = 0.0;
+  for (int t = threadIdx.x; t < n_tri; t += blockDim.x) {
+    const int I = tri_frag[3 * t], J = tri_frag[3 * t + 1], K = tri_frag[3 * t + 2];
+    const double d3 = e_tri[t] - e_mono[I] - e_mono[J] - e_mono[K] + dEV_tri[t];   // Eq. 17
+    auto pidx = [&](long long a, long long b) { return a * (2 * n_frag - a - 1) / 2 + (b - a - 1); };
+    const double cr = d3 - dE_pair[pidx(I, J)] - dE_pair[pidx(I, K)] - dE_pair[pidx(J, K)];  // Eq. 16
+    dE3[t] = d3;
+    corr[t] = cr;
+    neumaier_add(s, c, cr);
+  }
+  const double e3c = block_sum_compensated(s, c, red);
+  if (threadIdx.x == 0) {
+    totals[0] = e1;
+    totals[1] = e2;
+    totals[2] = e2 + e3c;
+  }
+}
+
+// Reorder coordinates from input atom order to the internal order.
+__global__ void gather_xyz_kernel(int n_atoms, const int* __restrict__ perm, const double* __restrict__ in,
+                                  double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_atoms) return;
+  const int s = perm[i];
+  out[3 * i] = in[3 * s];
+  out[3 * i + 1] = in[3 * s + 1];
+  out[3 * i + 2] = in[3 * s + 2];
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+
+#define LAUNCH_CHECK() do { cudaError_t e_ = cudaGetLastError(); if (e_ != cudaSuccess) return e_; } while (0)
+
+cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int* elem, const DevElem* el,
+                      GParams g, double* cn) {
+  cn_kernel<<<(n_atoms + 127) / 128, 128, 0, st>>>(n_atoms, xyz, elem, el, g, cn);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_integrals(cudaStream_t st, int n_nmer, int max_pairs, const Nmer* nmers, FragTab ft,
+                             const double* xyz, const int* elem, const int* atom_sh0, const double* cn,
+                             const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0) {
+  if (n_nmer == 0) return cudaSuccess;
+  const int chunks = max(1, min(64, (max_pairs + 127) / 128));
+  for (int b0 = 0; b0 < n_nmer; b0 += 65535) {
+    dim3 grid(chunks, min(65535, n_nmer - b0));
+    integrals_kernel<<<grid, 128, 0, st>>>(nmers + b0, ft, xyz, elem, atom_sh0, cn, el, kab, ne, g, S, H0);
+    LAUNCH_CHECK();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_gamma(cudaStream_t st, int n_nmer, int max_nsh, const Nmer* nmers, FragTab ft,
+                         const double* xyz, const int* elem, const int* sh_atom, const double* sh_inv_eta,
+                         GParams g, double* gam) {
+  if (n_nmer == 0) return cudaSuccess;
+  const int chunks = max(1, min(64, (max_nsh * max_nsh + 255) / 256));
+  for (int b0 = 0; b0 < n_nmer; b0 += 65535) {
+    dim3 grid(chunks, min(65535, n_nmer - b0));
+    gamma_kernel<<<grid, 256, 0, st>>>(nmers + b0, ft, xyz, elem, sh_atom, sh_inv_eta, g, gam);
+    LAUNCH_CHECK();
+  }
+  return cudaSuccess;
+}
+
+static size_t lowdin_smem(int max_n, int elem_bytes, int a_in_smem) {
+  const int npad = max_n + (max_n & 1);
+  size_t b = 0;
+  if (a_in_smem) b += (size_t)elem_bytes * npad * npad;
+  b += (size_t)elem_bytes * 2 * 16 * 64 + sizeof(double) * 32 + sizeof(double) * npad + 3 * sizeof(int) * npad;
+  b = (b + 15) & ~size_t(15);
+  b += 2 * (size_t)elem_bytes * npad + 16;
+  return b;
+}
+
+cudaError_t launch_lowdin(cudaStream_t st, int n_nmer, int max_n, const Nmer* nmers, const double* S,
+                          void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status) {
+  if (n_nmer == 0) return cudaSuccess;
+  if (use_float) {
+    const size_t sb = lowdin_smem(max_n, 4, a_in_smem);
+    cudaFuncSetAttribute(lowdin_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    lowdin_kernel<float><<<n_nmer, kBlock, sb, st>>>(nmers, S, (float*)CT, (float*)W, (float*)Ag, a_in_smem,
+                                                     1e-7, status);
+  } else {
+    const size_t sb = lowdin_smem(max_n, 8, a_in_smem);
+    cudaFuncSetAttribute(lowdin_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    lowdin_kernel<double><<<n_nmer, kBlock, sb, st>>>(nmers, S, (double*)CT, (double*)W, (double*)Ag,
+                                                      a_in_smem, 1e-14, status);
+  }
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+size_t scc_smem_size(int max_n, int max_nsh, int max_nat, int a_bytes) {
+  return scc_smem_bytes(max_n, max_nsh, max_nat, a_bytes);
+}
+
+cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
+  if (n_nmer == 0) return cudaSuccess;
+  SccArgs ar;
+  ar.nmers = L.nmers; ar.order = L.order; ar.ft = L.ft; ar.xyz = L.xyz; ar.elem = L.elem;
+  ar.atom_sh0 = L.atom_sh0; ar.el = L.el; ar.g = L.g; ar.S = L.S; ar.H0 = L.H0; ar.gam = L.gam;
+  ar.CTd = L.CTd; ar.W1d = L.W1d; ar.W2d = L.W2d; ar.Agd = L.Agd;
+  ar.CTf = L.CTf; ar.W1f = L.W1f; ar.W2f = L.W2f; ar.Agf = L.Agf;
+  ar.phi = L.phi; ar.dq_mono = L.dq_mono; ar.esp = L.esp; ar.dq = L.dq; ar.eps = L.eps; ar.hist = L.hist;
+  ar.energy = L.energy; ar.e_el = L.e_el; ar.e_rep = L.e_rep; ar.dEV = L.dEV; ar.iters = L.iters; ar.iters32 = L.iters32;
+  ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
+  ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap; ar.tol = L.tol; ar.etol = L.etol;
+  ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
+  ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
+  ar.max_n = L.max_n; ar.max_nsh = L.max_nsh; ar.max_nat = L.max_nat;
+  const int npad = L.max_n + (L.max_n & 1);
+  const int a_bytes = (L.a_smem_d ? 8 : (L.a_smem_f ? 4 : 0)) * npad * npad;
+  const size_t sb = scc_smem_bytes(L.max_n, L.max_nsh, L.max_nat, a_bytes);
+  cudaError_t e = cudaFuncSetAttribute(scc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+  if (e != cudaSuccess) return e;
+  scc_kernel<<<n_nmer, kBlock, sb, st>>>(ar);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
+                       const double* dq, GParams g, double* phi) {
+  phi_kernel<<<(n_sh + 255) / 256, 256, 0, st>>>(n_sh, xyz, sh_atom, sh_inv_eta, dq, g, phi);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds) {
+  frag_bounds_kernel<<<(n_frag + 127) / 128, 128, 0, st>>>(n_frag, ft, xyz, bounds);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, const double* bounds,
+                                 double cut, double* rmin) {
+  const long long npair = (long long)n_frag * (n_frag - 1) / 2;
+  if (npair == 0) return cudaSuccess;
+  const long long warps = npair;
+  const int blocks = (int)std::min<long long>((warps * 32 + 255) / 256, 148LL * 64);
+  pair_distance_kernel<<<blocks, 256, 0, st>>>(n_frag, ft, xyz, bounds, cut, rmin);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const long long* out_idx, FragTab ft,
+                         const double* xyz, const int* sh_atom, const double* sh_inv_eta, const double* dq,
+                         GParams g, double* out) {
+  if (n_pairs == 0) return cudaSuccess;
+  const int blocks = std::min(n_pairs, 148 * 16);
+  esdim_kernel<<<blocks, 256, 0, st>>>(n_pairs, pairs, out_idx, ft, xyz, sh_atom, sh_inv_eta, dq, g, out);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_maxdiff(cudaStream_t st, int n, const double* a, const double* b, double* out) {
+  maxdiff_kernel<<<1, 1024, 0, st>>>(n, a, b, out);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_fmo_sum(cudaStream_t st, int n_frag, const double* e_mono, long long n_pair, const int* pair_scc,
+                           const double* e_dim, const double* dEV_dim, double* dE_pair, int n_tri,
+                           const int* tri_frag, const double* e_tri, const double* dEV_tri, double* dE3,
+                           double* corr, double* totals) {
+  fmo_sum_kernel<<<1, 1024, 0, st>>>(n_frag, e_mono, n_pair, pair_scc, e_dim, dEV_dim, dE_pair, n_tri, tri_frag,
+                                      e_tri, dEV_tri, dE3, corr, totals);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+__global__ void stamp_kernel(unsigned long long* t) { *t = globaltimer_ns(); }
+
+cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t) {
+  stamp_kernel<<<1, 1, 0, st>>>(t);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_gather_xyz(cudaStream_t st, int n_atoms, const int* perm, const double* in, double* out) {
+  gather_xyz_kernel<<<(n_atoms + 255) / 256, 256, 0, st>>>(n_atoms, perm, in, out);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+}  // namespace fmo

@@ -1,0 +1,89 @@
+// Launch interface between the host library (capi.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fmo_device.cuh"
+
+namespace fmo {
+
+// per-n-mer status words (same values as the FMO_SCC_* enum of fmo_xtb.h)
+constexpr int FMO_SCC_CONVERGED_CODE = 0;
+constexpr int FMO_SCC_MAX_ITER_CODE = 1;
+constexpr int FMO_SCC_NAN_CODE = 2;
+constexpr int FMO_SCC_TIMEOUT_CODE = 3;
+constexpr int FMO_SCC_JACOBI_CODE = 4;
+
+struct SccLaunch {
+  const Nmer* nmers;
+  const int* order;
+  FragTab ft;
+  const double* xyz;
+  const int* elem;
+  const int* atom_sh0;
+  const DevElem* el;
+  GParams g;
+  const double* S;
+  const double* H0;
+  const double* gam;
+  double* CTd;
+  double* W1d;
+  double* W2d;
+  double* Agd;
+  float* CTf;
+  float* W1f;
+  float* W2f;
+  float* Agf;
+  const double* phi;
+  const double* dq_mono;
+  double* esp;
+  double* dq;
+  double* eps;
+  double* hist;
+  double* energy;
+  double* e_el;
+  double* e_rep;
+  double* dEV;
+  int* iters;
+  int* iters32;   // iterations spent in the FP32 phase
+  int* status;
+  int guess_from_mono;
+  int precision;
+  int max_iter;
+  int fp32_cap;
+  double tol, etol, switch_tol;
+  double jacobi_tol_d, jacobi_tol_f;
+  const unsigned long long* t0;   // device timestamp of the run start
+  unsigned long long budget_ns;   // 0 = no deadline
+  int a_smem_d, a_smem_f;
+  int max_n, max_nsh, max_nat;
+};
+
+cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int* elem, const DevElem* el,
+                      GParams g, double* cn);
+cudaError_t launch_integrals(cudaStream_t st, int n_nmer, int max_pairs, const Nmer* nmers, FragTab ft,
+                             const double* xyz, const int* elem, const int* atom_sh0, const double* cn,
+                             const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0);
+cudaError_t launch_gamma(cudaStream_t st, int n_nmer, int max_nsh, const Nmer* nmers, FragTab ft,
+                         const double* xyz, const int* elem, const int* sh_atom, const double* sh_inv_eta,
+                         GParams g, double* gam);
+cudaError_t launch_lowdin(cudaStream_t st, int n_nmer, int max_n, const Nmer* nmers, const double* S,
+                          void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status);
+size_t scc_smem_size(int max_n, int max_nsh, int max_nat, int a_bytes);
+cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L);
+cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
+                       const double* dq, GParams g, double* phi);
+cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);
+cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, const double* bounds,
+                                 double cut, double* rmin);
+cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const long long* out_idx, FragTab ft,
+                         const double* xyz, const int* sh_atom, const double* sh_inv_eta, const double* dq,
+                         GParams g, double* out);
+cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t);
+cudaError_t launch_maxdiff(cudaStream_t st, int n, const double* a, const double* b, double* out);
+cudaError_t launch_fmo_sum(cudaStream_t st, int n_frag, const double* e_mono, long long n_pair, const int* pair_scc,
+                           const double* e_dim, const double* dEV_dim, double* dE_pair, int n_tri,
+                           const int* tri_frag, const double* e_tri, const double* dEV_tri, double* dE3,
+                           double* corr, double* totals);
+cudaError_t launch_gather_xyz(cudaStream_t st, int n_atoms, const int* perm, const double* in, double* out);
+
+}  // namespace fmo

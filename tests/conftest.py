@@ -1,7 +1,12 @@
 import os
 import sys
 
-import pytest
+# one BLAS thread: the oracle's matrices are small, and many idle BLAS threads
+# on a large host slow them down by orders of magnitude
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import pytest  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:

@@ -1,0 +1,126 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs.  Tolerances: 1e-8 Eh per fragment energy and 1e-7 Eh for
+FMO totals in the FP64 path, 1e-6 Eh for the totals of the mixed path."""
+import numpy as np
+import pytest
+
+from oracle import fmo as ofmo
+from oracle import xtb
+from paper_2606_28022_b300.inputs import geometry as G
+from paper_2606_28022_b300.inputs.params import ANGSTROM
+
+pytestmark = pytest.mark.gpu
+
+E_FRAG = 1e-8
+E_TOT = 1e-7
+E_TOT_MIXED = 1e-6
+DQ = 1e-7
+
+
+@pytest.fixture(scope="module")
+def gpu(params):
+    from paper_2606_28022_b300 import build, fmo
+    build.build()
+    return fmo.FMO(params, 0)
+
+
+def run_gpu(gpu, system, **kw):
+    from paper_2606_28022_b300 import fmo
+    gpu.set_system(system)
+    gpu.run(fmo.options(**kw))
+    return gpu
+
+
+def compare(g, ref, e_tot=E_TOT, e_frag=E_FRAG, dq_tol=DQ, level=2):
+    e1, e2, e3 = g.energies()
+    mono = g.monomers()
+    assert np.max(np.abs(mono.energy - ref.e_mono)) < e_frag
+    assert np.max(np.abs(mono.shell_dq - np.concatenate(ref.dq_mono))) < dq_tol
+    assert (mono.status == 0).all()
+    assert abs(e1 - ref.e_fmo1) < e_tot
+    if level >= 2:
+        d = g.dimers()
+        assert np.array_equal(d.ij, ref.dimers)
+        assert np.array_equal(d.scc, ref.dimer_scc)
+        assert np.max(np.abs(d.dE - ref.dE_dimer)) < e_frag
+        assert abs(e2 - ref.e_fmo2) < e_tot
+    if level >= 3:
+        t = g.trimers()
+        assert np.array_equal(t.ijk, ref.trimers)
+        assert np.max(np.abs(t.corr - ref.corr_trimer), initial=0.0) < e_frag
+        assert abs(e3 - ref.e_fmo3) < e_tot
+
+
+def test_water8_fmo2_all_dimers_fp64(gpu, params, water64):
+    s = water64.subsystem(range(8))
+    ref = ofmo.fmo(s, params, ofmo.FMOOptions(all_dimers_scc=True))
+    compare(run_gpu(gpu, s, all_dimers_scc=1), ref)
+
+
+def test_water12_fmo2_esdim_fp64(gpu, params, water64):
+    # the 4.0 A rule splits the pairs into SCC dimers and ES-DIM pairs
+    s = water64.subsystem(range(12))
+    ref = ofmo.fmo(s, params, ofmo.FMOOptions())
+    assert ref.dimer_scc.any() and not ref.dimer_scc.all()
+    compare(run_gpu(gpu, s), ref)
+
+
+def test_water5_fmo3_fp64(gpu, params, water64):
+    s = water64.subsystem(range(5))
+    ref = ofmo.fmo(s, params, ofmo.FMOOptions(level=3, all_dimers_scc=True, trimer_cut=1e9))
+    compare(run_gpu(gpu, s, level=3, all_dimers_scc=1, trimer_cut=1e9), ref, level=3)
+
+
+def test_two_fragments_equal_full_scc_on_gpu(gpu, params, water64):
+    s = water64.subsystem([3, 7])
+    full = xtb.single_point(s, params)
+    g = run_gpu(gpu, s, all_dimers_scc=1)
+    assert abs(g.energies()[1] - full.energy) < E_TOT
+
+
+def test_single_fragment(gpu, params, water64):
+    s = water64.subsystem([2])
+    iso = xtb.single_point(s, params)
+    g = run_gpu(gpu, s)
+    e1, e2, _ = g.energies()
+    assert abs(e1 - iso.energy) < E_FRAG and abs(e2 - iso.energy) < E_FRAG
+    assert g.dimers().ij.shape == (0, 2)
+
+
+@pytest.fixture(scope="module")
+def anthracene4():
+    s, _ = G.anthracene_cluster(128, 2)
+    # four mutually close molecules of the seeded crystal
+    return s.subsystem([0, 1, 2, 3])
+
+
+def test_anthracene4_fmo2_fp64(gpu, params, anthracene4):
+    ref = ofmo.fmo(anthracene4, params, ofmo.FMOOptions(all_dimers_scc=True))
+    compare(run_gpu(gpu, anthracene4, all_dimers_scc=1), ref)
+
+
+def test_anthracene4_fmo2_mixed(gpu, params, anthracene4):
+    ref = ofmo.fmo(anthracene4, params, ofmo.FMOOptions(all_dimers_scc=True))
+    g = run_gpu(gpu, anthracene4, all_dimers_scc=1, precision="mixed")
+    e1, e2, _ = g.energies()
+    assert abs(e2 - ref.e_fmo2) < E_TOT_MIXED
+    assert abs(e1 - ref.e_fmo1) < E_TOT_MIXED
+
+
+def test_water8_mixed(gpu, params, water64):
+    s = water64.subsystem(range(8))
+    ref = ofmo.fmo(s, params, ofmo.FMOOptions(all_dimers_scc=True))
+    g = run_gpu(gpu, s, all_dimers_scc=1, precision="mixed")
+    assert abs(g.energies()[1] - ref.e_fmo2) < E_TOT_MIXED
+
+
+def test_new_coordinates_same_topology(gpu, params, water64):
+    from paper_2606_28022_b300 import fmo
+    s = water64.subsystem(range(4))
+    s2 = G.jittered(s, 0.05, 77)
+    ref = ofmo.fmo(s2, params, ofmo.FMOOptions(all_dimers_scc=True))
+    gpu.set_system(s)
+    gpu.run(fmo.options(all_dimers_scc=1))
+    gpu.set_coordinates(s2.xyz)
+    gpu.run(fmo.options(all_dimers_scc=1))
+    compare(gpu, ref)
