@@ -99,6 +99,7 @@ typedef struct fmo_params {
 } fmo_params;
 
 enum { FMO_PREC_FP64 = 0, FMO_PREC_MIXED = 1 };
+enum { FMO_LOOP_GLOBAL = 0, FMO_LOOP_NESTED = 1 };
 
 typedef struct fmo_options {
   int32_t level;            /* 1 = FMO1, 2 = FMO2 (Eq. 12), 3 = FMO3 (Eq. 16) */
@@ -109,7 +110,11 @@ typedef struct fmo_options {
   int32_t max_outer;        /* monomer ESP iterations */
   int32_t guess;            /* 0 neutral charges, 2 user charges (fmo_set_guess) */
   int32_t schedule;         /* 0 autotuned block size, 1 fixed block size */
-  int32_t reserved_;
+  int32_t monomer_loop;     /* FMO_LOOP_GLOBAL (default): one SCC iteration of
+                               every monomer per outer step, then one Broyden
+                               step on all monomer charges together;
+                               FMO_LOOP_NESTED: every monomer SCC converged in
+                               the ESP of the previous outer iterate */
   double dimer_cut;         /* SCC dimer iff closest atom pair < dimer_cut (bohr) */
   double trimer_cut;        /* SCC trimer iff all three pairs < trimer_cut */
   double scc_tol;           /* max |dq_out - dq_in| at SCC convergence (e) */
@@ -121,7 +126,8 @@ typedef struct fmo_options {
 
 /* Counters of the last fmo_run. */
 typedef struct fmo_stats {
-  int64_t n_monomer_solves;   /* monomer SCCs summed over outer iterations */
+  int64_t n_monomer_solves;   /* monomer SCCs brought to self-consistency (nested
+                                 loop: summed over outer iterations) */
   int64_t n_dimer_scc;        /* SCC dimers */
   int64_t n_dimer_esdim;      /* ES-DIM pairs (Eq. 15) */
   int64_t n_trimer_scc;       /* SCC trimers */

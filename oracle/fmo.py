@@ -13,8 +13,14 @@ paper step by step:
 READINGS (listed in the design notes):
   C-2  E_I, E_IJ, E_IJK are internal energies; the ESP acts only through the
        density, and dE^V supplies the embedding interaction.
-  C-9  the monomer loop is Jacobi-style (all monomers in the ESP of the
-       previous iterate) unless gauss_seidel=True.
+  C-9  the paper asks for monomer charges self-consistent in each other's
+       ESP without fixing the iteration.  monomer_loop="global" (default):
+       every outer step runs one SCC iteration of every monomer in the ESP of
+       the current charges and mixes the concatenated charge vector of all
+       monomers with modified Broyden; "nested": every monomer SCC is solved to
+       convergence in the ESP of the previous iterate (Jacobi-style, or
+       Gauss-Seidel with gauss_seidel=True).  Both have the same fixed point;
+       the nested form converges slowly and can diverge for large clusters.
   C-10 SCC dimer iff the closest inter-fragment atom distance < dimer_cut;
        SCC trimer iff all three pair distances < trimer_cut.
   C-11 E^V_{X,Y} sums over fragments K not in the n-mer Y.
@@ -45,6 +51,7 @@ class FMOOptions:
     max_iter: int = 300
     max_outer: int = 200
     gauss_seidel: bool = False
+    monomer_loop: str = "global"
     workers: int = 1
     mixer: str = "broyden"
 
@@ -116,6 +123,36 @@ class _Frags:
                        e_tol=opts.e_tol, max_iter=opts.max_iter, mixer=mixer)
 
 
+def _global_monomer_loop(fr, opts):
+    """One SCC iteration of every monomer per outer step, in the ESP of the
+    current charges, then one modified-Broyden update of all monomer charges
+    together; ends when the charges reproduce themselves (READING C-9)."""
+    s = fr.system
+    nf = s.n_frag
+    probs = []
+    for I in range(nf):
+        idx = fr.atoms[I]
+        probs.append(xtb.SCCProblem(s.Z[idx], s.xyz[idx], fr.params, fr.cn[idx],
+                                    charge=float(s.frag_charge[I])))
+    bounds = np.concatenate([[0], np.cumsum(fr.n_sh)])
+    split = lambda x: [x[bounds[I]:bounds[I + 1]] for I in range(nf)]
+    x = np.zeros(bounds[-1])
+    mixer = xtb.Broyden() if opts.mixer == "broyden" else xtb.LinearMixer(0.4)
+    e_prev = None
+    for outer in range(1, opts.max_outer + 1):
+        parts = split(x)
+        outs = [probs[I].step(parts[I], esp=fr.esp((I,), parts)) for I in range(nf)]
+        x_out = np.concatenate([o["dq_out"] for o in outs])
+        e_mono = np.array([o["e_el"] + probs[I].e_rep for I, o in enumerate(outs)])
+        diff = float(np.max(np.abs(x_out - x)))
+        e1 = float(np.sum(e_mono))
+        if e_prev is not None and diff < opts.outer_tol and abs(e1 - e_prev) < opts.e_tol:
+            return [p.copy() for p in split(x_out)], e_mono, outer
+        e_prev = e1
+        x = mixer.step(x, x_out)
+    return [p.copy() for p in split(x_out)], e_mono, opts.max_outer
+
+
 _POOL_STATE = {}
 
 
@@ -153,7 +190,10 @@ def fmo(system, params, opts: FMOOptions | None = None) -> FMOResult:
         e_mono = np.zeros(nf)
         mono_iters = np.zeros(nf, dtype=np.int64)
         outer = 0
-        for outer in range(1, opts.max_outer + 1):
+        if opts.monomer_loop == "global":
+            dq_mono, e_mono, outer = _global_monomer_loop(fr, opts)
+            mono_iters[:] = outer
+        for outer in (range(1, opts.max_outer + 1) if opts.monomer_loop == "nested" else []):
             change = 0.0
             if opts.gauss_seidel:
                 for I in range(nf):

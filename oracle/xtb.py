@@ -361,6 +361,56 @@ def n_electrons(Z, params, charge=0.0) -> float:
     return float(sum(params.elements[int(z)].n_valence for z in Z) - charge)
 
 
+class SCCProblem:
+    """The fixed matrices of one SCC solve (S, H0, gamma, X = S^-1/2, ...) and
+    the map from input shell charges to the output density and energy: one
+    iteration of the SCC loop (Eqs. 2, 3, 6, 7 and the ESP of Eq. 24)."""
+
+    def __init__(self, Z, xyz, params, cn, esp=None, charge=0.0, extra_fock=None, n_el=None):
+        self.Z, self.xyz, self.params = Z, xyz, params
+        self.kT = 3.166811563e-6 * params.t_el
+        self.basis = b = make_basis(Z, params)
+        self.S = overlap_matrix(Z, xyz, params, b)
+        self.H0 = h0_matrix(Z, xyz, params, self.S, cn, b)
+        self.gam = gamma_matrix(Z, xyz, params, b)
+        self.q0 = shell_param(Z, b, params, "q0_l")
+        self.g3 = atom_param(Z, params, "gamma3")
+        self.e_rep = repulsion_energy(Z, xyz, params)
+        self.n_el = n_electrons(Z, params, charge) if n_el is None else n_el
+        self.esp = np.zeros(b.n_sh) if esp is None else np.asarray(esp, dtype=np.float64)
+        self.extra_fock = extra_fock
+        s_val, s_vec = np.linalg.eigh(self.S)
+        self.X = (s_vec / np.sqrt(s_val)) @ s_vec.T           # Loewdin orthogonaliser
+
+    def step(self, dq, esp=None):
+        """Fock matrix from the input charges dq (and the embedding potential,
+        self.esp unless given), eigensolve, occupations, density, Mulliken
+        charges and the energy of the output density."""
+        import scipy.linalg as sla
+        b = self.basis
+        sh = b.ao_shell
+        nat = len(self.Z)
+        esp = self.esp if esp is None else esp
+        dq_atom = np.bincount(b.sh_atom, weights=dq, minlength=nat)
+        shift = self.gam @ dq - self.g3[b.sh_atom] * dq_atom[b.sh_atom] ** 2 + esp
+        F = self.H0 + 0.5 * self.S * (shift[sh][:, None] + shift[sh][None, :])
+        if self.extra_fock is not None:
+            F = F + self.extra_fock
+        eps, Cp = sla.eigh(self.X @ F @ self.X)
+        C = self.X @ Cp
+        occ, ef, mts = fermi_occupations(eps, self.n_el, self.kT)
+        P = (C * occ) @ C.T
+        pops = np.bincount(sh, weights=(P * self.S).sum(axis=1), minlength=b.n_sh)  # Eq. 3
+        dq_out = pops - self.q0
+        dq_out_atom = np.bincount(b.sh_atom, weights=dq_out, minlength=nat)
+        e_band = float(np.sum(P * self.H0))
+        e2 = 0.5 * float(dq_out @ self.gam @ dq_out)
+        e3 = -float(np.sum(self.g3 * dq_out_atom ** 3)) / 3.0
+        e_el = e_band + e2 + e3 + mts                                     # Eq. 2
+        return dict(dq_out=dq_out, e_el=e_el, e_band=e_band, e2=e2, e3=e3, mts=mts, P=P, C=C,
+                    eps=eps, occ=occ)
+
+
 def scc(Z, xyz, params, cn, esp=None, guess=None, charge=0.0, tol=1e-10, e_tol=1e-10,
         max_iter=300, mixer=None, extra_fock=None, n_el=None) -> SCCResult:
     """One GFN1-xTB SCC solve of a set of atoms.
@@ -374,57 +424,24 @@ def scc(Z, xyz, params, cn, esp=None, guess=None, charge=0.0, tol=1e-10, e_tol=1
     Returns the internal energy: the ESP and extra_fock only act through the
     density (READING C-2).
     """
-    import scipy.linalg as sla
-    kT = 3.166811563e-6 * params.t_el
-    basis = make_basis(Z, params)
-    S = overlap_matrix(Z, xyz, params, basis)
-    H0 = h0_matrix(Z, xyz, params, S, cn, basis)
-    gam = gamma_matrix(Z, xyz, params, basis)
-    q0 = shell_param(Z, basis, params, "q0_l")
-    g3 = atom_param(Z, params, "gamma3")
-    e_rep = repulsion_energy(Z, xyz, params)
-    if n_el is None:
-        n_el = n_electrons(Z, params, charge)
-    esp = np.zeros(basis.n_sh) if esp is None else np.asarray(esp, dtype=np.float64)
-    sh = basis.ao_shell
-    nat = len(Z)
-
-    # Loewdin orthogonaliser X = S^(-1/2)
-    s_val, s_vec = np.linalg.eigh(S)
-    X = (s_vec / np.sqrt(s_val)) @ s_vec.T
-
-    dq = np.zeros(basis.n_sh) if guess is None else np.asarray(guess, dtype=np.float64).copy()
+    prob = SCCProblem(Z, xyz, params, cn, esp=esp, charge=charge, extra_fock=extra_fock, n_el=n_el)
+    dq = np.zeros(prob.basis.n_sh) if guess is None else np.asarray(guess, dtype=np.float64).copy()
     mixer = Broyden() if mixer is None else mixer
     e_prev = None
     converged = False
     it = 0
     for it in range(1, max_iter + 1):
-        dq_atom = np.bincount(basis.sh_atom, weights=dq, minlength=nat)
-        # shell shifts: second order + third order + embedding (Eq. 7, Eq. 24)
-        shift = gam @ dq - g3[basis.sh_atom] * dq_atom[basis.sh_atom] ** 2 + esp
-        F = H0 + 0.5 * S * (shift[sh][:, None] + shift[sh][None, :])
-        if extra_fock is not None:
-            F = F + extra_fock
-        eps, Cp = sla.eigh(X @ F @ X)
-        C = X @ Cp
-        occ, ef, mts = fermi_occupations(eps, n_el, kT)
-        P = (C * occ) @ C.T
-        pops = np.bincount(sh, weights=(P * S).sum(axis=1), minlength=basis.n_sh)  # Eq. 3
-        dq_out = pops - q0
-        dq_out_atom = np.bincount(basis.sh_atom, weights=dq_out, minlength=nat)
-        e_band = float(np.sum(P * H0))
-        e2 = 0.5 * float(dq_out @ gam @ dq_out)
-        e3 = -float(np.sum(g3 * dq_out_atom ** 3)) / 3.0
-        e_el = e_band + e2 + e3 + mts                                     # Eq. 2
-        diff = np.max(np.abs(dq_out - dq)) if len(dq) else 0.0
-        if e_prev is not None and diff < tol and abs(e_el - e_prev) < e_tol:
+        r = prob.step(dq)
+        diff = np.max(np.abs(r["dq_out"] - dq)) if len(dq) else 0.0
+        if e_prev is not None and diff < tol and abs(r["e_el"] - e_prev) < e_tol:
             converged = True
             break
-        e_prev = e_el
-        dq = mixer.step(dq, dq_out)
-    return SCCResult(energy=e_el + e_rep, e_el=e_el, e_rep=e_rep, e_band=e_band, e_coul2=e2,
-                     e_coul3=e3, minus_ts=mts, dq=dq_out, P=P, S=S, H0=H0, C=C, eps=eps,
-                     occ=occ, iterations=it, converged=converged, basis=basis)
+        e_prev = r["e_el"]
+        dq = mixer.step(dq, r["dq_out"])
+    return SCCResult(energy=r["e_el"] + prob.e_rep, e_el=r["e_el"], e_rep=prob.e_rep, e_band=r["e_band"],
+                     e_coul2=r["e2"], e_coul3=r["e3"], minus_ts=r["mts"], dq=r["dq_out"], P=r["P"],
+                     S=prob.S, H0=prob.H0, C=r["C"], eps=r["eps"], occ=r["occ"], iterations=it,
+                     converged=converged, basis=prob.basis)
 
 
 def single_point(system, params, tol=1e-10, **kw) -> SCCResult:

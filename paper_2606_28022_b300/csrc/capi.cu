@@ -108,7 +108,7 @@ struct fmo_ctx {
   std::vector<double> f_nel, h_sh_inv_eta;
   DevBuf d_xyz, d_xyz_in, d_perm, d_elem, d_cn, d_atom_sh0, d_sh_atom, d_sh_inv_eta;
   DevBuf d_f_atom0, d_f_nat, d_f_sh0, d_f_nsh, d_f_ao0, d_f_nao;
-  DevBuf d_dq_mono, d_phi, d_bounds, d_rmin, d_scalar, d_t0;
+  DevBuf d_dq_mono, d_phi, d_bounds, d_rmin, d_scalar, d_t0, d_mix_hist, d_mix_state;
   DevBuf d_pair_scc, d_dE_pair, d_esdim_pairs, d_esdim_idx, d_tri_frag, d_dE3, d_corr, d_totals;
   std::vector<double> guess;
   bool have_guess = false;
@@ -310,7 +310,7 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
 }
 
 fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& sp, bool with_phi,
-                   int pass_id, cudaStream_t st) {
+                   int pass_id, cudaStream_t st, int single_step = 0, int step_phase = 1, int reortho = 0) {
   const int nn = int(P.nm.size());
   if (nn == 0) return FMO_OK;
   SccLaunch L{};
@@ -330,6 +330,9 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.precision = o.precision;
   L.max_iter = o.max_iter;
   L.fp32_cap = std::max(4, o.max_iter / 2);
+  L.single_step = single_step;
+  L.step_phase = step_phase;
+  L.reortho = reortho;
   L.tol = o.scc_tol; L.etol = o.e_tol; L.switch_tol = o.mixed_switch_tol;
   L.jacobi_tol_d = 1e-14;
   L.jacobi_tol_f = 2e-7;
@@ -404,6 +407,7 @@ void fmo_options_default(fmo_options* o) {
   o->max_outer = 200;
   o->guess = 0;
   o->schedule = 0;
+  o->monomer_loop = FMO_LOOP_GLOBAL;
   o->dimer_cut = 4.0 / 0.529177210903;
   o->trimer_cut = 4.0 / 0.529177210903;
   o->scc_tol = 1e-10;
@@ -447,7 +451,7 @@ void fmo_destroy(fmo_ctx* ctx) {
   for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
                     &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
                     &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_dq_mono, &ctx->d_phi,
-                    &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_pair_scc, &ctx->d_dE_pair,
+                    &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
                     &ctx->d_totals})
     b->release();
@@ -645,6 +649,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (o.max_iter < 1 || o.max_outer < 1 || !(o.scc_tol > 0) || !(o.e_tol > 0) || !(o.outer_tol > 0))
     return fail(ctx, FMO_ERR_ARG, "iteration limits and tolerances must be positive");
   if (o.guess == 2 && !ctx->have_guess) return fail(ctx, FMO_ERR_STATE, "guess = 2 needs fmo_set_guess");
+  if (o.monomer_loop != FMO_LOOP_GLOBAL && o.monomer_loop != FMO_LOOP_NESTED)
+    return fail(ctx, FMO_ERR_ARG, "unknown monomer loop");
   cudaSetDevice(ctx->device);
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
   std::memset(&ctx->stats, 0, sizeof(ctx->stats));
@@ -680,6 +686,40 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   int outer = 0;
   double h_change_v = 0.0;
   double* h_change = &h_change_v;
+  if (o.monomer_loop == FMO_LOOP_GLOBAL) {
+    // one SCC iteration of every monomer per outer step, then one Broyden
+    // step on all monomer charges (decided on the device)
+    CK(ctx->d_mix_hist.ensure(sizeof(double) * (2 * kHist + 2) * (size_t)ctx->n_sh));
+    CK(ctx->d_mix_state.ensure(mix_state_bytes()));
+    CK(cudaMemsetAsync(ctx->d_mix_state.p, 0, mix_state_bytes(), st));
+    int phase = (o.precision == FMO_PREC_MIXED) ? 0 : 1, reortho = 0, n32 = 0;
+    const int cap32 = std::max(8, o.max_outer / 2);
+    struct { double e_prev, diff, e1; int have_prev, hcount, hhead, converged, count; } hs{};
+    for (outer = 1; outer <= o.max_outer; ++outer) {
+      CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
+                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>()));
+      stage(st, "phi", outer);
+      fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 1, phase, reortho);
+      if (fs != FMO_OK) return fs;
+      reortho = 0;
+      CK(launch_global_mix(st, ctx->n_sh, ctx->d_dq_mono.as<double>(), ctx->mono.dq.as<double>(), nf,
+                           ctx->mono.energy.as<double>(), ctx->d_mix_hist.as<double>(), ctx->d_mix_state.p,
+                           o.outer_tol, o.e_tol, phase == 1));
+      CK(d2h(&hs, ctx->d_mix_state.p, sizeof(hs), st));
+      CK(sync_stream(st));
+      ctx->stats.kernel_launches += 2;
+      stage(st, "global mix", outer);
+      change = hs.converged ? 0.0 : hs.diff;
+      if (!(hs.diff == hs.diff)) break;
+      if (hs.converged) break;
+      if (phase == 0 && (hs.diff < o.mixed_switch_tol || ++n32 >= cap32)) {
+        phase = 1;
+        reortho = 1;
+        CK(cudaMemsetAsync(ctx->d_mix_state.p, 0, mix_state_bytes(), st));
+      }
+    }
+    ctx->stats.n_monomer_solves = nf;
+  } else {
   for (outer = 1; outer <= o.max_outer; ++outer) {
     CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
                   ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>()));
@@ -697,6 +737,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     change = *h_change;
     if (!(change == change)) break;
     if (change < o.outer_tol) break;
+  }
   }
   if (outer > o.max_outer) outer = o.max_outer;
   ctx->stats.outer_iterations = outer;

@@ -309,6 +309,9 @@ struct SccArgs {
   int precision;
   int max_iter;
   int fp32_cap;
+  int single_step;   // 1: exactly one SCC iteration, no mixing (global monomer loop)
+  int step_phase;    // single step: 0 FP32, 1 FP64
+  int reortho;       // single step: carry the FP32 vectors over to FP64 first
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
   const unsigned long long* t0;
@@ -598,7 +601,7 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, gemm);
   JacobiScratch<T> js{sm.jsp, sm.jsq, reinterpret_cast<T*>(sm.jsc), reinterpret_cast<T*>(sm.jss), sm.jsact};
   const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
-  if (sw < 0) *jac_fail = 1;
+  if (sw < 0 && sizeof(T) == 8) *jac_fail = 1;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
   __syncthreads();
   int nocc = 0;
@@ -754,7 +757,23 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   int status = FMO_SCC_MAX_ITER_CODE;
   int it = 0, it32 = 0, jac_fail = 0;
   double e_el = 0.0;
-  for (it = 1; it <= ar.max_iter; ++it) {
+  if (ar.single_step) {
+    // one iteration from the given charges in the given precision; the
+    // caller mixes the charges of all monomers together
+    phase = ar.step_phase;
+    if (phase == 1 && ar.precision == 1 && ar.reortho) {
+      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
+      __syncthreads();
+      reorthonormalise(nm, ar, sm, pd);
+    }
+    double diff = 0.0;
+    if (phase == 0) { e_el = scc_iteration<float>(nm, ar, sm, pf, ar.jacobi_tol_f, &jac_fail, &diff); it32 = 1; }
+    else e_el = scc_iteration<double>(nm, ar, sm, pd, ar.jacobi_tol_d, &jac_fail, &diff);
+    it = 1;
+    status = (phase == 1 && jac_fail) ? FMO_SCC_JACOBI_CODE
+             : (__syncthreads_or(!isfinite(e_el)) ? FMO_SCC_NAN_CODE : FMO_SCC_CONVERGED_CODE);
+  }
+  for (it = (ar.single_step ? ar.max_iter + 2 : 1); it <= ar.max_iter; ++it) {
     double diff = 0.0;
     if (phase == 0) {
       e_el = scc_iteration<float>(nm, ar, sm, pf, ar.jacobi_tol_f, &jac_fail, &diff);
@@ -784,10 +803,11 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       have_prev = false;
     }
   }
-  if (it > ar.max_iter) it = ar.max_iter;
+  if (ar.single_step) it = 1;
+  else if (it > ar.max_iter) it = ar.max_iter;
   if (jac_fail && status == FMO_SCC_CONVERGED_CODE) status = FMO_SCC_JACOBI_CODE;
-  // keep a float copy of the eigenvectors for a later warm start
-  if (ar.precision == 1) {
+  // keep a float copy of the final FP64 eigenvectors for a later warm start
+  if (ar.precision == 1 && phase == 1) {
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pf.CT[e] = float(pd.CT[e]);
   }
   // results
@@ -932,6 +952,112 @@ __global__ void esdim_kernel(int n_pairs, const int2* __restrict__ pairs, const 
   }
 }
 
+// Neumaier-compensated sum of one thread's strided subset, then a fixed tree.
+__device__ void neumaier_add(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+  s = t;
+}
+
+// Global monomer loop: one modified-Broyden step (Johnson 1988) on the
+// concatenated shell charges of all monomers.  x = current input (updated in
+// place), xo = the monomers' output charges, e = monomer energies.  Decides
+// convergence on the device: max |xo - x| < tol and |E1 - E1_prev| < etol
+// (E1 = sum of monomer energies, fixed order); then x <- xo.  One block.
+struct MixState {
+  double e_prev, diff, e1;
+  int have_prev, hcount, hhead, converged, count;
+};
+
+__global__ void global_mix_kernel(int n, double* __restrict__ x, const double* __restrict__ xo, int nf,
+                                  const double* __restrict__ e, double* __restrict__ hist, MixState* st,
+                                  double alpha, double w0, double tol, double etol, int allow_converge) {
+  __shared__ double red[32];
+  __shared__ double sa[kHist * kHist + 2 * kHist];
+  double* dF = hist;
+  double* U = hist + (size_t)kHist * n;
+  double* px = hist + (size_t)2 * kHist * n;
+  double* pF = px + n;
+  double dm = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dm = fmax(dm, fabs(xo[i] - x[i]));
+  dm = block_max(dm, red);
+  double es = 0.0, ec = 0.0;
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) neumaier_add(es, ec, e[i]);
+  const double e1 = block_sum(es + ec, red);
+  const int conv = allow_converge && st->have_prev && dm < tol && fabs(e1 - st->e_prev) < etol;
+  __syncthreads();
+  if (threadIdx.x == 0) { st->diff = dm; st->e1 = e1; st->converged = conv; st->e_prev = e1; st->have_prev = 1; }
+  if (conv) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xo[i];
+    return;
+  }
+  int hcount = st->hcount, hhead = st->hhead;
+  const int step = st->count;
+  if (step > 0) {
+    double nn = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double d = (xo[i] - x[i]) - pF[i];
+      nn += d * d;
+    }
+    const double norm = sqrt(block_sum(nn, red));
+    if (norm > 0.0) {
+      const int slot = (hhead + hcount) % kHist;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = ((xo[i] - x[i]) - pF[i]) / norm;
+        dF[(size_t)slot * n + i] = d;
+        U[(size_t)slot * n + i] = alpha * d + (x[i] - px[i]) / norm;
+      }
+      if (hcount < kHist) ++hcount; else hhead = (hhead + 1) % kHist;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { px[i] = x[i]; pF[i] = xo[i] - x[i]; }
+  __syncthreads();
+  const int m = hcount;
+  double* a = sa;
+  double* c = sa + kHist * kHist;
+  double* gv = c + kHist;
+  for (int q = 0; q < m * m + m; ++q) {
+    double v = 0.0;
+    if (q < m * m) {
+      const int k = (hhead + q / m) % kHist, l = (hhead + q % m) % kHist;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) v += dF[(size_t)k * n + i] * dF[(size_t)l * n + i];
+    } else {
+      const int k = (hhead + (q - m * m)) % kHist;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) v += dF[(size_t)k * n + i] * pF[i];
+    }
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) { if (q < m * m) a[q] = v; else c[q - m * m] = v; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && m > 0) {
+    double M[kHist][kHist + 1];
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < m; ++j) M[i][j] = a[i * m + j] + (i == j ? w0 * w0 : 0.0);
+      M[i][m] = c[i];
+    }
+    for (int col = 0; col < m; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < m; ++r) if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+      if (piv != col) for (int j = 0; j <= m; ++j) { const double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
+      const double d = M[col][col];
+      for (int r = 0; r < m; ++r) {
+        if (r == col) continue;
+        const double f = M[r][col] / d;
+        for (int j = col; j <= m; ++j) M[r][j] -= f * M[col][j];
+      }
+    }
+    for (int i = 0; i < m; ++i) gv[i] = M[i][m] / M[i][i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = x[i] + alpha * (xo[i] - x[i]);
+    for (int k = 0; k < m; ++k) v -= gv[k] * U[(size_t)((hhead + k) % kHist) * n + i];
+    x[i] = v;
+  }
+  if (threadIdx.x == 0) { st->hcount = hcount; st->hhead = hhead; st->count = step + 1; }
+}
+
 // max |a - b| over a vector (single block).
 __global__ void maxdiff_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
                                double* __restrict__ out) {
@@ -942,12 +1068,6 @@ __global__ void maxdiff_kernel(int n, const double* __restrict__ a, const double
   if (threadIdx.x == 0) *out = m;
 }
 
-// Neumaier-compensated sum of one thread's strided subset, then a fixed tree.
-__device__ void neumaier_add(double& s, double& c, double x) {
-  const double t = s + x;
-  if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
-  s = t;
-}
 
 __device__ double block_sum_compensated(double s, double c, double* red) {
   // combine (s + c) pairs with a fixed-shape tree
@@ -1095,7 +1215,8 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.phi = L.phi; ar.dq_mono = L.dq_mono; ar.esp = L.esp; ar.dq = L.dq; ar.eps = L.eps; ar.hist = L.hist;
   ar.energy = L.energy; ar.e_el = L.e_el; ar.e_rep = L.e_rep; ar.dEV = L.dEV; ar.iters = L.iters; ar.iters32 = L.iters32;
   ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
-  ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap; ar.tol = L.tol; ar.etol = L.etol;
+  ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
+  ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho; ar.tol = L.tol; ar.etol = L.etol;
   ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
   ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
   ar.max_n = L.max_n; ar.max_nsh = L.max_nsh; ar.max_nat = L.max_nat;
@@ -1142,6 +1263,16 @@ cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const 
   LAUNCH_CHECK();
   return cudaSuccess;
 }
+
+cudaError_t launch_global_mix(cudaStream_t st, int n, double* x, const double* xo, int nf, const double* e,
+                              double* hist, void* state, double tol, double etol, int allow_converge) {
+  global_mix_kernel<<<1, 1024, 0, st>>>(n, x, xo, nf, e, hist, (MixState*)state, 0.4, 0.01, tol, etol,
+                                         allow_converge);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+size_t mix_state_bytes() { return sizeof(MixState); }
 
 cudaError_t launch_maxdiff(cudaStream_t st, int n, const double* a, const double* b, double* out) {
   maxdiff_kernel<<<1, 1024, 0, st>>>(n, a, b, out);

@@ -50,6 +50,9 @@ struct SccLaunch {
   int precision;
   int max_iter;
   int fp32_cap;
+  int single_step;
+  int step_phase;
+  int reortho;
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
   const unsigned long long* t0;   // device timestamp of the run start
@@ -79,6 +82,9 @@ cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const 
                          const double* xyz, const int* sh_atom, const double* sh_inv_eta, const double* dq,
                          GParams g, double* out);
 cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t);
+cudaError_t launch_global_mix(cudaStream_t st, int n, double* x, const double* xo, int nf, const double* e,
+                              double* hist, void* state, double tol, double etol, int allow_converge);
+size_t mix_state_bytes();
 cudaError_t launch_maxdiff(cudaStream_t st, int n, const double* a, const double* b, double* out);
 cudaError_t launch_fmo_sum(cudaStream_t st, int n_frag, const double* e_mono, long long n_pair, const int* pair_scc,
                            const double* e_dim, const double* dEV_dim, double* dE_pair, int n_tri,

@@ -52,7 +52,7 @@ class FmoParams(C.Structure):
 class FmoOptions(C.Structure):
     _fields_ = [("level", C.c_int32), ("precision", C.c_int32), ("all_dimers_scc", C.c_int32),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("guess", C.c_int32),
-                ("schedule", C.c_int32), ("reserved_", C.c_int32), ("dimer_cut", C.c_double),
+                ("schedule", C.c_int32), ("monomer_loop", C.c_int32), ("dimer_cut", C.c_double),
                 ("trimer_cut", C.c_double), ("scc_tol", C.c_double), ("e_tol", C.c_double),
                 ("outer_tol", C.c_double), ("mixed_switch_tol", C.c_double),
                 ("deadline_s", C.c_double)]
@@ -162,6 +162,8 @@ def options(**kw) -> FmoOptions:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[v]
+        if k == "monomer_loop" and isinstance(v, str):
+            v = {"global": 0, "nested": 1}[v]
         setattr(o, k, v)
     return o
 

@@ -57,6 +57,12 @@ def test_water8_fmo2_all_dimers_fp64(gpu, params, water64):
     compare(run_gpu(gpu, s, all_dimers_scc=1), ref)
 
 
+def test_water8_nested_monomer_loop_fp64(gpu, params, water64):
+    s = water64.subsystem(range(8))
+    ref = ofmo.fmo(s, params, ofmo.FMOOptions(all_dimers_scc=True, monomer_loop="nested"))
+    compare(run_gpu(gpu, s, all_dimers_scc=1, monomer_loop="nested"), ref)
+
+
 def test_water12_fmo2_esdim_fp64(gpu, params, water64):
     # the 4.0 A rule splits the pairs into SCC dimers and ES-DIM pairs
     s = water64.subsystem(range(12))
@@ -124,3 +130,19 @@ def test_new_coordinates_same_topology(gpu, params, water64):
     gpu.set_coordinates(s2.xyz)
     gpu.run(fmo.options(all_dimers_scc=1))
     compare(gpu, ref)
+
+
+def test_anthracene32_monomer_loop_fp64_and_mixed(gpu, params):
+    # a cluster large enough that plain nested monomer iterations converge
+    # slowly: the global loop must reach the oracle's fixed point
+    from paper_2606_28022_b300 import fmo
+    s, _ = G.anthracene_cluster(128, 2)
+    s = s.subsystem(range(32))
+    ref = ofmo.fmo(s, params, ofmo.FMOOptions(level=1, dimer_cut=0.0))
+    gpu.set_system(s)
+    gpu.run(fmo.options(level=1))
+    mono = gpu.monomers()
+    assert np.max(np.abs(mono.energy - ref.e_mono)) < E_FRAG
+    assert np.max(np.abs(mono.shell_dq - np.concatenate(ref.dq_mono))) < DQ
+    gpu.run(fmo.options(level=1, precision="mixed"))
+    assert abs(gpu.energies()[0] - ref.e_fmo1) < E_TOT_MIXED

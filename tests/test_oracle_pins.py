@@ -355,12 +355,29 @@ def test_fmo_error_small_and_fmo3_better(params, water64):
     assert abs(r.e_fmo1 - full.energy) / 6 > 10 * e2
 
 
-def test_monomer_loop_fixed_point_independent_of_order(params, water64):
+@pytest.mark.parametrize("loop", ["nested-jacobi", "nested-gauss-seidel"])
+def test_monomer_loop_fixed_point_independent_of_order(params, water64, loop):
+    # READING C-9: how the monomer charges are iterated does not change the
+    # fixed point the paper defines (every monomer self-consistent in the ESP
+    # of all others)
     s = water64.subsystem([0, 1, 2, 3, 4])
-    a = fmo.fmo(s, params, fmo.FMOOptions(all_dimers_scc=True))
-    b = fmo.fmo(s, params, fmo.FMOOptions(all_dimers_scc=True, gauss_seidel=True))
+    a = fmo.fmo(s, params, fmo.FMOOptions(all_dimers_scc=True))          # global Broyden loop
+    b = fmo.fmo(s, params, fmo.FMOOptions(all_dimers_scc=True, monomer_loop="nested",
+                                          gauss_seidel=(loop == "nested-gauss-seidel")))
     assert a.e_fmo2 == pytest.approx(b.e_fmo2, abs=1e-9)
     assert np.allclose(np.concatenate(a.dq_mono), np.concatenate(b.dq_mono), atol=1e-9)
+
+
+def test_monomer_charges_are_self_consistent(params, water64):
+    # at the fixed point each monomer's SCC, solved alone in the ESP of the
+    # other monomers' final charges, reproduces its own charges
+    s = water64.subsystem(range(6))
+    r = fmo.fmo(s, params, fmo.FMOOptions(level=1, dimer_cut=0.0))
+    fr = fmo._Frags(s, params)
+    for I in (0, 3, 5):
+        alone = fr.solve((I,), fr.esp((I,), r.dq_mono), None, fmo.FMOOptions())
+        assert np.allclose(alone.dq, r.dq_mono[I], atol=1e-9)
+        assert alone.energy == pytest.approx(r.e_mono[I], abs=1e-9)
 
 
 def test_esdim_matches_scc_dimer_for_a_far_pair(params, water64):
