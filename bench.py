@@ -40,9 +40,11 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # FP32 FMA lanes x 2 flop
 FP64_PEAK_TFLOPS = 1.25                                 # nominal B300 FP64 rate
 
 
-def workload(rank: int):
+def workload(rank: int, n_mol: int = 128):
     from paper_2606_28022_b300.inputs import geometry as G
     system, info = G.anthracene_cluster(128, seed=2)
+    if n_mol < 128:                   # a smaller case (profiling): the first n_mol molecules
+        system = system.subsystem(range(n_mol))
     if rank > 0:                      # weak scaling: every rank its own jittered frame
         system = G.jittered(system, 0.02, 5000 + rank)
     return system, info
@@ -161,6 +163,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-mol", type=int, default=128,
+                    help="anthracenes in the workload (128 = the benchmark; fewer for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -186,7 +190,7 @@ def main():
         dist.barrier()
 
     params = synthetic_gfn1_table()
-    system, geo = workload(rank)
+    system, geo = workload(rank, args.n_mol)
     g = fmo.FMO(params, dev.index)
     g.set_system(system)
     stream = torch.cuda.current_stream(dev)
@@ -303,7 +307,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-                "config": {"workload": "anthracene128-FMO2: 128 C14H10 (3072 atoms), seeded herringbone "
+                "config": {"workload": f"anthracene{system.n_frag}-FMO2: {system.n_frag} C14H10 ({system.n_atoms} atoms), seeded herringbone "
                                        "a=8.56 b=6.04 c=11.16 A beta=124.7, 0.05 A jitter; SCC dimer iff "
                                        "closest atom < 4.0 A, else ES-DIM",
                            "precision": args.precision, "n_frag": system.n_frag,

@@ -14,6 +14,7 @@
 
 #include "../../include/fmo_xtb.h"
 #include "kernels.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace fmo;
 
@@ -108,7 +109,7 @@ struct fmo_ctx {
   std::vector<double> f_nel, h_sh_inv_eta;
   DevBuf d_xyz, d_xyz_in, d_perm, d_elem, d_cn, d_atom_sh0, d_sh_atom, d_sh_inv_eta;
   DevBuf d_f_atom0, d_f_nat, d_f_sh0, d_f_nsh, d_f_ao0, d_f_nao;
-  DevBuf d_dq_mono, d_phi, d_bounds, d_rmin, d_scalar, d_t0, d_mix_hist, d_mix_state;
+  DevBuf d_dq_mono, d_phi, d_phi_part, d_bounds, d_rmin, d_scalar, d_t0, d_mix_hist, d_mix_state;
   DevBuf d_pair_scc, d_dE_pair, d_esdim_pairs, d_esdim_idx, d_tri_frag, d_dE3, d_corr, d_totals;
   std::vector<double> guess;
   bool have_guess = false;
@@ -387,6 +388,14 @@ void stage(cudaStream_t st, const char* what, int k = -1) {
   fflush(stderr);
 }
 
+// NVTX range of the current stage of fmo_run (closed on every return path).
+struct StageRange {
+  bool open = false;
+  void set(const char* name) { end(); nvtxRangePushA(name); open = true; }
+  void end() { if (open) nvtxRangePop(); open = false; }
+  ~StageRange() { end(); }
+};
+
 double now_ms(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
@@ -450,7 +459,7 @@ void fmo_destroy(fmo_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
                     &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
-                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_dq_mono, &ctx->d_phi,
+                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
                     &ctx->d_totals})
@@ -592,6 +601,7 @@ fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const
   CK(upload(ctx->d_f_nao, ctx->f_nao, st));
   CK(ctx->d_dq_mono.ensure(sizeof(double) * sh));
   CK(ctx->d_phi.ensure(sizeof(double) * sh));
+  CK(ctx->d_phi_part.ensure(sizeof(double) * sh * (size_t)(phi_chunks(sh) + 1)));
   CK(ctx->d_bounds.ensure(sizeof(double) * 4 * n_frag));
   CK(ctx->d_scalar.ensure(sizeof(double) * 8));
   CK(ctx->d_t0.ensure(sizeof(unsigned long long)));
@@ -660,6 +670,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   cudaEvent_t ev[8];
   for (auto& e : ev) cudaEventCreate(&e);
   cudaEventRecord(ev[0], st);
+  StageRange sr;
+  sr.set("fmo_setup");
   CK(launch_stamp(st, ctx->d_t0.as<unsigned long long>()));
   // ---- coordination numbers of the whole system
   CK(launch_cn(st, ctx->n_atoms, ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(), ctx->d_el.as<DevElem>(), ctx->g,
@@ -682,6 +694,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (o.guess == 2) CK(h2d(ctx->d_dq_mono.p, ctx->guess.data(), sizeof(double) * ctx->n_sh, st));
   else CK(cudaMemsetAsync(ctx->d_dq_mono.p, 0, sizeof(double) * ctx->n_sh, st));
   cudaEventRecord(ev[1], st);
+  sr.set("fmo_monomers");
   double change = 1e300;
   int outer = 0;
   double h_change_v = 0.0;
@@ -697,7 +710,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     struct { double e_prev, diff, e1; int have_prev, hcount, hhead, converged, count; } hs{};
     for (outer = 1; outer <= o.max_outer; ++outer) {
       CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>()));
+                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
       stage(st, "phi", outer);
       fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 1, phase, reortho);
       if (fs != FMO_OK) return fs;
@@ -722,7 +735,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   } else {
   for (outer = 1; outer <= o.max_outer; ++outer) {
     CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                  ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>()));
+                  ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
     stage(st, "phi", outer);
     fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st);
     if (fs != FMO_OK) return fs;
@@ -743,9 +756,10 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   ctx->stats.outer_iterations = outer;
   // frozen ESP of the final monomer charges
   CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>()));
+                ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
   ctx->stats.kernel_launches += 1;
   cudaEventRecord(ev[2], st);
+  sr.set("fmo_select");
   // ---- n-mer selection
   const long long npair = (long long)nf * (nf - 1) / 2;
   std::vector<double> rmin(npair);
@@ -792,6 +806,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     }
   }
   cudaEventRecord(ev[3], st);
+  sr.set("fmo_dimers");
   stage(st, "selection", int(dim_tu.size()));
   ctx->stats.n_dimer_scc = (long long)dim_tu.size();
   ctx->stats.n_dimer_esdim = (long long)es_pairs.size();
@@ -821,6 +836,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     ctx->stats.kernel_launches += 1;
   }
   cudaEventRecord(ev[4], st);
+  sr.set("fmo_trimers");
   stage(st, "esdim", int(es_pairs.size()));
   // ---- SCC trimers
   CK(plan_pass(ctx, ctx->tri, tri_tu, tri_nf, false, o.precision, st));
@@ -839,6 +855,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   CK(ctx->d_dE3.ensure(sizeof(double) * std::max<size_t>(tri_tu.size(), 1)));
   CK(ctx->d_corr.ensure(sizeof(double) * std::max<size_t>(tri_tu.size(), 1)));
   cudaEventRecord(ev[5], st);
+  sr.set("fmo_sums");
   // ---- FMO sums
   CK(launch_fmo_sum(st, nf, ctx->mono.energy.as<double>(), o.level >= 2 ? npair : 0, ctx->d_pair_scc.as<int>(),
                     ctx->dim.energy.as<double>(), ctx->dim.dEV.as<double>(), ctx->d_dE_pair.as<double>(),
@@ -879,6 +896,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     CK(d2h(it_tri.data(), ctx->tri.iters.p, sizeof(int) * ntri, st));
   }
   cudaEventRecord(ev[6], st);
+  sr.end();
   CK(sync_stream(st));
   ctx->stats.ms_setup = now_ms(ev[0], ev[1]);
   ctx->stats.ms_monomer = now_ms(ev[1], ev[2]);

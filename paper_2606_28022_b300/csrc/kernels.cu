@@ -188,10 +188,20 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
   }
 }
 
+// x^(-1/2) in FP64 from the FP32 hardware estimate and two Newton-Raphson
+// steps y <- y (3 - x y^2) / 2 (each squares the relative error: ~1e-7 ->
+// ~1e-14 -> rounding level).  x must be a positive normal FP32 number.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+
 // gamma of Eqs. 4-5 from the distance and the two shell hardnesses.
 __device__ __forceinline__ double gamma_fn(double r2, double inv_eta_a, double inv_eta_b, double kg) {
   const double ie = 0.5 * (inv_eta_a + inv_eta_b);   // 1/eta, eta = harmonic mean
-  if (kg == 2.0) return 1.0 / sqrt(r2 + ie * ie);
+  if (kg == 2.0) return rsqrt_nr(r2 + ie * ie);
   return pow(pow(sqrt(r2), kg) + pow(ie, kg), -1.0 / kg);
 }
 
@@ -832,40 +842,59 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
 // ---------------------------------------------------------------------------
 // Supersystem potential phi_mu = sum_lambda gamma_mu,lambda dq_lambda over all
 // shells (the ESP of Eq. 21 before the fragment's own shells are removed).
+// Grid: blockIdx.x selects 256 target shells mu, blockIdx.y a chunk of source
+// shells lambda staged through shared memory; each chunk writes its partial
+// sums, which phi_reduce_kernel adds in chunk order (deterministic).
 
-__global__ void phi_kernel(int n_sh, const double* __restrict__ xyz, const int* __restrict__ sh_atom,
-                           const double* __restrict__ sh_inv_eta, const double* __restrict__ dq,
-                           GParams g, double* __restrict__ phi) {
+__global__ void __launch_bounds__(256) phi_kernel(int n_sh, int chunk, const double* __restrict__ xyz,
+                                                  const int* __restrict__ sh_atom,
+                                                  const double* __restrict__ sh_inv_eta,
+                                                  const double* __restrict__ dq, GParams g,
+                                                  double* __restrict__ part) {
   __shared__ double tx[256], ty[256], tz[256], te[256], tq[256];
   const int mu = blockIdx.x * blockDim.x + threadIdx.x;
-  double x = 0, y = 0, z = 0, ie = 0;
+  double x = 0, y = 0, z = 0, ie = 1.0;
   if (mu < n_sh) {
     const int a = sh_atom[mu];
     x = xyz[3 * a]; y = xyz[3 * a + 1]; z = xyz[3 * a + 2];
     ie = sh_inv_eta[mu];
   }
+  const int l0 = blockIdx.y * chunk, l1 = min(n_sh, l0 + chunk);
   double acc = 0.0;
-  for (int t0 = 0; t0 < n_sh; t0 += 256) {
+  for (int t0 = l0; t0 < l1; t0 += 256) {
     const int l = t0 + threadIdx.x;
-    if (l < n_sh) {
+    if (l < l1) {
       const int b = sh_atom[l];
       tx[threadIdx.x] = xyz[3 * b]; ty[threadIdx.x] = xyz[3 * b + 1]; tz[threadIdx.x] = xyz[3 * b + 2];
       te[threadIdx.x] = sh_inv_eta[l];
       tq[threadIdx.x] = dq[l];
-    } else {
-      tx[threadIdx.x] = ty[threadIdx.x] = tz[threadIdx.x] = 0.0;
-      te[threadIdx.x] = 1.0;
-      tq[threadIdx.x] = 0.0;
     }
     __syncthreads();
-    const int m = min(256, n_sh - t0);
-    for (int k = 0; k < m; ++k) {
-      const double dx = x - tx[k], dy = y - ty[k], dz = z - tz[k];
-      acc += gamma_fn(dx * dx + dy * dy + dz * dz, ie, te[k], g.k_g) * tq[k];
+    const int m = min(256, l1 - t0);
+    if (g.k_g == 2.0) {
+      for (int k = 0; k < m; ++k) {
+        const double dx = x - tx[k], dy = y - ty[k], dz = z - tz[k];
+        const double e = 0.5 * (ie + te[k]);
+        acc = fma(rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, e * e)))), tq[k], acc);
+      }
+    } else {
+      for (int k = 0; k < m; ++k) {
+        const double dx = x - tx[k], dy = y - ty[k], dz = z - tz[k];
+        acc += gamma_fn(dx * dx + dy * dy + dz * dz, ie, te[k], g.k_g) * tq[k];
+      }
     }
     __syncthreads();
   }
-  if (mu < n_sh) phi[mu] = acc;
+  if (mu < n_sh) part[(size_t)blockIdx.y * n_sh + mu] = acc;
+}
+
+__global__ void phi_reduce_kernel(int n_sh, int n_chunk, const double* __restrict__ part,
+                                  double* __restrict__ phi) {
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu >= n_sh) return;
+  double s = 0.0;
+  for (int c = 0; c < n_chunk; ++c) s += part[(size_t)c * n_sh + mu];
+  phi[mu] = s;
 }
 
 // Fragment centroids and bounding radii (for pruning the pair search).
@@ -1230,9 +1259,21 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   return cudaSuccess;
 }
 
+// Source-shell chunking of the phi kernel: enough blocks for 4 per SM.
+int phi_chunks(int n_sh) {
+  const int mu_blocks = (n_sh + 255) / 256;
+  const int want = (4 * 148 + mu_blocks - 1) / mu_blocks;
+  return std::max(1, std::min(want, (n_sh + 255) / 256));
+}
+
 cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
-                       const double* dq, GParams g, double* phi) {
-  phi_kernel<<<(n_sh + 255) / 256, 256, 0, st>>>(n_sh, xyz, sh_atom, sh_inv_eta, dq, g, phi);
+                       const double* dq, GParams g, double* phi, double* part) {
+  const int nc = phi_chunks(n_sh);
+  const int chunk = (((n_sh + nc - 1) / nc) + 255) / 256 * 256;
+  const int ncu = (n_sh + chunk - 1) / chunk;
+  phi_kernel<<<dim3((n_sh + 255) / 256, ncu), 256, 0, st>>>(n_sh, chunk, xyz, sh_atom, sh_inv_eta, dq, g, part);
+  LAUNCH_CHECK();
+  phi_reduce_kernel<<<(n_sh + 255) / 256, 256, 0, st>>>(n_sh, ncu, part, phi);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

@@ -73,8 +73,9 @@ cudaError_t launch_lowdin(cudaStream_t st, int n_nmer, int max_n, const Nmer* nm
                           void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status);
 size_t scc_smem_size(int max_n, int max_nsh, int max_nat, int a_bytes);
 cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L);
+int phi_chunks(int n_sh);
 cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
-                       const double* dq, GParams g, double* phi);
+                       const double* dq, GParams g, double* phi, double* part);
 cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);
 cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, const double* bounds,
                                  double cut, double* rmin);
