@@ -225,6 +225,44 @@ fmo_status fmo_get_trimers(fmo_ctx *ctx, int64_t *n, int32_t *ijk, double *dE3, 
 
 fmo_status fmo_get_stats(fmo_ctx *ctx, fmo_stats *st);
 
+/*
+ * SCC solve of one molecule that allocates no device memory.
+ *
+ * For callers that cannot allocate device memory while they run: work being
+ * captured into a CUDA graph, real-time loops that forbid allocation after
+ * start-up, or hosts whose memory manager owns all device memory.  The paper
+ * has no counterpart; it is a packaging of the library's own kernels.
+ *
+ * Solves the GFN1-xTB SCC of one closed-shell molecule (one fragment) from a
+ * neutral guess, optionally in an external shell potential, with the table
+ * *p and the tolerances, iteration limit and precision of *opt.  Results
+ * equal those of fmo_run on a one-fragment system (E_I and shell charges).
+ *   Z[n_atoms]           host atomic numbers (1 <= n_atoms <= 128)
+ *   xyz_dev[3*n_atoms]   device coordinates (bohr), atom-major
+ *   charge               net charge of the molecule (e)
+ *   esp_dev[n_shell]     device external potential per shell (Eh/e), or NULL
+ *   energy_dev[1]        device output: E = E_el + E_rep (Eh)
+ *   shell_dq_dev[n_shell] device output: shell charges, table order per atom
+ *   status_dev[1]        device output (or NULL): FMO_SCC_* word
+ *   cuda_stream          stream for all work (NULL: the legacy default stream)
+ *   err[err_len]         host buffer for a message (or NULL)
+ * Limits: at most 256 basis functions, 128 shells and 128 atoms; larger
+ * molecules return FMO_ERR_ARG with a message.  The call only enqueues work:
+ * read the outputs after the stream has finished.
+ * Memory: all scratch (about 4.5 MiB) is one fixed device array that every
+ * GPU loading the library holds until the process exits.  The first call on
+ * a device looks up that array's device address; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (other streams, other
+ * host threads) race: serialise them.
+ * Errors: FMO_ERR_ARG (NULL pointers, sizes, open shell, unknown element),
+ * FMO_ERR_UNSUPPORTED, FMO_ERR_CUDA (launch or copy failure).
+ */
+fmo_status fmo_scc_solve_noalloc(const fmo_params *p, int32_t n_atoms, const int32_t *Z,
+                                 const double *xyz_dev, int32_t charge, const double *esp_dev,
+                                 const fmo_options *opt, double *energy_dev, double *shell_dq_dev,
+                                 int32_t *status_dev, void *cuda_stream, char *err, int32_t err_len);
+
 /* Message of the last error on this context ("" if none). */
 const char *fmo_last_error(const fmo_ctx *ctx);
 
