@@ -122,6 +122,14 @@ typedef struct fmo_options {
   double outer_tol;         /* monomer loop: max charge change (e) */
   double mixed_switch_tol;  /* mixed: FP32 until max |dq_out - dq_in| < this */
   double deadline_s;        /* wall-clock limit per fmo_run, 0 = none */
+  int32_t mixed_finish;     /* mixed precision, dimers and trimers: FP64
+                               iterations after the FP32 phase (0: converge in
+                               FP64 to scc_tol/e_tol).  Their interaction
+                               energies are variational in the n-mer density
+                               (the ESP is fixed), so the FP64 energy of the
+                               FP32-converged charges is off only to second
+                               order in the FP32 charge error. */
+  int32_t reserved_;
 } fmo_options;
 
 /* Counters of the last fmo_run. */
@@ -150,7 +158,8 @@ typedef struct fmo_stats {
 typedef struct fmo_ctx fmo_ctx;
 
 /* Fill *o with the defaults: level 2, FP64, ES-DIM on, cut 4.0 A, tolerances
- * 1e-10, max_iter 300, max_outer 200, switch 1e-5, no deadline. */
+ * 1e-10, max_iter 300, max_outer 200, switch 1e-5, one FP64 finishing
+ * iteration for mixed-precision dimers and trimers, no deadline. */
 void fmo_options_default(fmo_options *o);
 
 /* Create a context on CUDA device `device` with a copy of the table *p.

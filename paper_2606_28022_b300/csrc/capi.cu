@@ -109,7 +109,7 @@ struct fmo_ctx {
   std::vector<double> f_nel, h_sh_inv_eta;
   DevBuf d_xyz, d_xyz_in, d_perm, d_elem, d_cn, d_atom_sh0, d_sh_atom, d_sh_inv_eta;
   DevBuf d_f_atom0, d_f_nat, d_f_sh0, d_f_nsh, d_f_ao0, d_f_nao;
-  DevBuf d_dq_mono, d_phi, d_phi_part, d_bounds, d_rmin, d_scalar, d_t0, d_mix_hist, d_mix_state;
+  DevBuf d_trace, d_dq_mono, d_phi, d_phi_part, d_bounds, d_rmin, d_scalar, d_t0, d_mix_hist, d_mix_state;
   DevBuf d_pair_scc, d_dE_pair, d_esdim_pairs, d_esdim_idx, d_tri_frag, d_dE3, d_corr, d_totals;
   std::vector<double> guess;
   bool have_guess = false;
@@ -310,8 +310,24 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
   return FMO_OK;
 }
 
+// FMO_DEBUG=1 in the environment: synchronise after each stage of fmo_run and
+// report it on stderr (diagnostics only; the computation is unchanged).
+int debug_level() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("FMO_DEBUG"); v = (e && e[0] >= '1' && e[0] <= '9') ? e[0] - '0' : 0; }
+  return v;
+}
+bool debug_on() { return debug_level() >= 1; }
+void stage(cudaStream_t st, const char* what, int k = -1) {
+  if (!debug_on()) return;
+  cudaError_t e = sync_stream(st);
+  fprintf(stderr, "[fmo] %s %d: %s\n", what, k, cudaGetErrorString(e));
+  fflush(stderr);
+}
+
 fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& sp, bool with_phi,
-                   int pass_id, cudaStream_t st, int single_step = 0, int step_phase = 1, int reortho = 0) {
+                   int pass_id, cudaStream_t st, int single_step = 0, int step_phase = 1, int reortho = 0,
+                   int cold = 1, int reortho32 = 0, double jac_hint = 1.0) {
   const int nn = int(P.nm.size());
   if (nn == 0) return FMO_OK;
   SccLaunch L{};
@@ -334,6 +350,17 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.single_step = single_step;
   L.step_phase = step_phase;
   L.reortho = reortho;
+  L.cold_refine = cold;
+  L.reortho32 = reortho32;
+  L.jac_hint = jac_hint;
+  L.fp64_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED) ? std::max(0, o.mixed_finish) : 0;
+  L.trace = nullptr;
+  const bool tracing = debug_level() >= 2 && pass_id == 1;
+  if (tracing) {
+    CK(ctx->d_trace.ensure(sizeof(double) * 512));
+    CK(cudaMemsetAsync(ctx->d_trace.p, 0, sizeof(double) * 512, st));
+    L.trace = ctx->d_trace.as<double>();
+  }
   L.tol = o.scc_tol; L.etol = o.e_tol; L.switch_tol = o.mixed_switch_tol;
   L.jacobi_tol_d = 1e-14;
   L.jacobi_tol_f = 2e-7;
@@ -362,6 +389,14 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->stats.ms_scc[pass_id] += ms;
+  if (tracing) {
+    std::vector<double> tr(512);
+    CK(d2h(tr.data(), ctx->d_trace.p, sizeof(double) * 512, st));
+    CK(sync_stream(st));
+    fprintf(stderr, "[fmo] residual per iteration (first dimer; negative = FP32):");
+    for (int i = 1; i < 512 && tr[i] != 0.0; ++i) fprintf(stderr, " %.1e", tr[i]);
+    fprintf(stderr, "\n");
+  }
   ctx->stats.scc_launches[pass_id] += 1;
   for (int i = 0; i < nn; ++i) {
     const double n3 = 15.0 * double(P.nm[i].n) * P.nm[i].n * P.nm[i].n;
@@ -372,20 +407,6 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
     ctx->stats.flops_fp64[pass_id] += n3 * i64;
   }
   return FMO_OK;
-}
-
-// FMO_DEBUG=1 in the environment: synchronise after each stage of fmo_run and
-// report it on stderr (diagnostics only; the computation is unchanged).
-bool debug_on() {
-  static int v = -1;
-  if (v < 0) { const char* e = getenv("FMO_DEBUG"); v = (e && e[0] == '1') ? 1 : 0; }
-  return v == 1;
-}
-void stage(cudaStream_t st, const char* what, int k = -1) {
-  if (!debug_on()) return;
-  cudaError_t e = sync_stream(st);
-  fprintf(stderr, "[fmo] %s %d: %s\n", what, k, cudaGetErrorString(e));
-  fflush(stderr);
 }
 
 // NVTX range of the current stage of fmo_run (closed on every return path).
@@ -423,6 +444,7 @@ void fmo_options_default(fmo_options* o) {
   o->e_tol = 1e-10;
   o->outer_tol = 1e-10;
   o->mixed_switch_tol = 1e-5;
+  o->mixed_finish = 1;
   o->deadline_s = 0.0;
 }
 
@@ -459,7 +481,7 @@ void fmo_destroy(fmo_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
                     &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
-                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
+                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
                     &ctx->d_totals})
@@ -712,7 +734,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
                     ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
       stage(st, "phi", outer);
-      fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 1, phase, reortho);
+      fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 1, phase, reortho, outer == 1 ? 1 : 0,
+                   (phase == 0 && outer > 1 && outer % 4 == 0) ? 1 : 0, outer == 1 ? 1.0 : hs.diff);
       if (fs != FMO_OK) return fs;
       reortho = 0;
       CK(launch_global_mix(st, ctx->n_sh, ctx->d_dq_mono.as<double>(), ctx->mono.dq.as<double>(), nf,
@@ -728,7 +751,10 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       if (phase == 0 && (hs.diff < o.mixed_switch_tol || ++n32 >= cap32)) {
         phase = 1;
         reortho = 1;
-        CK(cudaMemsetAsync(ctx->d_mix_state.p, 0, mix_state_bytes(), st));
+        // keep the Broyden history, but form no secant across the hand-over
+        // (clear have_prev and the step count of the mixer state)
+        CK(cudaMemsetAsync((char*)ctx->d_mix_state.p + 3 * sizeof(double), 0, sizeof(int), st));
+        CK(cudaMemsetAsync((char*)ctx->d_mix_state.p + 3 * sizeof(double) + 4 * sizeof(int), 0, sizeof(int), st));
       }
     }
     ctx->stats.n_monomer_solves = nf;
@@ -737,7 +763,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
                   ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
     stage(st, "phi", outer);
-    fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st);
+    fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 0, 1, 0, outer == 1 ? 1 : 0);
     if (fs != FMO_OK) return fs;
     stage(st, "monomer scc", outer);
     CK(launch_maxdiff(st, ctx->n_sh, ctx->mono.dq.as<double>(), ctx->d_dq_mono.as<double>(),

@@ -9,7 +9,10 @@ namespace fmo {
 constexpr int kMaxShell = 3;
 constexpr int kMaxPrim = 12;
 constexpr int kMaxElem = 16;      // distinct elements in one system
-constexpr int kHist = 8;          // Broyden history length
+#ifndef FMO_HIST
+#define FMO_HIST 8
+#endif
+constexpr int kHist = FMO_HIST;   // Broyden history length
 constexpr int kBlock = 256;       // threads of the SCC kernels
 
 // One element of the table, compacted to the elements present.  cn[][] holds
@@ -124,13 +127,14 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // ---------------------------------------------------------------------------
 // Block-level GEMM: C[m][n] = sum_k a(m,k) * b(n,k) with
 //   a(m,k) = A[m*sam + kk*sak] * (kscale ? kscale[k] : 1),
-//   b(n,k) = B[n*sbn + kk*sbk],   kk = kidx ? kidx[k] : k.
+//   b(n,k) = B[n*sbn + kk*sbk],   kk = kidx ? kidx[k] : k
+// (B may be stored in a wider type TB; it is rounded to T on load).
 // 64x64 output tiles, BK = 16, 256 threads with 4x4 outputs each.  Operand
 // tiles are staged in shared memory (smem: 2*16*64 elements of T).
 
-template <typename T>
+template <typename T, typename TB = T>
 __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long long sam,
-                           long long sak, const T* __restrict__ B, long long sbn, long long sbk,
+                           long long sak, const TB* __restrict__ B, long long sbn, long long sbk,
                            T* __restrict__ C, long long ldc, const int* __restrict__ kidx,
                            const double* __restrict__ kscale, T* smem) {
   constexpr int BM = 64, BN = 64, BK = 16;
@@ -171,7 +175,7 @@ __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long lo
           T v = T(0);
           if (gn < N && gk < K) {
             const long long kr = kidx ? kidx[gk] : gk;
-            v = B[gn * sbn + kr * sbk];
+            v = T(B[gn * sbn + kr * sbk]);
           }
           Bs[kk * BN + nn] = v;
         }

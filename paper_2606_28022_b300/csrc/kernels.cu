@@ -322,6 +322,11 @@ struct SccArgs {
   int single_step;   // 1: exactly one SCC iteration, no mixing (global monomer loop)
   int step_phase;    // single step: 0 FP32, 1 FP64
   int reortho;       // single step: carry the FP32 vectors over to FP64 first
+  int cold_refine;   // the vectors are the Loewdin start: restore S-orthonormality in FP64 first
+  int reortho32;     // single step: one FP32 Newton-Schulz step before the iteration
+  double jac_hint;   // SCC residual before this launch (sets the first Jacobi threshold)
+  int fp64_finish;   // mixed: stop after this many FP64 iterations (0: converge in FP64)
+  double* trace;     // optional: residual per iteration of the first n-mer in the order
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
   const unsigned long long* t0;
@@ -466,15 +471,18 @@ __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_o
 // Modified Broyden mixing (Johnson 1988) of the shell-charge vector, FP64.
 // x_new = x_in + a F - sum_n g_n u_n, F = x_out - x_in, dF/dx normalised
 // differences, u = a dF + dx, (w0^2 I + dF dF^T) g = dF F.
+// With secant = false the step uses the stored history but adds no new pair:
+// the first step after the FP32 -> FP64 hand-over, whose residual difference
+// would mix the two precisions' slightly different fixed points.
 __device__ void broyden_step(int nsh, int it, double* hist, SccSmem& sm, int& hcount, int& hhead,
-                             double alpha, double w0) {
+                             double alpha, double w0, bool secant = true) {
   double* dF = hist;                          // [kHist][nsh]
   double* U = hist + (size_t)kHist * nsh;     // [kHist][nsh]
   double* px = hist + (size_t)2 * kHist * nsh;
   double* pF = px + nsh;
   double* red = sm.red;
   __shared__ double s_norm;
-  if (it > 1) {
+  if (it > 1 && secant) {
     double nn = 0.0;
     for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
       const double F = sm.dqout[i] - sm.dqin[i];
@@ -674,26 +682,36 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
 }
 
 // CT <- (M^{-1/2}) CT with M = CT S CT^T, by Newton-Schulz steps
-// CT <- 1.5 CT - 0.5 M CT (each squares the error of M - I), FP64, until
-// max |M - I| < 1e-14: restores the S-orthonormality of eigenvectors carried
-// over from FP32, whose rotations drift it by up to ~1e-4.
-__device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<double> pp) {
+// CT <- 1.5 CT - 0.5 M CT (each squares the error of M - I), until
+// max |M - I| < tol or max_steps: restores the S-orthonormality of the
+// eigenvector rows (the FP32 Loewdin start, FP32 rotations and the hand-over
+// from FP32 to FP64 all leave it slightly off).
+template <typename T>
+__device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<T> pp, int max_steps,
+                                 double tol) {
   const int n = nm.n;
-  double* gemm = reinterpret_cast<double*>(sm.gemm);
+  T* gemm = reinterpret_cast<T*>(sm.gemm);
   const double* Sm = ar.S + nm.mat;
-  for (int step = 0; step < 4; ++step) {
-    block_gemm<double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, gemm);   // V = CT S
-    block_gemm<double>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.W1, n, nullptr, nullptr, gemm);  // M = V CT^T
+  for (int step = 0; step < max_steps; ++step) {
+    block_gemm<T, double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, gemm);   // V = CT S
+    block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.W1, n, nullptr, nullptr, gemm);       // M = V CT^T
     double err = 0.0;
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
-      err = fmax(err, fabs(pp.W1[e] - ((e / n) == (e % n) ? 1.0 : 0.0)));
+      err = fmax(err, fabs(double(pp.W1[e]) - ((e / n) == (e % n) ? 1.0 : 0.0)));
     err = block_max(err, sm.red);
-    if (err < 1e-14) break;
-    block_gemm<double>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, gemm);  // M CT
+    if (err < tol) break;
+    block_gemm<T>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, gemm);       // M CT
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
-      pp.CT[e] = 1.5 * pp.CT[e] - 0.5 * pp.W2[e];
+      pp.CT[e] = T(1.5) * pp.CT[e] - T(0.5) * pp.W2[e];
     __syncthreads();
   }
+}
+
+// Jacobi threshold (relative to max |A_ii|) for an SCC iteration whose
+// previous residual was `last`: rotations far below the SCC error change
+// nothing the loop needs, so early iterations rotate only the large elements.
+__device__ __forceinline__ double jacobi_threshold(double last, double floor_tol) {
+  return fmax(floor_tol, fmin(1e-4, 1e-3 * last));
 }
 
 __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
@@ -771,25 +789,61 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     // one iteration from the given charges in the given precision; the
     // caller mixes the charges of all monomers together
     phase = ar.step_phase;
-    if (phase == 1 && ar.precision == 1 && ar.reortho) {
+    if ((phase == 1 && ar.precision == 1 && ar.reortho) || (phase == 0 && ar.cold_refine)) {
       for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
       __syncthreads();
-      reorthonormalise(nm, ar, sm, pd);
     }
+    if (ar.cold_refine || (phase == 1 && ar.precision == 1 && ar.reortho))
+      reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
+    if (phase == 0 && ar.cold_refine) {
+      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pf.CT[e] = float(pd.CT[e]);
+      __syncthreads();
+    }
+    if (phase == 0 && ar.reortho32 && !ar.cold_refine) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
     double diff = 0.0;
-    if (phase == 0) { e_el = scc_iteration<float>(nm, ar, sm, pf, ar.jacobi_tol_f, &jac_fail, &diff); it32 = 1; }
-    else e_el = scc_iteration<double>(nm, ar, sm, pd, ar.jacobi_tol_d, &jac_fail, &diff);
+    if (phase == 0) {
+      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_f), &jac_fail, &diff);
+      it32 = 1;
+    } else {
+      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_d), &jac_fail, &diff);
+    }
     it = 1;
     status = (phase == 1 && jac_fail) ? FMO_SCC_JACOBI_CODE
              : (__syncthreads_or(!isfinite(e_el)) ? FMO_SCC_NAN_CODE : FMO_SCC_CONVERGED_CODE);
   }
+  double last = ar.jac_hint;
+  bool fresh64 = false;
+  int n64 = 0;
+  bool fp32_converged = false;
+  if (!ar.single_step && ar.cold_refine) {
+    // the Loewdin start made S-orthonormal to FP64 accuracy
+    if (phase == 0) {
+      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
+      __syncthreads();
+    }
+    reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
+    if (phase == 0) {
+      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pf.CT[e] = float(pd.CT[e]);
+      __syncthreads();
+    }
+  }
   for (it = (ar.single_step ? ar.max_iter + 2 : 1); it <= ar.max_iter; ++it) {
     double diff = 0.0;
     if (phase == 0) {
-      e_el = scc_iteration<float>(nm, ar, sm, pf, ar.jacobi_tol_f, &jac_fail, &diff);
+      if (it32 > 0 && it32 % 4 == 0) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
+      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(last, ar.jacobi_tol_f), &jac_fail, &diff);
       ++it32;
     } else {
-      e_el = scc_iteration<double>(nm, ar, sm, pd, ar.jacobi_tol_d, &jac_fail, &diff);
+      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(last, ar.jacobi_tol_d), &jac_fail, &diff);
+    }
+    last = diff;
+    if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 512) ar.trace[it] = phase ? diff : -diff;
+    if (phase == 1 && ar.precision == 1 && ar.fp64_finish > 0 && ++n64 >= ar.fp64_finish) {
+      // FP64 energy of the FP32-converged charges (variational for n-mers
+      // in a fixed ESP); the loop ends here
+      status = fp32_converged ? FMO_SCC_CONVERGED_CODE : FMO_SCC_MAX_ITER_CODE;
+      if (__syncthreads_or(!isfinite(e_el))) status = FMO_SCC_NAN_CODE;
+      break;
     }
     // loop decisions are made block-uniform with barrier votes (thread 0's
     // timer read decides the deadline)
@@ -804,13 +858,16 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       status = FMO_SCC_TIMEOUT_CODE;
       break;
     }
-    broyden_step(nsh, it, hist, sm, hcount, hhead, 0.4, 0.01);
+    broyden_step(nsh, it, hist, sm, hcount, hhead, 0.4, 0.01, !fresh64);
+    fresh64 = false;
     if (__syncthreads_and(phase == 0 && (diff < ar.switch_tol || it32 >= ar.fp32_cap))) {
       for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
       __syncthreads();
-      reorthonormalise(nm, ar, sm, pd);
+      reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
       phase = 1;
       have_prev = false;
+      fresh64 = true;
+      fp32_converged = diff < ar.switch_tol;
     }
   }
   if (ar.single_step) it = 1;
@@ -1245,7 +1302,9 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.energy = L.energy; ar.e_el = L.e_el; ar.e_rep = L.e_rep; ar.dEV = L.dEV; ar.iters = L.iters; ar.iters32 = L.iters32;
   ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
-  ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho; ar.tol = L.tol; ar.etol = L.etol;
+  ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho;
+  ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.trace = L.trace;
+  ar.fp64_finish = L.fp64_finish; ar.tol = L.tol; ar.etol = L.etol;
   ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
   ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
   ar.max_n = L.max_n; ar.max_nsh = L.max_nsh; ar.max_nat = L.max_nat;

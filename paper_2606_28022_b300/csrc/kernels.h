@@ -53,6 +53,11 @@ struct SccLaunch {
   int single_step;
   int step_phase;
   int reortho;
+  int cold_refine;
+  int reortho32;
+  double jac_hint;
+  double* trace;
+  int fp64_finish;
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
   const unsigned long long* t0;   // device timestamp of the run start

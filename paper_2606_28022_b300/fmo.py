@@ -55,7 +55,7 @@ class FmoOptions(C.Structure):
                 ("schedule", C.c_int32), ("monomer_loop", C.c_int32), ("dimer_cut", C.c_double),
                 ("trimer_cut", C.c_double), ("scc_tol", C.c_double), ("e_tol", C.c_double),
                 ("outer_tol", C.c_double), ("mixed_switch_tol", C.c_double),
-                ("deadline_s", C.c_double)]
+                ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class FmoStats(C.Structure):
