@@ -126,8 +126,8 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // ---------------------------------------------------------------------------
 // Block-level GEMM: C[m][n] = sum_k a(m,k) * b(n,k) with
-//   a(m,k) = A[m*sam + kk*sak] * (kscale ? kscale[k] : 1),
-//   b(n,k) = B[n*sbn + kk*sbk],   kk = kidx ? kidx[k] : k
+//   a(m,k) = A[m*sam + ka*sak] * (kscale ? kscale[k] : 1),  ka = kidx ? kidx[k] : k,
+//   b(n,k) = B[n*sbn + kb*sbk],                             kb = kidx_b ? kidx_b[k] : k
 // (B may be stored in a wider type TB; it is rounded to T on load).
 // 64x64 output tiles, BK = 16, 256 threads with 4x4 outputs each.  Operand
 // tiles are staged in shared memory (smem: 2*16*64 elements of T).
@@ -136,7 +136,7 @@ template <typename T, typename TB = T>
 __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long long sam,
                            long long sak, const TB* __restrict__ B, long long sbn, long long sbk,
                            T* __restrict__ C, long long ldc, const int* __restrict__ kidx,
-                           const double* __restrict__ kscale, T* smem) {
+                           const int* __restrict__ kidx_b, const double* __restrict__ kscale, T* smem) {
   constexpr int BM = 64, BN = 64, BK = 16;
   T* As = smem;             // [BK][BM]
   T* Bs = smem + BK * BM;   // [BK][BN]
@@ -174,7 +174,7 @@ __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long lo
           const int gn = n0 + nn, gk = k0 + kk;
           T v = T(0);
           if (gn < N && gk < K) {
-            const long long kr = kidx ? kidx[gk] : gk;
+            const long long kr = kidx_b ? kidx_b[gk] : gk;
             v = T(B[gn * sbn + kr * sbk]);
           }
           Bs[kk * BN + nn] = v;

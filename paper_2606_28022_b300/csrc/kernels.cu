@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kBlock) lowdin_kernel(const Nmer* __restrict__
   for (int i = threadIdx.x; i < n; i += blockDim.x) scale[i] = 1.0 / sqrt(double(A[i * npad + i]));
   __syncthreads();
   // X = V diag(s^-1/2) V^T with V^T = CT rows
-  block_gemm<T>(n, n, n, CTm, 1, n, CTm, 1, n, Wm, n, nullptr, scale, gemm);
+  block_gemm<T>(n, n, n, CTm, 1, n, CTm, 1, n, Wm, n, nullptr, nullptr, scale, gemm);
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) CTm[e] = Wm[e];
   __syncthreads();
 }
@@ -350,6 +350,8 @@ struct SccSmem {
   double* eps;
   double* focc;
   int* occ;
+  int* virt;     // rows with zero occupation (orbital-rotation updates)
+  int* misc;     // [0] number of virt rows, [1] rotation update allowed
   double* bro;   // Broyden small matrix (kHist*kHist + 2*kHist)
   NmerMaps mp;
   int* jsp;
@@ -371,6 +373,8 @@ __host__ __device__ inline size_t scc_smem_bytes(int max_n, int max_nsh, int max
   b += 2 * align16(sizeof(double) * max_nat);          // dqat g3
   b += 2 * align16(sizeof(double) * npad);             // eps focc
   b += align16(sizeof(int) * npad);                    // occ
+  b += align16(sizeof(int) * npad);                    // virt
+  b += align16(sizeof(int) * 4);                       // misc
   b += align16(sizeof(double) * (kHist * kHist + 4 * kHist + 8));
   b += align16(sizeof(int16_t) * npad);                // ao_sh
   b += align16(sizeof(int16_t) * max_nsh);             // sh_at
@@ -402,6 +406,8 @@ __device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, i
   s.eps = (double*)take(sizeof(double) * npad);
   s.focc = (double*)take(sizeof(double) * npad);
   s.occ = (int*)take(sizeof(int) * npad);
+  s.virt = (int*)take(sizeof(int) * npad);
+  s.misc = (int*)take(sizeof(int) * 4);
   s.bro = (double*)take(sizeof(double) * (kHist * kHist + 4 * kHist + 8));
   s.mp.ao_sh = (int16_t*)take(sizeof(int16_t) * npad);
   s.mp.sh_at = (int16_t*)take(sizeof(int16_t) * max_nsh);
@@ -455,12 +461,26 @@ __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_o
     if (lane == 0) s_mts = 2.0 * kT * mts;
     __syncwarp();
     if (lane == 0) {
-      int k = 0;
+      // occ: rows entering the density (occupation above 1e-30), the
+      // occupied ones (f > 1) first; virt: rows with f <= 1.  The
+      // orbital-rotation update partitions at f = 1 and is allowed only when
+      // every occupation is 2 or 0 to within 1e-14.
+      int k = 0, v = 0;
+      double f_occ_min = 2.0, f_vir_max = 0.0;
       for (int i = 0; i < n; ++i) {
         const double f = sm.focc[i];
-        if (f > 1e-30) sm.occ[k++] = i;
+        if (f > 1.0) { sm.occ[k++] = i; f_occ_min = fmin(f_occ_min, f); }
+        else { sm.virt[v++] = i; f_vir_max = fmax(f_vir_max, f); }
+      }
+      const int nro = k;
+      for (int i = 0; i < n; ++i) {
+        const double f = sm.focc[i];
+        if (f <= 1.0 && f > 1e-30) sm.occ[k++] = i;
       }
       s_nocc = k;
+      sm.misc[0] = v;
+      sm.misc[1] = (nro > 0 && v > 0 && f_occ_min > 2.0 - 1e-14 && f_vir_max < 1e-14) ? 1 : 0;
+      sm.misc[2] = nro;
     }
   }
   __syncthreads();
@@ -574,7 +594,7 @@ struct PrecPtrs {
 // One SCC iteration in precision T.  Returns E_el; writes dq_out, eps.
 template <typename T>
 __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<T> pp,
-                                double jac_tol, int* jac_fail, double* diff_out) {
+                                double jac_tol, int* jac_fail, double* diff_out, bool allow_rot) {
   const int n = nm.n, nsh = nm.nsh, nat = nm.nat, npad = nm.npad;
   const double* Sm = ar.S + nm.mat;
   const double* Hm = ar.H0 + nm.mat;
@@ -615,21 +635,73 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   __syncthreads();
   T* gemm = reinterpret_cast<T*>(sm.gemm);
   // U = CT F  (W2), then A = U CT^T: the Fock matrix in the current MO basis
-  block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, gemm);
-  block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, gemm);
-  JacobiScratch<T> js{sm.jsp, sm.jsq, reinterpret_cast<T*>(sm.jsc), reinterpret_cast<T*>(sm.jss), sm.jsact};
-  const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
-  if (sw < 0 && sizeof(T) == 8) *jac_fail = 1;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
-  __syncthreads();
+  block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
+  block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, nullptr, gemm);
   int nocc = 0;
-  const double mts = fermi_step(n, nm.nel, ar.g.kT, sm, &nocc);
+  double mts = 0.0;
+  bool rotated = false;
+  if (allow_rot) {
+    // Warm start: the rows of CT are eigenvectors of the previous Fock
+    // matrix, so A is nearly diagonal.  With integer occupations only the
+    // occupied-virtual block matters for the density: one second-order
+    // rotation C <- (1 + k + k^2/2) C with k_ia = A_ia / (A_ii - A_aa) (i
+    // occupied, a empty; first-order perturbation theory) removes it to
+    // second order in |A_ia|.  At the SCC
+    // fixed point A_ia = 0, so the fixed point is unchanged.
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
+    __syncthreads();
+    mts = fermi_step(n, nm.nel, ar.g.kT, sm, &nocc);
+    if (sm.misc[1]) {
+      const int no = sm.misc[2], nv = sm.misc[0];
+      T* K = pp.W2;                                 // no x nv
+      double kmax = 0.0;
+      for (long long e = threadIdx.x; e < (long long)no * nv; e += blockDim.x) {
+        const int i = sm.occ[e / nv], a = sm.virt[e % nv];
+        const double k = double(pp.A[(long long)i * pp.lda + a]) / (sm.eps[i] - sm.eps[a]);
+        K[e] = T(k);
+        kmax = fmax(kmax, fabs(k));
+      }
+      kmax = block_max(kmax, sm.red);
+      // (1 + k + k^2/2) keeps orthonormality up to k^4/4: rotate only while
+      // that stays below the working precision, otherwise diagonalise
+      rotated = kmax <= (sizeof(T) == 8 ? 1e-4 : 2e-2);
+    }
+    if (rotated) {
+      const int no = sm.misc[2], nv = sm.misc[0];
+      T* K = pp.W2;
+      T* dCo = pp.W1;                               // no x n : K C_v
+      T* Dv = pp.W1 + (long long)no * n;            // nv x n : K^T C_o
+      T* Yo = pp.W2 + (long long)no * nv;           // no x n : K Dv
+      T* Yv = pp.A;                                 // nv x n : K^T dCo (A is no longer needed)
+      block_gemm<T>(no, n, nv, K, nv, 1, pp.CT, 1, n, dCo, n, nullptr, sm.virt, nullptr, gemm);
+      block_gemm<T>(nv, n, no, K, 1, nv, pp.CT, 1, n, Dv, n, nullptr, sm.occ, nullptr, gemm);
+      block_gemm<T>(no, n, nv, K, nv, 1, Dv, 1, n, Yo, n, nullptr, nullptr, nullptr, gemm);
+      block_gemm<T>(nv, n, no, K, 1, nv, dCo, 1, n, Yv, n, nullptr, nullptr, nullptr, gemm);
+      for (long long e = threadIdx.x; e < (long long)no * n; e += blockDim.x) {
+        const long long r = (long long)sm.occ[e / n] * n + e % n;
+        pp.CT[r] = pp.CT[r] + dCo[e] - T(0.5) * Yo[e];
+      }
+      for (long long e = threadIdx.x; e < (long long)nv * n; e += blockDim.x) {
+        const long long r = (long long)sm.virt[e / n] * n + e % n;
+        pp.CT[r] = pp.CT[r] - Dv[e] - T(0.5) * Yv[e];
+      }
+      __syncthreads();
+    }
+  }
+  if (!rotated) {
+    JacobiScratch<T> js{sm.jsp, sm.jsq, reinterpret_cast<T*>(sm.jsc), reinterpret_cast<T*>(sm.jss), sm.jsact};
+    const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
+    if (sw < 0 && sizeof(T) == 8) *jac_fail = 1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
+    __syncthreads();
+    mts = fermi_step(n, nm.nel, ar.g.kT, sm, &nocc);
+  }
   // compacted occupations
   double* fc = reinterpret_cast<double*>(sm.jsc);   // js scratch is free here (npad doubles)
   for (int k = threadIdx.x; k < nocc; k += blockDim.x) fc[k] = sm.focc[sm.occ[k]];
   __syncthreads();
   // density P = sum_occ f_i c_i c_i^T  (W1)
-  block_gemm<T>(n, n, nocc, pp.CT, 1, n, pp.CT, 1, n, pp.W1, n, sm.occ, fc, gemm);
+  block_gemm<T>(n, n, nocc, pp.CT, 1, n, pp.CT, 1, n, pp.W1, n, sm.occ, sm.occ, fc, gemm);
   // Mulliken shell populations (Eq. 3) and the band energy sum P H0, one warp per shell
   double eb_local = 0.0;
   {
@@ -693,14 +765,14 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
   T* gemm = reinterpret_cast<T*>(sm.gemm);
   const double* Sm = ar.S + nm.mat;
   for (int step = 0; step < max_steps; ++step) {
-    block_gemm<T, double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, gemm);   // V = CT S
-    block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.W1, n, nullptr, nullptr, gemm);       // M = V CT^T
+    block_gemm<T, double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);   // V = CT S
+    block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.W1, n, nullptr, nullptr, nullptr, gemm);       // M = V CT^T
     double err = 0.0;
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
       err = fmax(err, fabs(double(pp.W1[e]) - ((e / n) == (e % n) ? 1.0 : 0.0)));
     err = block_max(err, sm.red);
     if (err < tol) break;
-    block_gemm<T>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, gemm);       // M CT
+    block_gemm<T>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, nullptr, gemm);       // M CT
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
       pp.CT[e] = T(1.5) * pp.CT[e] - T(0.5) * pp.W2[e];
     __syncthreads();
@@ -777,6 +849,20 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     pf.W2 = ar.W2f + nm.mat;
     pf.A = ar.a_smem_f ? reinterpret_cast<float*>(sm.A) : ar.Agf + nm.apad;
   }
+  // Mixed precision with the FP64 eigen-solve matrix in shared memory: that
+  // region (8 npad^2 bytes) also holds the FP32 matrix (4 npad^2) and the FP32
+  // eigenvector rows (4 n^2) during the FP32 phase, so the rotations of every
+  // Jacobi round stay on chip.  The FP64 matrix takes the region over after
+  // the hand-over, when the FP32 rows are no longer needed.
+  float* const ctf_g = (ar.precision == 1) ? ar.CTf + nm.mat : nullptr;
+  const bool ct_smem = ar.a_smem_d && ar.precision == 1;
+  float* const ctf_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sm.A) +
+                                                align16(sizeof(float) * (size_t)npad * npad));
+  auto load_ct_smem = [&]() {
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) ctf_s[e] = ctf_g[e];
+    __syncthreads();
+    pf.CT = ctf_s;
+  };
   double* hist = ar.hist + nm.hist;
   int hcount = 0, hhead = 0;
   int phase = (ar.precision == 1) ? 0 : 1;   // 0: FP32 loose, 1: FP64
@@ -789,23 +875,25 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     // one iteration from the given charges in the given precision; the
     // caller mixes the charges of all monomers together
     phase = ar.step_phase;
-    if ((phase == 1 && ar.precision == 1 && ar.reortho) || (phase == 0 && ar.cold_refine)) {
+    if (phase == 1 && ar.precision == 1 && ar.reortho) {
       for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
       __syncthreads();
-    }
-    if (ar.cold_refine || (phase == 1 && ar.precision == 1 && ar.reortho))
+      reorthonormalise<double>(nm, ar, sm, pd, 3, 1e-13);
+    } else if (ar.cold_refine && phase == 1) {
       reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
-    if (phase == 0 && ar.cold_refine) {
-      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pf.CT[e] = float(pd.CT[e]);
-      __syncthreads();
+    } else if (ar.cold_refine) {
+      reorthonormalise<float>(nm, ar, sm, pf, 2, 1e-6);
     }
+    if (phase == 0 && ct_smem) load_ct_smem();
     if (phase == 0 && ar.reortho32 && !ar.cold_refine) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
     double diff = 0.0;
     if (phase == 0) {
-      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_f), &jac_fail, &diff);
+      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_f), &jac_fail, &diff,
+                                  !ar.cold_refine);
       it32 = 1;
     } else {
-      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_d), &jac_fail, &diff);
+      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_d), &jac_fail, &diff,
+                                   !ar.cold_refine);
     }
     it = 1;
     status = (phase == 1 && jac_fail) ? FMO_SCC_JACOBI_CODE
@@ -816,25 +904,21 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   int n64 = 0;
   bool fp32_converged = false;
   if (!ar.single_step && ar.cold_refine) {
-    // the Loewdin start made S-orthonormal to FP64 accuracy
-    if (phase == 0) {
-      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
-      __syncthreads();
-    }
-    reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
-    if (phase == 0) {
-      for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pf.CT[e] = float(pd.CT[e]);
-      __syncthreads();
-    }
+    // the Loewdin start made S-orthonormal to the working precision
+    if (phase == 0) reorthonormalise<float>(nm, ar, sm, pf, 2, 1e-6);
+    else reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
   }
+  if (!ar.single_step && phase == 0 && ct_smem) load_ct_smem();
   for (it = (ar.single_step ? ar.max_iter + 2 : 1); it <= ar.max_iter; ++it) {
     double diff = 0.0;
     if (phase == 0) {
       if (it32 > 0 && it32 % 4 == 0) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
-      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(last, ar.jacobi_tol_f), &jac_fail, &diff);
+      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(last, ar.jacobi_tol_f), &jac_fail, &diff,
+                                  it > 1 || !ar.cold_refine);
       ++it32;
     } else {
-      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(last, ar.jacobi_tol_d), &jac_fail, &diff);
+      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(last, ar.jacobi_tol_d), &jac_fail, &diff,
+                                   it > 1 || !ar.cold_refine);
     }
     last = diff;
     if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 512) ar.trace[it] = phase ? diff : -diff;
@@ -863,7 +947,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     if (__syncthreads_and(phase == 0 && (diff < ar.switch_tol || it32 >= ar.fp32_cap))) {
       for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
       __syncthreads();
-      reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
+      reorthonormalise<double>(nm, ar, sm, pd, 3, 1e-13);
       phase = 1;
       have_prev = false;
       fresh64 = true;
@@ -873,9 +957,12 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   if (ar.single_step) it = 1;
   else if (it > ar.max_iter) it = ar.max_iter;
   if (jac_fail && status == FMO_SCC_CONVERGED_CODE) status = FMO_SCC_JACOBI_CODE;
-  // keep a float copy of the final FP64 eigenvectors for a later warm start
+  // keep a float copy of the final eigenvectors in global memory for a later
+  // warm start
   if (ar.precision == 1 && phase == 1) {
-    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pf.CT[e] = float(pd.CT[e]);
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) ctf_g[e] = float(pd.CT[e]);
+  } else if (ar.precision == 1 && ct_smem) {
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) ctf_g[e] = pf.CT[e];
   }
   // results
   double dev = 0.0;
