@@ -280,7 +280,10 @@ SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision) {
 }
 
 // S, H0, gamma and the Loewdin start of every n-mer of a pass.
-fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, cudaStream_t st) {
+// warm_from: in mixed precision, start the n-mers from the final monomer
+// rows of this pass instead of the Loewdin orthogonaliser.
+fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, cudaStream_t st,
+                      const Pass* warm_from = nullptr) {
   const int nn = int(P.nm.size());
   if (nn == 0) return FMO_OK;
   const SmemPlan& s = sp;
@@ -303,9 +306,14 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
     if (use_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
     else CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
   }
-  CK(launch_lowdin(st, nn, P.max_n, P.d_nm.as<Nmer>(), P.S.as<double>(),
-                   use_f ? P.CTf.p : P.CTd.p, use_f ? P.W1f.p : P.W1d.p, use_f ? P.Agf.p : P.Agd.p,
-                   use_f ? 1 : 0, a_in, P.status.as<int>()));
+  if (warm_from && use_f) {
+    CK(launch_warm_start(st, nn, P.d_nm.as<Nmer>(), warm_from->d_nm.as<Nmer>(), warm_from->CTf.as<float>(),
+                         P.CTf.as<float>()));
+  } else {
+    CK(launch_lowdin(st, nn, P.max_n, P.d_nm.as<Nmer>(), P.S.as<double>(),
+                     use_f ? P.CTf.p : P.CTd.p, use_f ? P.W1f.p : P.W1d.p, use_f ? P.Agf.p : P.Agd.p,
+                     use_f ? 1 : 0, a_in, P.status.as<int>()));
+  }
   ctx->stats.kernel_launches += 3;
   return FMO_OK;
 }
@@ -354,6 +362,9 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.reortho32 = reortho32;
   L.jac_hint = jac_hint;
   L.fp64_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED) ? std::max(0, o.mixed_finish) : 0;
+  const bool warm_nmer = (pass_id >= 1 && o.precision == FMO_PREC_MIXED);
+  L.cold_steps = warm_nmer ? 12 : 2;
+  L.first_rot = warm_nmer ? 1 : 0;
   L.trace = nullptr;
   const bool tracing = debug_level() >= 2 && pass_id == 1;
   if (tracing) {
@@ -843,7 +854,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (sp_dim.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->dim))
     return fail(ctx, FMO_ERR_UNSUPPORTED, "dimer too large");
   if (!dim_tu.empty()) {
-    fs = setup_pass(ctx, ctx->dim, o.precision, sp_dim, st);
+    fs = setup_pass(ctx, ctx->dim, o.precision, sp_dim, st, &ctx->mono);
     if (fs != FMO_OK) return fs;
     stage(st, "dimer setup");
     fs = run_scc(ctx, ctx->dim, o, sp_dim, true, 1, st);
@@ -870,7 +881,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (sp_tri.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->tri))
     return fail(ctx, FMO_ERR_UNSUPPORTED, "trimer too large");
   if (!tri_tu.empty()) {
-    fs = setup_pass(ctx, ctx->tri, o.precision, sp_tri, st);
+    fs = setup_pass(ctx, ctx->tri, o.precision, sp_tri, st, &ctx->mono);
     if (fs != FMO_OK) return fs;
     fs = run_scc(ctx, ctx->tri, o, sp_tri, true, 2, st);
     if (fs != FMO_OK) return fs;

@@ -279,6 +279,33 @@ __global__ void __launch_bounds__(kBlock) lowdin_kernel(const Nmer* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Warm start of an n-mer from its monomers' final eigenvector rows: the
+// block-diagonal C_I (+) C_J (+) C_K in the n-mer's AO order (fragments in
+// the n-mer's order).  These rows are S-orthonormal within each fragment but
+// not across fragments; the SCC kernel restores that by Newton-Schulz
+// steps before its first iteration.
+
+__global__ void warm_start_kernel(const Nmer* __restrict__ nmers, const Nmer* __restrict__ mono,
+                                  const float* __restrict__ mono_ct, float* __restrict__ ct) {
+  const Nmer nm = nmers[blockIdx.x];
+  const int n = nm.n;
+  int off[4] = {0, n, n, n};
+  for (int k = 0; k < nm.nfrag; ++k) off[k + 1] = off[k] + mono[nm.frag[k]].n;
+  float* C = ct + nm.mat;
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int r = int(e / n), c = int(e % n);
+    const int kr = (r >= off[1]) + (r >= off[2]);
+    const int kc = (c >= off[1]) + (c >= off[2]);
+    float v = 0.f;
+    if (kr == kc) {
+      const Nmer& m = mono[nm.frag[kr]];
+      v = mono_ct[m.mat + (long long)(r - off[kr]) * m.n + (c - off[kc])];
+    }
+    C[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Persistent batched SCC kernel: one block per n-mer iterates the SCC loop of
 // Eqs. 2-7 to self-consistency in its embedding potential (Eqs. 20-21).
 
@@ -326,6 +353,8 @@ struct SccArgs {
   int reortho32;     // single step: one FP32 Newton-Schulz step before the iteration
   double jac_hint;   // SCC residual before this launch (sets the first Jacobi threshold)
   int fp64_finish;   // mixed: stop after this many FP64 iterations (0: converge in FP64)
+  int cold_steps;    // Newton-Schulz steps allowed for the cold start (far from orthonormal: more)
+  int first_rot;     // the first iteration may use the rotation update (warm rows)
   double* trace;     // optional: residual per iteration of the first n-mer in the order
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
@@ -904,8 +933,8 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   int n64 = 0;
   bool fp32_converged = false;
   if (!ar.single_step && ar.cold_refine) {
-    // the Loewdin start made S-orthonormal to the working precision
-    if (phase == 0) reorthonormalise<float>(nm, ar, sm, pf, 2, 1e-6);
+    // the starting rows made S-orthonormal to the working precision
+    if (phase == 0) reorthonormalise<float>(nm, ar, sm, pf, ar.cold_steps, 1e-6);
     else reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
   }
   if (!ar.single_step && phase == 0 && ct_smem) load_ct_smem();
@@ -914,7 +943,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     if (phase == 0) {
       if (it32 > 0 && it32 % 4 == 0) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
       e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(last, ar.jacobi_tol_f), &jac_fail, &diff,
-                                  it > 1 || !ar.cold_refine);
+                                  it > 1 || !ar.cold_refine || ar.first_rot);
       ++it32;
     } else {
       e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(last, ar.jacobi_tol_d), &jac_fail, &diff,
@@ -1391,7 +1420,7 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
   ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho;
   ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.trace = L.trace;
-  ar.fp64_finish = L.fp64_finish; ar.tol = L.tol; ar.etol = L.etol;
+  ar.fp64_finish = L.fp64_finish; ar.cold_steps = L.cold_steps; ar.first_rot = L.first_rot; ar.tol = L.tol; ar.etol = L.etol;
   ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
   ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
   ar.max_n = L.max_n; ar.max_nsh = L.max_nsh; ar.max_nat = L.max_nat;
@@ -1410,6 +1439,14 @@ int phi_chunks(int n_sh) {
   const int mu_blocks = (n_sh + 255) / 256;
   const int want = (4 * 148 + mu_blocks - 1) / mu_blocks;
   return std::max(1, std::min(want, (n_sh + 255) / 256));
+}
+
+cudaError_t launch_warm_start(cudaStream_t st, int n_nmer, const Nmer* nmers, const Nmer* mono, const float* mono_ct,
+                              float* ct) {
+  if (n_nmer == 0) return cudaSuccess;
+  warm_start_kernel<<<n_nmer, 256, 0, st>>>(nmers, mono, mono_ct, ct);
+  LAUNCH_CHECK();
+  return cudaSuccess;
 }
 
 cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,

@@ -58,6 +58,8 @@ struct SccLaunch {
   double jac_hint;
   double* trace;
   int fp64_finish;
+  int cold_steps;
+  int first_rot;
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
   const unsigned long long* t0;   // device timestamp of the run start
@@ -78,6 +80,8 @@ cudaError_t launch_lowdin(cudaStream_t st, int n_nmer, int max_n, const Nmer* nm
                           void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status);
 size_t scc_smem_size(int max_n, int max_nsh, int max_nat, int a_bytes);
 cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L);
+cudaError_t launch_warm_start(cudaStream_t st, int n_nmer, const Nmer* nmers, const Nmer* mono, const float* mono_ct,
+                              float* ct);
 int phi_chunks(int n_sh);
 cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
                        const double* dq, GParams g, double* phi, double* part);

@@ -258,6 +258,7 @@ extern "C" fmo_status fmo_scc_solve_noalloc(const fmo_params* p, int32_t n_atoms
   sl.guess_from_mono = 1; sl.precision = o.precision; sl.max_iter = o.max_iter;
   sl.fp32_cap = std::max(4, o.max_iter / 2); sl.single_step = 0; sl.step_phase = 1; sl.reortho = 0;
   sl.cold_refine = 1; sl.reortho32 = 0; sl.jac_hint = 1.0; sl.trace = nullptr;
+  sl.cold_steps = 2; sl.first_rot = 0;
   sl.tol = o.scc_tol; sl.etol = o.e_tol; sl.switch_tol = o.mixed_switch_tol;
   sl.jacobi_tol_d = 1e-14; sl.jacobi_tol_f = 2e-7;
   sl.t0 = nullptr; sl.budget_ns = 0;
