@@ -621,9 +621,35 @@ struct PrecPtrs {
 };
 
 // One SCC iteration in precision T.  Returns E_el; writes dq_out, eps.
+// Rotation of the rows CT (type T) by the generator K (n_o x n_v, type TG,
+// stored at Kg): C_o += K C_v - 1/2 K K^T C_o, C_v += -K^T C_o - 1/2 K^T K C_v
+// with the products formed in precision TG on the TG copy src of the rows.
+// w1: n x n, w2 after K: n_o x n, yv: n_v x n (all TG).
+template <typename T, typename TG>
+__device__ void rotate_rows(int n, int no, int nv, const int* occ, const int* virt, T* CT, const TG* src,
+                            const TG* Kg, TG* w1, TG* w2, TG* yv, TG* gemm) {
+  TG* dCo = w1;                               // no x n : K C_v
+  TG* Dv = w1 + (long long)no * n;            // nv x n : K^T C_o
+  TG* Yo = w2;                                // no x n : K Dv
+  block_gemm<TG>(no, n, nv, Kg, nv, 1, src, 1, n, dCo, n, nullptr, virt, nullptr, gemm);
+  block_gemm<TG>(nv, n, no, Kg, 1, nv, src, 1, n, Dv, n, nullptr, occ, nullptr, gemm);
+  block_gemm<TG>(no, n, nv, Kg, nv, 1, Dv, 1, n, Yo, n, nullptr, nullptr, nullptr, gemm);
+  block_gemm<TG>(nv, n, no, Kg, 1, nv, dCo, 1, n, yv, n, nullptr, nullptr, nullptr, gemm);
+  for (long long e = threadIdx.x; e < (long long)no * n; e += blockDim.x) {
+    const long long r = (long long)occ[e / n] * n + e % n;
+    CT[r] = CT[r] + T(dCo[e] - TG(0.5) * Yo[e]);
+  }
+  for (long long e = threadIdx.x; e < (long long)nv * n; e += blockDim.x) {
+    const long long r = (long long)virt[e / n] * n + e % n;
+    CT[r] = CT[r] - T(Dv[e] + TG(0.5) * yv[e]);
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<T> pp,
-                                double jac_tol, int* jac_fail, double* diff_out, bool allow_rot) {
+                                double jac_tol, int* jac_fail, double* diff_out, bool allow_rot,
+                                float* f_ct = nullptr, float* f_w1 = nullptr, float* f_w2 = nullptr) {
   const int n = nm.n, nsh = nm.nsh, nat = nm.nat, npad = nm.npad;
   const double* Sm = ar.S + nm.mat;
   const double* Hm = ar.H0 + nm.mat;
@@ -697,24 +723,18 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     }
     if (rotated) {
       const int no = sm.misc[2], nv = sm.misc[0];
-      T* K = pp.W2;
-      T* dCo = pp.W1;                               // no x n : K C_v
-      T* Dv = pp.W1 + (long long)no * n;            // nv x n : K^T C_o
-      T* Yo = pp.W2 + (long long)no * nv;           // no x n : K Dv
-      T* Yv = pp.A;                                 // nv x n : K^T dCo (A is no longer needed)
-      block_gemm<T>(no, n, nv, K, nv, 1, pp.CT, 1, n, dCo, n, nullptr, sm.virt, nullptr, gemm);
-      block_gemm<T>(nv, n, no, K, 1, nv, pp.CT, 1, n, Dv, n, nullptr, sm.occ, nullptr, gemm);
-      block_gemm<T>(no, n, nv, K, nv, 1, Dv, 1, n, Yo, n, nullptr, nullptr, nullptr, gemm);
-      block_gemm<T>(nv, n, no, K, 1, nv, dCo, 1, n, Yv, n, nullptr, nullptr, nullptr, gemm);
-      for (long long e = threadIdx.x; e < (long long)no * n; e += blockDim.x) {
-        const long long r = (long long)sm.occ[e / n] * n + e % n;
-        pp.CT[r] = pp.CT[r] + dCo[e] - T(0.5) * Yo[e];
+      if (sizeof(T) == 8 && f_ct) {
+        // mixed-precision FP64 iteration: the rotation is a small correction
+        // (|k| ~ FP32 rounding), so its products run in FP32 on FP32 copies
+        for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) f_ct[e] = float(pp.CT[e]);
+        for (long long e = threadIdx.x; e < (long long)no * nv; e += blockDim.x) f_w2[e] = float(pp.W2[e]);
+        __syncthreads();
+        rotate_rows<T, float>(n, no, nv, sm.occ, sm.virt, pp.CT, f_ct, f_w2, f_w1, f_w2 + (long long)no * nv,
+                              reinterpret_cast<float*>(pp.A), reinterpret_cast<float*>(sm.gemm));
+      } else {
+        rotate_rows<T, T>(n, no, nv, sm.occ, sm.virt, pp.CT, pp.CT, pp.W2, pp.W1, pp.W2 + (long long)no * nv, pp.A,
+                          gemm);
       }
-      for (long long e = threadIdx.x; e < (long long)nv * n; e += blockDim.x) {
-        const long long r = (long long)sm.virt[e / n] * n + e % n;
-        pp.CT[r] = pp.CT[r] - Dv[e] - T(0.5) * Yv[e];
-      }
-      __syncthreads();
     }
   }
   if (!rotated) {
@@ -806,6 +826,33 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
       pp.CT[e] = T(1.5) * pp.CT[e] - T(0.5) * pp.W2[e];
     __syncthreads();
   }
+}
+
+// FP32 -> FP64 hand-over: the FP64 rows (converted from FP32) are
+// S-orthonormal to about 1e-7.  M = CT S CT^T is formed in FP64; the
+// Newton-Schulz correction CT <- CT - 1/2 (M - I) CT only needs the small
+// (M - I) to relative FP32 accuracy, so that product runs in FP32 (on the
+// FP32 rows, equal to CT to 1e-7).  One step leaves ~1e-14; a second,
+// all-FP64 step follows only if the start was worse than 1e-6.
+__device__ void reortho_handover(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<double> pd,
+                                 const float* ct32, float* wf1, float* wf2) {
+  const int n = nm.n;
+  double* gemm = reinterpret_cast<double*>(sm.gemm);
+  const double* Sm = ar.S + nm.mat;
+  block_gemm<double>(n, n, n, pd.CT, n, 1, Sm, n, 1, pd.W2, n, nullptr, nullptr, nullptr, gemm);   // V = CT S
+  block_gemm<double>(n, n, n, pd.W2, n, 1, pd.CT, n, 1, pd.W1, n, nullptr, nullptr, nullptr, gemm);  // M
+  double err = 0.0;
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const double d = pd.W1[e] - ((e / n) == (e % n) ? 1.0 : 0.0);
+    wf1[e] = float(d);
+    err = fmax(err, fabs(d));
+  }
+  err = block_max(err, sm.red);
+  float* gf = reinterpret_cast<float*>(sm.gemm);
+  block_gemm<float>(n, n, n, wf1, n, 1, ct32, 1, n, wf2, n, nullptr, nullptr, nullptr, gf);   // (M - I) CT
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] -= 0.5 * double(wf2[e]);
+  __syncthreads();
+  if (err > 1e-6) reorthonormalise<double>(nm, ar, sm, pd, 3, 1e-13);
 }
 
 // Jacobi threshold (relative to max |A_ii|) for an SCC iteration whose
@@ -907,7 +954,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     if (phase == 1 && ar.precision == 1 && ar.reortho) {
       for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
       __syncthreads();
-      reorthonormalise<double>(nm, ar, sm, pd, 3, 1e-13);
+      reortho_handover(nm, ar, sm, pd, pf.CT, pf.W1, pf.W2);
     } else if (ar.cold_refine && phase == 1) {
       reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
     } else if (ar.cold_refine) {
@@ -922,7 +969,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       it32 = 1;
     } else {
       e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_d), &jac_fail, &diff,
-                                   !ar.cold_refine);
+                                   !ar.cold_refine, ar.precision == 1 ? ctf_g : nullptr, pf.W1, pf.W2);
     }
     it = 1;
     status = (phase == 1 && jac_fail) ? FMO_SCC_JACOBI_CODE
@@ -947,7 +994,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       ++it32;
     } else {
       e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(last, ar.jacobi_tol_d), &jac_fail, &diff,
-                                   it > 1 || !ar.cold_refine);
+                                   it > 1 || !ar.cold_refine, ar.precision == 1 ? ctf_g : nullptr, pf.W1, pf.W2);
     }
     last = diff;
     if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 512) ar.trace[it] = phase ? diff : -diff;
@@ -976,7 +1023,12 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     if (__syncthreads_and(phase == 0 && (diff < ar.switch_tol || it32 >= ar.fp32_cap))) {
       for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
       __syncthreads();
-      reorthonormalise<double>(nm, ar, sm, pd, 3, 1e-13);
+      if (ct_smem) {
+        // the FP32 rows leave shared memory (the FP64 matrix takes it over)
+        for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) ctf_g[e] = pf.CT[e];
+        __syncthreads();
+      }
+      reortho_handover(nm, ar, sm, pd, ct_smem ? ctf_g : pf.CT, pf.W1, pf.W2);
       phase = 1;
       have_prev = false;
       fresh64 = true;
