@@ -292,7 +292,9 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
   CK(launch_integrals(st, nn, P.max_pairs, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
                       ctx->d_elem.as<int>(), ctx->d_atom_sh0.as<int>(), ctx->d_cn.as<double>(),
                       ctx->d_el.as<DevElem>(), ctx->d_kab.as<double>(), ctx->ne, ctx->g, P.S.as<double>(),
-                      P.H0.as<double>()));
+                      P.H0.as<double>(), warm_from ? warm_from->d_nm.as<Nmer>() : nullptr,
+                      warm_from ? warm_from->S.as<double>() : nullptr,
+                      warm_from ? warm_from->H0.as<double>() : nullptr));
   CK(launch_gamma(st, nn, P.max_nsh, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
                   ctx->d_elem.as<int>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(), ctx->g,
                   P.gam.as<double>()));
@@ -306,7 +308,7 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
     if (use_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
     else CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
   }
-  if (warm_from && use_f) {
+  if (warm_from && use_f) {   // warm start in mixed precision only
     CK(launch_warm_start(st, nn, P.d_nm.as<Nmer>(), warm_from->d_nm.as<Nmer>(), warm_from->CTf.as<float>(),
                          P.CTf.as<float>()));
   } else {

@@ -76,30 +76,53 @@ __device__ void build_maps(const Nmer& nm, const FragTab ft, const int* __restri
 // p = a + b at P = (aA + bB)/p; s-s overlap (pi/p)^{3/2} exp(-ab/p R^2); a p
 // factor contributes (P - A)_i, a pair of p factors (P-A)_i (P-B)_j + d_ij/2p.
 
+// With mono != nullptr the intra-fragment blocks are copied from the monomer
+// pass (identical: the CN is that of the whole system) and only pairs of
+// atoms in different fragments are evaluated.
 __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
                                  const double* __restrict__ xyz, const int* __restrict__ elem,
                                  const int* __restrict__ atom_sh0, const double* __restrict__ cn,
                                  const DevElem* __restrict__ el, const double* __restrict__ kab,
                                  int ne, GParams g, double* __restrict__ S,
-                                 double* __restrict__ H0) {
+                                 double* __restrict__ H0, const Nmer* __restrict__ mono,
+                                 const double* __restrict__ mono_S, const double* __restrict__ mono_H0) {
   const Nmer nm = nmers[blockIdx.y];
   __shared__ int s_glob[512];
   __shared__ int s_ao0[512];
+  __shared__ unsigned char s_fk[512];
+  __shared__ int s_foff[4];
   if (threadIdx.x == 0) {
     int la = 0, lao = 0;
     for (int k = 0; k < nm.nfrag; ++k) {
       const int f = nm.frag[k];
+      s_foff[k] = lao;
       for (int i = 0; i < ft.nat[f]; ++i) {
         const int ga = ft.atom0[f] + i;
         s_glob[la] = ga;
         s_ao0[la] = lao;
+        s_fk[la] = (unsigned char)k;
         const DevElem& e = el[elem[ga]];
         for (int s = 0; s < e.nsh; ++s) lao += 2 * e.l[s] + 1;
         ++la;
       }
     }
+    s_foff[nm.nfrag] = lao;
   }
   __syncthreads();
+  if (mono) {
+    // intra-fragment blocks from the monomer matrices
+    const int n = nm.n;
+    for (int k = 0; k < nm.nfrag; ++k) {
+      const Nmer& m = mono[nm.frag[k]];
+      const int o = s_foff[k], nk = m.n;
+      for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)nk * nk;
+           e += (long long)gridDim.x * blockDim.x) {
+        const int u = int(e / nk), v = int(e % nk);
+        S[nm.mat + (long long)(o + u) * n + (o + v)] = mono_S[m.mat + e];
+        H0[nm.mat + (long long)(o + u) * n + (o + v)] = mono_H0[m.mat + e];
+      }
+    }
+  }
   const long long npairs = (long long)nm.nat * (nm.nat + 1) / 2;
   const int n = nm.n;
   double* Sm = S + nm.mat;
@@ -111,6 +134,7 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
     while (i * (i + 1) / 2 > e) --i;
     while ((i + 1) * (i + 2) / 2 <= e) ++i;
     const int ai = int(i), bj = int(e - i * (i + 1) / 2);
+    if (mono && s_fk[ai] == s_fk[bj]) continue;      // copied above
     const int ga = s_glob[ai], gb = s_glob[bj];
     const DevElem& EA = el[elem[ga]];
     const DevElem& EB = el[elem[gb]];
@@ -1403,12 +1427,14 @@ cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int
 
 cudaError_t launch_integrals(cudaStream_t st, int n_nmer, int max_pairs, const Nmer* nmers, FragTab ft,
                              const double* xyz, const int* elem, const int* atom_sh0, const double* cn,
-                             const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0) {
+                             const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0,
+                             const Nmer* mono, const double* mono_S, const double* mono_H0) {
   if (n_nmer == 0) return cudaSuccess;
   const int chunks = max(1, min(64, (max_pairs + 127) / 128));
   for (int b0 = 0; b0 < n_nmer; b0 += 65535) {
     dim3 grid(chunks, min(65535, n_nmer - b0));
-    integrals_kernel<<<grid, 128, 0, st>>>(nmers + b0, ft, xyz, elem, atom_sh0, cn, el, kab, ne, g, S, H0);
+    integrals_kernel<<<grid, 128, 0, st>>>(nmers + b0, ft, xyz, elem, atom_sh0, cn, el, kab, ne, g, S, H0, mono,
+                                           mono_S, mono_H0);
     LAUNCH_CHECK();
   }
   return cudaSuccess;

@@ -72,7 +72,9 @@ cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int
                       GParams g, double* cn);
 cudaError_t launch_integrals(cudaStream_t st, int n_nmer, int max_pairs, const Nmer* nmers, FragTab ft,
                              const double* xyz, const int* elem, const int* atom_sh0, const double* cn,
-                             const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0);
+                             const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0,
+                             const Nmer* mono = nullptr, const double* mono_S = nullptr,
+                             const double* mono_H0 = nullptr);
 cudaError_t launch_gamma(cudaStream_t st, int n_nmer, int max_nsh, const Nmer* nmers, FragTab ft,
                          const double* xyz, const int* elem, const int* sh_atom, const double* sh_inv_eta,
                          GParams g, double* gam);
