@@ -100,6 +100,7 @@ typedef struct fmo_params {
 
 enum { FMO_PREC_FP64 = 0, FMO_PREC_MIXED = 1 };
 enum { FMO_LOOP_GLOBAL = 0, FMO_LOOP_NESTED = 1 };
+enum { FMO_NMER_FINISH_ENERGY = 0, FMO_NMER_FINISH_ITERATE = 1 };
 
 typedef struct fmo_options {
   int32_t level;            /* 1 = FMO1, 2 = FMO2 (Eq. 12), 3 = FMO3 (Eq. 16) */
@@ -122,14 +123,19 @@ typedef struct fmo_options {
   double outer_tol;         /* monomer loop: max charge change (e) */
   double mixed_switch_tol;  /* mixed: FP32 until max |dq_out - dq_in| < this */
   double deadline_s;        /* wall-clock limit per fmo_run, 0 = none */
-  int32_t mixed_finish;     /* mixed precision, dimers and trimers: FP64
-                               iterations after the FP32 phase (0: converge in
-                               FP64 to scc_tol/e_tol).  Their interaction
-                               energies are variational in the n-mer density
-                               (the ESP is fixed), so the FP64 energy of the
-                               FP32-converged charges is off only to second
-                               order in the FP32 charge error. */
-  int32_t reserved_;
+  int32_t mixed_finish;     /* nmer_finish = FMO_NMER_FINISH_ITERATE: FP64 SCC
+                               iterations of dimers and trimers after the FP32
+                               phase (0: converge in FP64 to scc_tol/e_tol) */
+  int32_t nmer_finish;      /* mixed precision, dimers and trimers: how the FP32
+                               phase ends.  FMO_NMER_FINISH_ENERGY (default):
+                               energy and charges of the FP32-converged density
+                               evaluated in FP64, its occupied orbitals first
+                               made S-orthonormal in FP64.
+                               FMO_NMER_FINISH_ITERATE: mixed_finish FP64 SCC
+                               iterations.  Either way the n-mer interaction
+                               energy is variational in the n-mer density (its
+                               ESP is fixed), so it is off only to second order
+                               in the FP32 charge error. */
 } fmo_options;
 
 /* Counters of the last fmo_run. */

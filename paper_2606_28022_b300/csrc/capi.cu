@@ -97,7 +97,8 @@ struct fmo_ctx {
   int z_to_e[FMO_MAX_Z];
   std::vector<DevElem> h_el;
   std::vector<double> h_kab;
-  DevBuf d_el, d_kab;
+  std::vector<PrimPair> h_prim;           // geometry-free primitive-pair factors
+  DevBuf d_el, d_kab, d_prim;
   GParams g;
   int smem_optin = 0;
   // system
@@ -180,6 +181,28 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (v.empty()) return cudaSuccess;
   return h2d(b.p, v.data(), sizeof(T) * v.size(), st);
+}
+
+// Geometry-free factors of every pair of primitives of the element table
+// (layout of prim_pair_index), from the normalised contraction coefficients.
+void build_prim_table(const std::vector<DevElem>& el, std::vector<PrimPair>& t) {
+  const int ne = int(el.size());
+  t.assign((size_t)ne * ne * kMaxShell * kMaxShell * kMaxPrim * kMaxPrim, PrimPair{0, 0, 0, 0, 0});
+  for (int ea = 0; ea < ne; ++ea)
+    for (int eb = 0; eb < ne; ++eb)
+      for (int sa = 0; sa < el[ea].nsh; ++sa)
+        for (int sb = 0; sb < el[eb].nsh; ++sb)
+          for (int pa = 0; pa < el[ea].nprim[sa]; ++pa)
+            for (int pb = 0; pb < el[eb].nprim[sb]; ++pb) {
+              const double a = el[ea].alpha[sa][pa], b = el[eb].alpha[sb][pb];
+              PrimPair q;
+              q.ip = 1.0 / (a + b);
+              q.abp = a * b * q.ip;
+              q.ap = a * q.ip;
+              q.bp = b * q.ip;
+              q.pref = el[ea].cn[sa][pa] * el[eb].cn[sb][pb] * std::pow(M_PI * q.ip, 1.5);
+              t[prim_pair_index(ne, ea, eb, sa, sb, pa, pb)] = q;
+            }
 }
 
 int elem_nao(const DevElem& e) {
@@ -294,7 +317,7 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
                       ctx->d_el.as<DevElem>(), ctx->d_kab.as<double>(), ctx->ne, ctx->g, P.S.as<double>(),
                       P.H0.as<double>(), warm_from ? warm_from->d_nm.as<Nmer>() : nullptr,
                       warm_from ? warm_from->S.as<double>() : nullptr,
-                      warm_from ? warm_from->H0.as<double>() : nullptr));
+                      warm_from ? warm_from->H0.as<double>() : nullptr, ctx->d_prim.as<PrimPair>()));
   CK(launch_gamma(st, nn, P.max_nsh, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
                   ctx->d_elem.as<int>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(), ctx->g,
                   P.gam.as<double>()));
@@ -364,14 +387,17 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.reortho32 = reortho32;
   L.jac_hint = jac_hint;
   L.fp64_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED) ? std::max(0, o.mixed_finish) : 0;
+  L.energy_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED && o.nmer_finish == FMO_NMER_FINISH_ENERGY);
   const bool warm_nmer = (pass_id >= 1 && o.precision == FMO_PREC_MIXED);
   L.cold_steps = warm_nmer ? 12 : 2;
   L.first_rot = warm_nmer ? 1 : 0;
+  L.first_jac_tol = warm_nmer ? 1e-3 : 0.0;
   L.trace = nullptr;
-  const bool tracing = debug_level() >= 2 && pass_id == 1;
+  // FMO_DEBUG=2 traces the first (largest) dimer, FMO_DEBUG=3 the first trimer
+  const bool tracing = debug_level() >= 2 && pass_id == std::min(2, debug_level() - 1);
   if (tracing) {
-    CK(ctx->d_trace.ensure(sizeof(double) * 512));
-    CK(cudaMemsetAsync(ctx->d_trace.p, 0, sizeof(double) * 512, st));
+    CK(ctx->d_trace.ensure(sizeof(double) * 1536));
+    CK(cudaMemsetAsync(ctx->d_trace.p, 0, sizeof(double) * 1536, st));
     L.trace = ctx->d_trace.as<double>();
   }
   L.tol = o.scc_tol; L.etol = o.e_tol; L.switch_tol = o.mixed_switch_tol;
@@ -403,12 +429,19 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   cudaEventDestroy(e1);
   ctx->stats.ms_scc[pass_id] += ms;
   if (tracing) {
-    std::vector<double> tr(512);
-    CK(d2h(tr.data(), ctx->d_trace.p, sizeof(double) * 512, st));
+    std::vector<double> tr(1536);
+    CK(d2h(tr.data(), ctx->d_trace.p, sizeof(double) * 1536, st));
     CK(sync_stream(st));
-    fprintf(stderr, "[fmo] residual per iteration (first dimer; negative = FP32):");
-    for (int i = 1; i < 512 && tr[i] != 0.0; ++i) fprintf(stderr, " %.1e", tr[i]);
-    fprintf(stderr, "\n");
+    int last = 1;
+    while (last < 511 && tr[last + 1] != 0.0) ++last;
+    fprintf(stderr, "[fmo] pass %d, first n-mer (n = %d): residual per iteration (negative = FP32):", pass_id,
+            P.nm[P.order[0]].n);
+    for (int i = 1; i <= last; ++i) fprintf(stderr, " %.1e", tr[i]);
+    fprintf(stderr, "\n[fmo] Jacobi sweeps per iteration (-1 = rotation step):");
+    for (int i = 1; i <= last; ++i) fprintf(stderr, " %d", int(tr[512 + i]));
+    fprintf(stderr, "\n[fmo] Mcycles: start %.2f, per iteration:", tr[1024] * 1e-6);
+    for (int i = 1; i <= last; ++i) fprintf(stderr, " %.2f", tr[1024 + i] * 1e-6);
+    fprintf(stderr, ", FP64 energy finish %.2f\n", tr[1535] * 1e-6);
   }
   ctx->stats.scc_launches[pass_id] += 1;
   for (int i = 0; i < nn; ++i) {
@@ -418,6 +451,11 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
     ctx->stats.iters_fp64[pass_id] += i64;
     ctx->stats.flops_fp32[pass_id] += n3 * i32;
     ctx->stats.flops_fp64[pass_id] += n3 * i64;
+    if (L.energy_finish) {
+      // C_o S, C_o H0 and two C_o S C_o^T products in FP64
+      const double nn_ = P.nm[i].n, no = 0.5 * P.nm[i].nel;
+      ctx->stats.flops_fp64[pass_id] += 4.0 * no * nn_ * nn_ + 4.0 * no * no * nn_;
+    }
   }
   return FMO_OK;
 }
@@ -492,7 +530,7 @@ fmo_status fmo_create(fmo_ctx** out, const fmo_params* p, int device) {
 void fmo_destroy(fmo_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
+  for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_prim, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
                     &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
                     &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
@@ -618,8 +656,10 @@ fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const
   ctx->n_sh = sh;
   ctx->n_ao = ao;
   cudaStream_t st = ctx->own_stream;
+  build_prim_table(ctx->h_el, ctx->h_prim);
   CK(upload(ctx->d_el, ctx->h_el, st));
   CK(upload(ctx->d_kab, ctx->h_kab, st));
+  CK(upload(ctx->d_prim, ctx->h_prim, st));
   CK(upload(ctx->d_xyz, xyz_int, st));
   CK(upload(ctx->d_perm, ctx->perm, st));
   CK(ctx->d_xyz_in.ensure(sizeof(double) * 3 * n_atoms));
@@ -696,6 +736,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (o.guess == 2 && !ctx->have_guess) return fail(ctx, FMO_ERR_STATE, "guess = 2 needs fmo_set_guess");
   if (o.monomer_loop != FMO_LOOP_GLOBAL && o.monomer_loop != FMO_LOOP_NESTED)
     return fail(ctx, FMO_ERR_ARG, "unknown monomer loop");
+  if (o.nmer_finish != FMO_NMER_FINISH_ENERGY && o.nmer_finish != FMO_NMER_FINISH_ITERATE)
+    return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
   cudaSetDevice(ctx->device);
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
   std::memset(&ctx->stats, 0, sizeof(ctx->stats));
@@ -744,8 +786,10 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     const int cap32 = std::max(8, o.max_outer / 2);
     struct { double e_prev, diff, e1; int have_prev, hcount, hhead, converged, count; } hs{};
     for (outer = 1; outer <= o.max_outer; ++outer) {
+      // the FP32 phase works with an FP32 estimate of the potential
       CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
+                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>(),
+                    phase == 0 ? 1 : 0));
       stage(st, "phi", outer);
       fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 1, phase, reortho, outer == 1 ? 1 : 0,
                    (phase == 0 && outer > 1 && outer % 4 == 0) ? 1 : 0, outer == 1 ? 1.0 : hs.diff);

@@ -64,6 +64,18 @@ struct Nmer {
   long long apad;      // offset of its npad x npad scratch (eigen-solve matrix)
 };
 
+// Geometry-free factors of one pair of contracted Gaussian primitives (a on
+// shell sa of element ea, b on shell sb of element eb): with p = a + b,
+// pref = c_a c_b (pi/p)^{3/2}, abp = a b / p, ip = 1/p, ap = a/p, bp = b/p.
+// The s-s overlap of the pair at distance R is pref exp(-abp R^2).
+struct PrimPair {
+  double pref, abp, ip, ap, bp;
+};
+
+__host__ __device__ inline long long prim_pair_index(int ne, int ea, int eb, int sa, int sb, int pa, int pb) {
+  return (((((long long)ea * ne + eb) * kMaxShell + sa) * kMaxShell + sb) * kMaxPrim + pa) * kMaxPrim + pb;
+}
+
 // Local -> global index maps of an n-mer, held in shared memory.
 struct NmerMaps {
   int16_t* ao_sh;      // [n]   local shell of each AO
@@ -235,14 +247,22 @@ __device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol
   const int npad = n + (n & 1);
   const int half = npad / 2;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  int* list = js.act + half;   // act holds npad ints: [0, half) flags, [half, npad) active pairs
+  // active-pair counters, one per round modulo 3: a counter is cleared two
+  // rounds after it was read, so no thread can still be using it
+  __shared__ int s_cnt[3];
+  if (tid == 0) { s_cnt[0] = 0; s_cnt[1] = 0; s_cnt[2] = 0; }
+  __syncthreads();
+  int round = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double dmax = 0.0;
     for (int i = tid; i < n; i += blockDim.x) dmax = fmax(dmax, fabs(double(A[i * lda + i])));
     dmax = block_max(dmax, red);
     const double thr = tol * fmax(dmax, 1e-30);
     int rotations = 0;
-    for (int r = 0; r < npad - 1; ++r) {
-      int active = 0;
+    for (int r = 0; r < npad - 1; ++r, ++round) {
+      const int slot = round % 3;
       for (int k = tid; k < half; k += blockDim.x) {
         const int m = npad - 1;
         int p, q;
@@ -263,46 +283,55 @@ __device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol
           }
         }
         js.p[k] = p; js.q[k] = q; js.c[k] = c; js.s[k] = s; js.act[k] = a;
-        active |= a;
+        if (a) list[atomicAdd(&s_cnt[slot], 1)] = k;
       }
-      if (!__syncthreads_or(active)) continue;
+      __syncthreads();
+      const int na = s_cnt[slot];
+      if (tid == 0) s_cnt[(round + 2) % 3] = 0;
+      if (na == 0) continue;
       ++rotations;
-      // 2x2 block updates
-      const int nblk = half * half;
-      for (int e = tid; e < nblk; e += blockDim.x) {
-        const int k = e / half, k2 = e % half;
-        if (k2 < k) continue;                      // symmetric: upper blocks only
-        if (!js.act[k] && !js.act[k2]) continue;
-        const int p = js.p[k], q = js.q[k], p2 = js.p[k2], q2 = js.q[k2];
-        const T c = js.c[k], s = js.s[k], c2 = js.c[k2], s2 = js.s[k2];
-        const T b00 = A[p * lda + p2], b01 = A[p * lda + q2];
-        const T b10 = A[q * lda + p2], b11 = A[q * lda + q2];
-        const T t00 = b00 * c2 - b01 * s2, t01 = b00 * s2 + b01 * c2;
-        const T t10 = b10 * c2 - b11 * s2, t11 = b10 * s2 + b11 * c2;
-        const T x00 = c * t00 - s * t10, x01 = c * t01 - s * t11;
-        const T x10 = s * t00 + c * t10, x11 = s * t01 + c * t11;
-        if (k == k2) {
-          A[p * lda + p] = x00;
-          A[q * lda + q] = x11;
-          A[p * lda + q] = T(0);
-          A[q * lda + p] = T(0);
-        } else {
-          A[p * lda + p2] = x00; A[p * lda + q2] = x01;
-          A[q * lda + p2] = x10; A[q * lda + q2] = x11;
-          A[p2 * lda + p] = x00; A[q2 * lda + p] = x01;
-          A[p2 * lda + q] = x10; A[q2 * lda + q] = x11;
-        }
-      }
-      // rotate the rows p, q of CT
-      const long long work = (long long)half * ncol;
-      for (long long e = tid; e < work; e += blockDim.x) {
-        const int k = int(e / ncol), j = int(e % ncol);
-        if (!js.act[k]) continue;
+      // 2x2 block updates A <- J^T A J: one warp per active pair k, lanes over
+      // the partner pairs k2 (a block of two active pairs is done once, by
+      // the warp of the smaller k)
+      for (int i = wid; i < na; i += nw) {
+        const int k = list[i];
         const int p = js.p[k], q = js.q[k];
         const T c = js.c[k], s = js.s[k];
-        const T vp = CT[p * ldc + j], vq = CT[q * ldc + j];
-        CT[p * ldc + j] = c * vp - s * vq;
-        CT[q * ldc + j] = s * vp + c * vq;
+        for (int k2 = lane; k2 < half; k2 += 32) {
+          if (js.act[k2] && k2 < k) continue;
+          const int p2 = js.p[k2], q2 = js.q[k2];
+          const T c2 = js.c[k2], s2 = js.s[k2];
+          const T b00 = A[p * lda + p2], b01 = A[p * lda + q2];
+          const T b10 = A[q * lda + p2], b11 = A[q * lda + q2];
+          const T t00 = b00 * c2 - b01 * s2, t01 = b00 * s2 + b01 * c2;
+          const T t10 = b10 * c2 - b11 * s2, t11 = b10 * s2 + b11 * c2;
+          const T x00 = c * t00 - s * t10, x01 = c * t01 - s * t11;
+          const T x10 = s * t00 + c * t10, x11 = s * t01 + c * t11;
+          if (k == k2) {
+            A[p * lda + p] = x00;
+            A[q * lda + q] = x11;
+            A[p * lda + q] = T(0);
+            A[q * lda + p] = T(0);
+          } else {
+            A[p * lda + p2] = x00; A[p * lda + q2] = x01;
+            A[q * lda + p2] = x10; A[q * lda + q2] = x11;
+            A[p2 * lda + p] = x00; A[q2 * lda + p] = x01;
+            A[p2 * lda + q] = x10; A[q2 * lda + q] = x11;
+          }
+        }
+      }
+      // rotate the rows p, q of CT: one warp per active pair, lanes over columns
+      for (int i = wid; i < na; i += nw) {
+        const int k = list[i];
+        const int p = js.p[k], q = js.q[k];
+        const T c = js.c[k], s = js.s[k];
+        T* rp = CT + p * ldc;
+        T* rq = CT + q * ldc;
+        for (int j = lane; j < ncol; j += 32) {
+          const T vp = rp[j], vq = rq[j];
+          rp[j] = c * vp - s * vq;
+          rq[j] = s * vp + c * vq;
+        }
       }
       __syncthreads();
     }

@@ -20,12 +20,14 @@ namespace fmo {
 
 __global__ void cn_kernel(int n_atoms, const double* __restrict__ xyz, const int* __restrict__ elem,
                           const DevElem* __restrict__ el, GParams g, double* __restrict__ cn) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per atom a, lanes over the partners b
+  const int lane = threadIdx.x & 31;
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (a >= n_atoms) return;
   const double xa = xyz[3 * a], ya = xyz[3 * a + 1], za = xyz[3 * a + 2];
   const double ra = el[elem[a]].rcov;
   double s = 0.0;
-  for (int b = 0; b < n_atoms; ++b) {
+  for (int b = lane; b < n_atoms; b += 32) {
     if (b == a) continue;
     const double dx = xyz[3 * b] - xa, dy = xyz[3 * b + 1] - ya, dz = xyz[3 * b + 2] - za;
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -33,7 +35,8 @@ __global__ void cn_kernel(int n_atoms, const double* __restrict__ xyz, const int
     const double arg = -g.cn_k1 * (g.cn_k2 * (ra + el[elem[b]].rcov) / r - 1.0);
     s += 1.0 / (1.0 + exp(arg));
   }
-  cn[a] = s;
+  s = warp_sum(s);
+  if (lane == 0) cn[a] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -76,6 +79,11 @@ __device__ void build_maps(const Nmer& nm, const FragTab ft, const int* __restri
 // p = a + b at P = (aA + bB)/p; s-s overlap (pi/p)^{3/2} exp(-ab/p R^2); a p
 // factor contributes (P - A)_i, a pair of p factors (P-A)_i (P-B)_j + d_ij/2p.
 
+// Primitive pairs whose Gaussian factor exp(-ab/p R^2) is below e^-46 (about
+// 1e-20) are skipped.  prim (optional) holds the geometry-free factors of
+// every primitive pair (PrimPair); without it they are formed here.
+constexpr double kPrimScreen = 46.0;
+
 // With mono != nullptr the intra-fragment blocks are copied from the monomer
 // pass (identical: the CN is that of the whole system) and only pairs of
 // atoms in different fragments are evaluated.
@@ -85,7 +93,8 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
                                  const DevElem* __restrict__ el, const double* __restrict__ kab,
                                  int ne, GParams g, double* __restrict__ S,
                                  double* __restrict__ H0, const Nmer* __restrict__ mono,
-                                 const double* __restrict__ mono_S, const double* __restrict__ mono_H0) {
+                                 const double* __restrict__ mono_S, const double* __restrict__ mono_H0,
+                                 const PrimPair* __restrict__ prim) {
   const Nmer nm = nmers[blockIdx.y];
   __shared__ int s_glob[512];
   __shared__ int s_ao0[512];
@@ -162,13 +171,24 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
 #pragma unroll
           for (int v = 0; v < 3; ++v) blk[u][v] = 0.0;
         for (int pa = 0; pa < EA.nprim[sa]; ++pa) {
-          const double a = EA.alpha[sa][pa], ca = EA.cn[sa][pa];
           for (int pb = 0; pb < EB.nprim[sb]; ++pb) {
-            const double b = EB.alpha[sb][pb], cb = EB.cn[sb][pb];
-            const double p = a + b, ip = 1.0 / p;
-            const double s00 = ca * cb * pow(M_PI * ip, 1.5) * exp(-a * b * ip * r2);
-            const double PA[3] = {b * ip * dx, b * ip * dy, b * ip * dz};
-            const double PB[3] = {-a * ip * dx, -a * ip * dy, -a * ip * dz};
+            PrimPair q;
+            if (prim) {
+              q = prim[prim_pair_index(ne, elem[ga], elem[gb], sa, sb, pa, pb)];
+            } else {
+              const double a = EA.alpha[sa][pa], b = EB.alpha[sb][pb];
+              q.ip = 1.0 / (a + b);
+              q.abp = a * b * q.ip;
+              q.ap = a * q.ip;
+              q.bp = b * q.ip;
+              q.pref = EA.cn[sa][pa] * EB.cn[sb][pb] * (M_PI * q.ip) * sqrt(M_PI * q.ip);
+            }
+            const double xe = q.abp * r2;
+            if (xe > kPrimScreen) continue;   // exp(-xe) < 1e-20
+            const double s00 = q.pref * exp(-xe);
+            const double ip = q.ip;
+            const double PA[3] = {q.bp * dx, q.bp * dy, q.bp * dz};
+            const double PB[3] = {-q.ap * dx, -q.ap * dy, -q.ap * dz};
             if (la == 0 && lb == 0) {
               blk[0][0] += s00;
             } else if (la == 1 && lb == 0) {
@@ -212,20 +232,20 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
   }
 }
 
-// x^(-1/2) in FP64 from the FP32 hardware estimate and two Newton-Raphson
-// steps y <- y (3 - x y^2) / 2 (each squares the relative error: ~1e-7 ->
-// ~1e-14 -> rounding level).  x must be a positive normal FP32 number.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  double y = (double)rsqrtf((float)x);
-  y = y * (1.5 - 0.5 * x * y * y);
-  y = y * (1.5 - 0.5 * x * y * y);
-  return y;
+// x^(-1/2) in FP64 from the FP32 hardware estimate y0 and one third-order
+// correction: with r = 1 - x y0^2 (|r| ~ 1e-7; y0^2 is exact in FP64),
+// y = y0 (1 + r/2 + 3r^2/8) has relative error O(r^3), below FP64 rounding.
+// x must be a positive normal FP32 number.
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  const double y0 = (double)rsqrtf((float)x);
+  const double r = fma(-x, y0 * y0, 1.0);
+  return fma(y0 * r, fma(0.375, r, 0.5), y0);
 }
 
 // gamma of Eqs. 4-5 from the distance and the two shell hardnesses.
 __device__ __forceinline__ double gamma_fn(double r2, double inv_eta_a, double inv_eta_b, double kg) {
   const double ie = 0.5 * (inv_eta_a + inv_eta_b);   // 1/eta, eta = harmonic mean
-  if (kg == 2.0) return rsqrt_nr(r2 + ie * ie);
+  if (kg == 2.0) return rsqrt_fp64(r2 + ie * ie);
   return pow(pow(sqrt(r2), kg) + pow(ie, kg), -1.0 / kg);
 }
 
@@ -377,8 +397,10 @@ struct SccArgs {
   int reortho32;     // single step: one FP32 Newton-Schulz step before the iteration
   double jac_hint;   // SCC residual before this launch (sets the first Jacobi threshold)
   int fp64_finish;   // mixed: stop after this many FP64 iterations (0: converge in FP64)
+  int energy_finish; // mixed n-mers: end with the FP64 energy of the FP32-converged density
   int cold_steps;    // Newton-Schulz steps allowed for the cold start (far from orthonormal: more)
   int first_rot;     // the first iteration may use the rotation update (warm rows)
+  double first_jac_tol;  // > 0: Jacobi threshold of the first FP32 iteration (warm rows)
   double* trace;     // optional: residual per iteration of the first n-mer in the order
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
@@ -404,7 +426,7 @@ struct SccSmem {
   double* focc;
   int* occ;
   int* virt;     // rows with zero occupation (orbital-rotation updates)
-  int* misc;     // [0] number of virt rows, [1] rotation update allowed
+  int* misc;     // [0] number of virt rows, [1] rotation update allowed, [2] rows to rotate, [3] trace
   double* bro;   // Broyden small matrix (kHist*kHist + 2*kHist)
   NmerMaps mp;
   int* jsp;
@@ -635,6 +657,38 @@ __device__ void broyden_step(int nsh, int it, double* hist, SccSmem& sm, int& hc
   __syncthreads();
 }
 
+// Energy of Eq. 2 without the -TS term from the output shell charges
+// sm.dqout and the per-shell band energies sm.sig (sum_mu in shell P_mu,nu
+// H0_nu,mu); also max |dq_out - dq_in| (into *diff_out).
+__device__ double energy_of_output(const Nmer& nm, const SccArgs& ar, SccSmem& sm, double* diff_out) {
+  const int nsh = nm.nsh, nat = nm.nat;
+  const double* G = ar.gam + nm.gam;
+  for (int a = threadIdx.x; a < nat; a += blockDim.x) sm.dqat[a] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nsh; ++s) sm.dqat[sm.mp.sh_at[s]] += sm.dqout[s];
+  }
+  __syncthreads();
+  double part = 0.0, dmax = 0.0;
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = wid; s < nsh; s += nw) {
+      double v = 0.0;
+      for (int t = lane; t < nsh; t += 32) v += G[(size_t)s * nsh + t] * sm.dqout[t];
+      v = warp_sum(v);
+      if (lane == 0) {
+        part += sm.sig[s] + 0.5 * sm.dqout[s] * v;
+        dmax = fmax(dmax, fabs(sm.dqout[s] - sm.dqin[s]));
+      }
+    }
+  }
+  for (int a = threadIdx.x; a < nat; a += blockDim.x)
+    part -= sm.g3[a] * sm.dqat[a] * sm.dqat[a] * sm.dqat[a] / 3.0;
+  const double e_sum = block_sum(part, sm.red);
+  *diff_out = block_max(dmax, sm.red);
+  return e_sum;
+}
+
 template <typename T>
 struct PrecPtrs {
   T* CT;
@@ -719,6 +773,7 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   int nocc = 0;
   double mts = 0.0;
   bool rotated = false;
+  if (threadIdx.x == 0) sm.misc[3] = -1;   // -1: rotation step, else Jacobi sweeps
   if (allow_rot) {
     // Warm start: the rows of CT are eigenvectors of the previous Fock
     // matrix, so A is nearly diagonal.  With integer occupations only the
@@ -765,6 +820,7 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     JacobiScratch<T> js{sm.jsp, sm.jsq, reinterpret_cast<T*>(sm.jsc), reinterpret_cast<T*>(sm.jss), sm.jsact};
     const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
     if (sw < 0 && sizeof(T) == 8) *jac_fail = 1;
+    if (threadIdx.x == 0) sm.misc[3] = sw;   // sweeps (diagnostic trace)
     for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
     __syncthreads();
     mts = fermi_step(n, nm.nel, ar.g.kT, sm, &nocc);
@@ -797,33 +853,8 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     }
   }
   __syncthreads();
-  // energy of Eq. 2 from the output density
-  for (int a = threadIdx.x; a < nat; a += blockDim.x) sm.dqat[a] = 0.0;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < nsh; ++s) sm.dqat[sm.mp.sh_at[s]] += sm.dqout[s];
-  }
-  __syncthreads();
-  double part = 0.0, dmax = 0.0;
-  {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int s = wid; s < nsh; s += nw) {
-      double v = 0.0;
-      for (int t = lane; t < nsh; t += 32) v += G[(size_t)s * nsh + t] * sm.dqout[t];
-      v = warp_sum(v);
-      if (lane == 0) {
-        part += sm.sig[s] + 0.5 * sm.dqout[s] * v;
-        dmax = fmax(dmax, fabs(sm.dqout[s] - sm.dqin[s]));
-      }
-    }
-  }
-  for (int a = threadIdx.x; a < nat; a += blockDim.x)
-    part -= sm.g3[a] * sm.dqat[a] * sm.dqat[a] * sm.dqat[a] / 3.0;
   (void)eb_local;
-  const double e_sum = block_sum(part, sm.red);
-  const double dm = block_max(dmax, sm.red);
-  *diff_out = dm;
-  return e_sum + mts;
+  return energy_of_output(nm, ar, sm, diff_out) + mts;
 }
 
 // CT <- (M^{-1/2}) CT with M = CT S CT^T, by Newton-Schulz steps
@@ -879,6 +910,81 @@ __device__ void reortho_handover(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
   if (err > 1e-6) reorthonormalise<double>(nm, ar, sm, pd, 3, 1e-13);
 }
 
+// FP64 energy of the density held by FP32 eigenvector rows (mixed
+// precision, dimers and trimers).  The FP32 phase has converged the n-mer to
+// a charge residual near FP32 rounding.  Only the occupied rows c_k enter
+// P = sum_k f_k c_k c_k^T, so only they are made S-orthonormal in FP64:
+// W = C_o S and Y = C_o H0 are formed in FP64 once, M = W C_o^T (no x no),
+// and each Newton-Schulz step X <- X - 1/2 (M - I) X is applied to C_o, W and
+// Y together (the small (M - I) X products in FP32).  Then the Mulliken
+// populations (P S)_mu,mu = sum_k f_k C_k,mu W_k,mu (Eq. 3) and the band
+// energy sum_k f_k C_k . Y_k give E_el of Eq. 2 from sm.dqout.  Rounding of
+// the FP32 rows is a rotation of the occupied space by ~1e-7 once the rows
+// are orthonormal, and the n-mer energy in its fixed ESP is stationary under
+// such rotations, so it enters the energy at second order.
+// ct32: the FP32 rows in global memory; wf1, wf2: n x n FP32 scratch.
+__device__ double fp64_energy_of_rows(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<double> pd,
+                                      const float* ct32, float* wf1, float* wf2) {
+  const int n = nm.n, nsh = nm.nsh;
+  const double* Sm = ar.S + nm.mat;
+  const double* Hm = ar.H0 + nm.mat;
+  int no = 0;
+  const double mts = fermi_step(n, nm.nel, ar.g.kT, sm, &no);   // occupations of the last FP32 iteration
+  double* Co = pd.CT;   // no x n
+  double* W = pd.W1;    // no x n
+  double* Y = pd.W2;    // no x n
+  double* M = pd.A;     // no x no
+  for (long long e = threadIdx.x; e < (long long)no * n; e += blockDim.x)
+    Co[e] = double(ct32[(long long)sm.occ[e / n] * n + e % n]);
+  __syncthreads();
+  double* gemm = reinterpret_cast<double*>(sm.gemm);
+  float* gf = reinterpret_cast<float*>(sm.gemm);
+  block_gemm<double>(no, n, n, Co, n, 1, Sm, n, 1, W, n, nullptr, nullptr, nullptr, gemm);   // W = C_o S
+  block_gemm<double>(no, n, n, Co, n, 1, Hm, n, 1, Y, n, nullptr, nullptr, nullptr, gemm);   // Y = C_o H0
+  double err0 = 0.0;
+  for (int step = 0; step < 2; ++step) {
+    block_gemm<double>(no, no, n, W, n, 1, Co, n, 1, M, no, nullptr, nullptr, nullptr, gemm);   // M = C_o S C_o^T
+    double err = 0.0;
+    for (long long e = threadIdx.x; e < (long long)no * no; e += blockDim.x) {
+      const double d = M[e] - ((e / no) == (e % no) ? 1.0 : 0.0);
+      wf1[e] = float(d);
+      err = fmax(err, fabs(d));
+    }
+    err = block_max(err, sm.red);
+    if (step == 0) err0 = err;
+    else if (err0 <= 1e-8) break;   // one step left ~err0^2: done
+    double* X[3] = {Co, W, Y};
+    for (int x = 0; x < 3; ++x) {
+      block_gemm<float, double>(no, n, no, wf1, no, 1, X[x], 1, n, wf2, n, nullptr, nullptr, nullptr, gf);
+      for (long long e = threadIdx.x; e < (long long)no * n; e += blockDim.x) X[x][e] -= 0.5 * double(wf2[e]);
+      __syncthreads();
+    }
+  }
+  // per-AO population and band energy, one thread per AO (coalesced rows)
+  double* pop = reinterpret_cast<double*>(sm.jsc);
+  double* band = reinterpret_cast<double*>(sm.jss);
+  for (int mu = threadIdx.x; mu < n; mu += blockDim.x) {
+    double p = 0.0, b = 0.0;
+    for (int k = 0; k < no; ++k) {
+      const double fc = sm.focc[sm.occ[k]] * Co[(long long)k * n + mu];
+      p += fc * W[(long long)k * n + mu];
+      b += fc * Y[(long long)k * n + mu];
+    }
+    pop[mu] = p;
+    band[mu] = b;
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsh; s += blockDim.x) {
+    double p = 0.0, b = 0.0;
+    for (int k = sm.mp.sh_ao0[s]; k < sm.mp.sh_ao0[s + 1]; ++k) { p += pop[k]; b += band[k]; }
+    sm.dqout[s] = p - sm.q0[s];
+    sm.sig[s] = b;
+  }
+  __syncthreads();
+  double diff = 0.0;
+  return energy_of_output(nm, ar, sm, &diff) + mts;
+}
+
 // Jacobi threshold (relative to max |A_ii|) for an SCC iteration whose
 // previous residual was `last`: rotations far below the SCC error change
 // nothing the loop needs, so early iterations rotate only the large elements.
@@ -894,6 +1000,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   const int a_bytes = (ar.a_smem_d ? int(sizeof(double)) : (ar.a_smem_f ? int(sizeof(float)) : 0)) *
                       ((ar.max_n + (ar.max_n & 1)) * (ar.max_n + (ar.max_n & 1)));
   SccSmem sm = carve_scc_smem(smem_raw, ar.max_n, ar.max_nsh, ar.max_nat, a_bytes);
+  const long long t_start = clock64();
   build_maps(nm, ar.ft, ar.elem, ar.atom_sh0, ar.el, sm.mp);
   // per-shell / per-atom constants
   for (int s = threadIdx.x; s < nsh; s += blockDim.x) {
@@ -1003,25 +1110,38 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   bool fresh64 = false;
   int n64 = 0;
   bool fp32_converged = false;
+  bool energy_done = false;
   if (!ar.single_step && ar.cold_refine) {
     // the starting rows made S-orthonormal to the working precision
     if (phase == 0) reorthonormalise<float>(nm, ar, sm, pf, ar.cold_steps, 1e-6);
     else reorthonormalise<double>(nm, ar, sm, pd, 4, 1e-14);
   }
   if (!ar.single_step && phase == 0 && ct_smem) load_ct_smem();
+  long long t_it = clock64();
+  if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0) ar.trace[1024] = double(t_it - t_start);
   for (it = (ar.single_step ? ar.max_iter + 2 : 1); it <= ar.max_iter; ++it) {
     double diff = 0.0;
     if (phase == 0) {
       if (it32 > 0 && it32 % 4 == 0) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
-      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(last, ar.jacobi_tol_f), &jac_fail, &diff,
-                                  it > 1 || !ar.cold_refine || ar.first_rot);
+      // a warm start only needs near-canonical rows before the rotation
+      // updates take over: its first eigen-solve may be loose
+      const double thr = (it == 1 && ar.first_jac_tol > 0) ? ar.first_jac_tol : jacobi_threshold(last, ar.jacobi_tol_f);
+      e_el = scc_iteration<float>(nm, ar, sm, pf, thr, &jac_fail, &diff, it > 1 || !ar.cold_refine || ar.first_rot);
       ++it32;
     } else {
       e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(last, ar.jacobi_tol_d), &jac_fail, &diff,
                                    it > 1 || !ar.cold_refine, ar.precision == 1 ? ctf_g : nullptr, pf.W1, pf.W2);
     }
     last = diff;
-    if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 512) ar.trace[it] = phase ? diff : -diff;
+    if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 512) {
+      // per iteration: residual (negative in FP32), Jacobi sweeps (-1 =
+      // rotation step) and SM cycles
+      const long long t1 = clock64();
+      ar.trace[it] = phase ? diff : -diff;
+      ar.trace[512 + it] = sm.misc[3];
+      ar.trace[1024 + it] = double(t1 - t_it);
+      t_it = t1;
+    }
     if (phase == 1 && ar.precision == 1 && ar.fp64_finish > 0 && ++n64 >= ar.fp64_finish) {
       // FP64 energy of the FP32-converged charges (variational for n-mers
       // in a fixed ESP); the loop ends here
@@ -1032,6 +1152,20 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     // loop decisions are made block-uniform with barrier votes (thread 0's
     // timer read decides the deadline)
     if (__syncthreads_or(!isfinite(e_el) || !isfinite(diff))) { status = FMO_SCC_NAN_CODE; break; }
+    if (ar.energy_finish && __syncthreads_and(phase == 0 && (diff < ar.switch_tol || it32 >= ar.fp32_cap))) {
+      // n-mer in mixed precision: FP64 energy of the FP32-converged density
+      const long long tf = clock64();
+      if (ct_smem) {
+        for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) ctf_g[e] = pf.CT[e];
+        __syncthreads();
+      }
+      e_el = fp64_energy_of_rows(nm, ar, sm, pd, ctf_g, pf.W1, pf.W2);
+      status = diff < ar.switch_tol ? FMO_SCC_CONVERGED_CODE : FMO_SCC_MAX_ITER_CODE;
+      if (__syncthreads_or(!isfinite(e_el))) status = FMO_SCC_NAN_CODE;
+      if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0) ar.trace[1535] = double(clock64() - tf);
+      energy_done = true;
+      break;
+    }
     if (__syncthreads_and(phase == 1 && have_prev && diff < ar.tol && fabs(e_el - e_prev) < ar.etol)) {
       status = FMO_SCC_CONVERGED_CODE;
       break;
@@ -1066,7 +1200,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   // warm start
   if (ar.precision == 1 && phase == 1) {
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) ctf_g[e] = float(pd.CT[e]);
-  } else if (ar.precision == 1 && ct_smem) {
+  } else if (ar.precision == 1 && ct_smem && !energy_done) {
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) ctf_g[e] = pf.CT[e];
   }
   // results
@@ -1095,46 +1229,52 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
 // shells lambda staged through shared memory; each chunk writes its partial
 // sums, which phi_reduce_kernel adds in chunk order (deterministic).
 
+// T = double: the potential in FP64.  T = float: an FP32 estimate (pair terms
+// and the sum over one chunk in FP32) for the FP32 phase of the mixed-
+// precision monomer loop, whose charges are only FP32-accurate anyway.
+template <typename T>
 __global__ void __launch_bounds__(256) phi_kernel(int n_sh, int chunk, const double* __restrict__ xyz,
                                                   const int* __restrict__ sh_atom,
                                                   const double* __restrict__ sh_inv_eta,
                                                   const double* __restrict__ dq, GParams g,
                                                   double* __restrict__ part) {
-  __shared__ double tx[256], ty[256], tz[256], te[256], tq[256];
+  __shared__ T tx[256], ty[256], tz[256], te[256], tq[256];
   const int mu = blockIdx.x * blockDim.x + threadIdx.x;
-  double x = 0, y = 0, z = 0, ie = 1.0;
+  T x = 0, y = 0, z = 0, ie = 1;
   if (mu < n_sh) {
     const int a = sh_atom[mu];
-    x = xyz[3 * a]; y = xyz[3 * a + 1]; z = xyz[3 * a + 2];
-    ie = sh_inv_eta[mu];
+    x = T(xyz[3 * a]); y = T(xyz[3 * a + 1]); z = T(xyz[3 * a + 2]);
+    ie = T(sh_inv_eta[mu]);
   }
   const int l0 = blockIdx.y * chunk, l1 = min(n_sh, l0 + chunk);
-  double acc = 0.0;
+  T acc = 0;
   for (int t0 = l0; t0 < l1; t0 += 256) {
     const int l = t0 + threadIdx.x;
     if (l < l1) {
       const int b = sh_atom[l];
-      tx[threadIdx.x] = xyz[3 * b]; ty[threadIdx.x] = xyz[3 * b + 1]; tz[threadIdx.x] = xyz[3 * b + 2];
-      te[threadIdx.x] = sh_inv_eta[l];
-      tq[threadIdx.x] = dq[l];
+      tx[threadIdx.x] = T(xyz[3 * b]); ty[threadIdx.x] = T(xyz[3 * b + 1]); tz[threadIdx.x] = T(xyz[3 * b + 2]);
+      te[threadIdx.x] = T(sh_inv_eta[l]);
+      tq[threadIdx.x] = T(dq[l]);
     }
     __syncthreads();
     const int m = min(256, l1 - t0);
     if (g.k_g == 2.0) {
       for (int k = 0; k < m; ++k) {
-        const double dx = x - tx[k], dy = y - ty[k], dz = z - tz[k];
-        const double e = 0.5 * (ie + te[k]);
-        acc = fma(rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, e * e)))), tq[k], acc);
+        const T dx = x - tx[k], dy = y - ty[k], dz = z - tz[k];
+        const T e = T(0.5) * (ie + te[k]);
+        const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e * e)));
+        if constexpr (sizeof(T) == 8) acc = fma(rsqrt_fp64(r2), tq[k], acc);
+        else acc = fma(rsqrtf(r2), tq[k], acc);
       }
     } else {
       for (int k = 0; k < m; ++k) {
-        const double dx = x - tx[k], dy = y - ty[k], dz = z - tz[k];
-        acc += gamma_fn(dx * dx + dy * dy + dz * dz, ie, te[k], g.k_g) * tq[k];
+        const double dx = double(x) - double(tx[k]), dy = double(y) - double(ty[k]), dz = double(z) - double(tz[k]);
+        acc += T(gamma_fn(dx * dx + dy * dy + dz * dz, double(ie), double(te[k]), g.k_g) * double(tq[k]));
       }
     }
     __syncthreads();
   }
-  if (mu < n_sh) part[(size_t)blockIdx.y * n_sh + mu] = acc;
+  if (mu < n_sh) part[(size_t)blockIdx.y * n_sh + mu] = double(acc);
 }
 
 __global__ void phi_reduce_kernel(int n_sh, int n_chunk, const double* __restrict__ part,
@@ -1295,17 +1435,21 @@ __global__ void global_mix_kernel(int n, double* __restrict__ x, const double* _
   double* a = sa;
   double* c = sa + kHist * kHist;
   double* gv = c + kHist;
-  for (int q = 0; q < m * m + m; ++q) {
-    double v = 0.0;
-    if (q < m * m) {
-      const int k = (hhead + q / m) % kHist, l = (hhead + q % m) % kHist;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) v += dF[(size_t)k * n + i] * dF[(size_t)l * n + i];
-    } else {
-      const int k = (hhead + (q - m * m)) % kHist;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) v += dF[(size_t)k * n + i] * pF[i];
+  {
+    // the m^2 + m dot products, one warp each (fixed order: deterministic)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = wid; q < m * m + m; q += nw) {
+      double v = 0.0;
+      if (q < m * m) {
+        const int k = (hhead + q / m) % kHist, l = (hhead + q % m) % kHist;
+        for (int i = lane; i < n; i += 32) v += dF[(size_t)k * n + i] * dF[(size_t)l * n + i];
+      } else {
+        const int k = (hhead + (q - m * m)) % kHist;
+        for (int i = lane; i < n; i += 32) v += dF[(size_t)k * n + i] * pF[i];
+      }
+      v = warp_sum(v);
+      if (lane == 0) { if (q < m * m) a[q] = v; else c[q - m * m] = v; }
     }
-    v = block_sum(v, red);
-    if (threadIdx.x == 0) { if (q < m * m) a[q] = v; else c[q - m * m] = v; }
   }
   __syncthreads();
   if (threadIdx.x == 0 && m > 0) {
@@ -1420,7 +1564,7 @@ __global__ void gather_xyz_kernel(int n_atoms, const int* __restrict__ perm, con
 
 cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int* elem, const DevElem* el,
                       GParams g, double* cn) {
-  cn_kernel<<<(n_atoms + 127) / 128, 128, 0, st>>>(n_atoms, xyz, elem, el, g, cn);
+  cn_kernel<<<(int)(((long long)n_atoms * 32 + 255) / 256), 256, 0, st>>>(n_atoms, xyz, elem, el, g, cn);
   LAUNCH_CHECK();
   return cudaSuccess;
 }
@@ -1428,13 +1572,13 @@ cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int
 cudaError_t launch_integrals(cudaStream_t st, int n_nmer, int max_pairs, const Nmer* nmers, FragTab ft,
                              const double* xyz, const int* elem, const int* atom_sh0, const double* cn,
                              const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0,
-                             const Nmer* mono, const double* mono_S, const double* mono_H0) {
+                             const Nmer* mono, const double* mono_S, const double* mono_H0, const PrimPair* prim) {
   if (n_nmer == 0) return cudaSuccess;
   const int chunks = max(1, min(64, (max_pairs + 127) / 128));
   for (int b0 = 0; b0 < n_nmer; b0 += 65535) {
     dim3 grid(chunks, min(65535, n_nmer - b0));
     integrals_kernel<<<grid, 128, 0, st>>>(nmers + b0, ft, xyz, elem, atom_sh0, cn, el, kab, ne, g, S, H0, mono,
-                                           mono_S, mono_H0);
+                                           mono_S, mono_H0, prim);
     LAUNCH_CHECK();
   }
   return cudaSuccess;
@@ -1498,7 +1642,7 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
   ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho;
   ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.trace = L.trace;
-  ar.fp64_finish = L.fp64_finish; ar.cold_steps = L.cold_steps; ar.first_rot = L.first_rot; ar.tol = L.tol; ar.etol = L.etol;
+  ar.fp64_finish = L.fp64_finish; ar.energy_finish = L.energy_finish; ar.first_jac_tol = L.first_jac_tol; ar.cold_steps = L.cold_steps; ar.first_rot = L.first_rot; ar.tol = L.tol; ar.etol = L.etol;
   ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
   ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
   ar.max_n = L.max_n; ar.max_nsh = L.max_nsh; ar.max_nat = L.max_nat;
@@ -1528,11 +1672,13 @@ cudaError_t launch_warm_start(cudaStream_t st, int n_nmer, const Nmer* nmers, co
 }
 
 cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
-                       const double* dq, GParams g, double* phi, double* part) {
+                       const double* dq, GParams g, double* phi, double* part, int use_float) {
   const int nc = phi_chunks(n_sh);
   const int chunk = (((n_sh + nc - 1) / nc) + 255) / 256 * 256;
   const int ncu = (n_sh + chunk - 1) / chunk;
-  phi_kernel<<<dim3((n_sh + 255) / 256, ncu), 256, 0, st>>>(n_sh, chunk, xyz, sh_atom, sh_inv_eta, dq, g, part);
+  const dim3 grid((n_sh + 255) / 256, ncu);
+  if (use_float) phi_kernel<float><<<grid, 256, 0, st>>>(n_sh, chunk, xyz, sh_atom, sh_inv_eta, dq, g, part);
+  else phi_kernel<double><<<grid, 256, 0, st>>>(n_sh, chunk, xyz, sh_atom, sh_inv_eta, dq, g, part);
   LAUNCH_CHECK();
   phi_reduce_kernel<<<(n_sh + 255) / 256, 256, 0, st>>>(n_sh, ncu, part, phi);
   LAUNCH_CHECK();

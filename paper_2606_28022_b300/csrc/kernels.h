@@ -58,8 +58,10 @@ struct SccLaunch {
   double jac_hint;
   double* trace;
   int fp64_finish;
+  int energy_finish;
   int cold_steps;
   int first_rot;
+  double first_jac_tol;
   double tol, etol, switch_tol;
   double jacobi_tol_d, jacobi_tol_f;
   const unsigned long long* t0;   // device timestamp of the run start
@@ -74,7 +76,7 @@ cudaError_t launch_integrals(cudaStream_t st, int n_nmer, int max_pairs, const N
                              const double* xyz, const int* elem, const int* atom_sh0, const double* cn,
                              const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0,
                              const Nmer* mono = nullptr, const double* mono_S = nullptr,
-                             const double* mono_H0 = nullptr);
+                             const double* mono_H0 = nullptr, const PrimPair* prim = nullptr);
 cudaError_t launch_gamma(cudaStream_t st, int n_nmer, int max_nsh, const Nmer* nmers, FragTab ft,
                          const double* xyz, const int* elem, const int* sh_atom, const double* sh_inv_eta,
                          GParams g, double* gam);
@@ -86,7 +88,7 @@ cudaError_t launch_warm_start(cudaStream_t st, int n_nmer, const Nmer* nmers, co
                               float* ct);
 int phi_chunks(int n_sh);
 cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
-                       const double* dq, GParams g, double* phi, double* part);
+                       const double* dq, GParams g, double* phi, double* part, int use_float = 0);
 cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);
 cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, const double* bounds,
                                  double cut, double* rmin);

@@ -55,7 +55,7 @@ class FmoOptions(C.Structure):
                 ("schedule", C.c_int32), ("monomer_loop", C.c_int32), ("dimer_cut", C.c_double),
                 ("trimer_cut", C.c_double), ("scc_tol", C.c_double), ("e_tol", C.c_double),
                 ("outer_tol", C.c_double), ("mixed_switch_tol", C.c_double),
-                ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("reserved_", C.c_int32)]
+                ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("nmer_finish", C.c_int32)]
 
 
 class FmoStats(C.Structure):
@@ -164,6 +164,8 @@ def options(**kw) -> FmoOptions:
             v = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[v]
         if k == "monomer_loop" and isinstance(v, str):
             v = {"global": 0, "nested": 1}[v]
+        if k == "nmer_finish" and isinstance(v, str):
+            v = {"energy": 0, "iterate": 1}[v]
         setattr(o, k, v)
     return o
 
