@@ -393,11 +393,13 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.first_rot = warm_nmer ? 1 : 0;
   L.first_jac_tol = warm_nmer ? 1e-3 : 0.0;
   L.trace = nullptr;
-  // FMO_DEBUG=2 traces the first (largest) dimer, FMO_DEBUG=3 the first trimer
-  const bool tracing = debug_level() >= 2 && pass_id == std::min(2, debug_level() - 1);
+  // FMO_DEBUG=2 traces the first (largest) dimer, FMO_DEBUG=3 the first
+  // trimer, FMO_DEBUG=4 the first monomer (every launch of the monomer loop)
+  const int dl = debug_level();
+  const bool tracing = (dl == 2 && pass_id == 1) || (dl == 3 && pass_id == 2) || (dl == 4 && pass_id == 0);
   if (tracing) {
-    CK(ctx->d_trace.ensure(sizeof(double) * 1536));
-    CK(cudaMemsetAsync(ctx->d_trace.p, 0, sizeof(double) * 1536, st));
+    CK(ctx->d_trace.ensure(sizeof(double) * kTraceLen));
+    CK(cudaMemsetAsync(ctx->d_trace.p, 0, sizeof(double) * kTraceLen, st));
     L.trace = ctx->d_trace.as<double>();
   }
   L.tol = o.scc_tol; L.etol = o.e_tol; L.switch_tol = o.mixed_switch_tol;
@@ -429,8 +431,8 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   cudaEventDestroy(e1);
   ctx->stats.ms_scc[pass_id] += ms;
   if (tracing) {
-    std::vector<double> tr(1536);
-    CK(d2h(tr.data(), ctx->d_trace.p, sizeof(double) * 1536, st));
+    std::vector<double> tr(kTraceLen);
+    CK(d2h(tr.data(), ctx->d_trace.p, sizeof(double) * kTraceLen, st));
     CK(sync_stream(st));
     int last = 1;
     while (last < 511 && tr[last + 1] != 0.0) ++last;
@@ -442,6 +444,11 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
     fprintf(stderr, "\n[fmo] Mcycles: start %.2f, per iteration:", tr[1024] * 1e-6);
     for (int i = 1; i <= last; ++i) fprintf(stderr, " %.2f", tr[1024 + i] * 1e-6);
     fprintf(stderr, ", FP64 energy finish %.2f\n", tr[1535] * 1e-6);
+    fprintf(stderr, "[fmo] Mcycles summed over iterations: Fock %.2f, transform %.2f, occupations %.2f, "
+            "rotation/Jacobi %.2f, density %.2f, populations %.2f, energy %.2f\n",
+            tr[kTraceParts] * 1e-6, tr[kTraceParts + 1] * 1e-6, tr[kTraceParts + 2] * 1e-6,
+            tr[kTraceParts + 3] * 1e-6, tr[kTraceParts + 4] * 1e-6, tr[kTraceParts + 5] * 1e-6,
+            tr[kTraceParts + 6] * 1e-6);
   }
   ctx->stats.scc_launches[pass_id] += 1;
   for (int i = 0; i < nn; ++i) {

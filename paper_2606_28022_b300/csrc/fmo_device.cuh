@@ -141,84 +141,136 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 //   a(m,k) = A[m*sam + ka*sak] * (kscale ? kscale[k] : 1),  ka = kidx ? kidx[k] : k,
 //   b(n,k) = B[n*sbn + kb*sbk],                             kb = kidx_b ? kidx_b[k] : k
 // (B may be stored in a wider type TB; it is rounded to T on load).
-// 64x64 output tiles, BK = 16, 256 threads with 4x4 outputs each.  Operand
-// tiles are staged in shared memory (smem: 2*16*64 elements of T).
+// 256 threads as a 16 x 16 grid, each computing TM x TN outputs of a
+// (16 TM) x (16 TN) tile; BK = 16.  The tile edge (64 or 80) is chosen per
+// dimension to waste the least padding (an n = 76 monomer fits one 80-row
+// tile instead of two 64-row tiles).  The next k-slice is fetched into
+// registers while the current one is multiplied from shared memory (smem:
+// kGemmSmemElems elements of T).  Ends with __syncthreads().
 
-template <typename T, typename TB = T>
-__device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long long sam,
-                           long long sak, const TB* __restrict__ B, long long sbn, long long sbk,
-                           T* __restrict__ C, long long ldc, const int* __restrict__ kidx,
-                           const int* __restrict__ kidx_b, const double* __restrict__ kscale, T* smem) {
-  constexpr int BM = 64, BN = 64, BK = 16;
-  T* As = smem;             // [BK][BM]
-  T* Bs = smem + BK * BM;   // [BK][BN]
+constexpr int kGemmSmemElems = 2 * 16 * (80 + 1);
+
+template <typename T, typename TB, int TM, int TN>
+__device__ __forceinline__ void block_gemm_tile(int M, int N, int K, const T* __restrict__ A, long long sam,
+                                                long long sak, const TB* __restrict__ B, long long sbn,
+                                                long long sbk, T* __restrict__ C, long long ldc,
+                                                const int* __restrict__ kidx, const int* __restrict__ kidx_b,
+                                                const double* __restrict__ kscale, T* smem) {
+  constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
+  // rows of the staged slices padded by one element: the k-contiguous
+  // stores (16 k values per warp) then fall into distinct banks
+  constexpr int LDA = BM + 1, LDB = BN + 1;
+  T* As = smem;              // [BK][LDA]
+  T* Bs = smem + BK * LDA;   // [BK][LDB]
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const bool a_k_contig = (sak == 1);
   const bool b_k_contig = (sbk == 1);
+  // per-thread slice elements: k offset, shared-memory slot, row offset in
+  // global memory (-1: outside the matrix)
+  int ka[TM], kb[TN], sa[TM], sb[TN];
+  long long oa[TM], ob[TN];
+  T ra[TM], rb[TN];
   for (int m0 = 0; m0 < M; m0 += BM) {
     for (int n0 = 0; n0 < N; n0 += BN) {
-      T acc[4][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int r = 0; r < TM; ++r) {
+        const int e = tid + r * kBlock;
+        int kk, mm;
+        if (a_k_contig) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+        ka[r] = kk;
+        sa[r] = kk * LDA + mm;
+        oa[r] = (m0 + mm < M) ? (long long)(m0 + mm) * sam : -1;
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-      for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int r = 0; r < TN; ++r) {
+        const int e = tid + r * kBlock;
+        int kk, nn;
+        if (b_k_contig) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+        kb[r] = kk;
+        sb[r] = kk * LDB + nn;
+        ob[r] = (n0 + nn < N) ? (long long)(n0 + nn) * sbn : -1;
+      }
+      T acc[TM][TN];
 #pragma unroll
-        for (int r = 0; r < (BM * BK) / kBlock; ++r) {
-          const int e = tid + r * kBlock;
-          int kk, mm;
-          if (a_k_contig) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
-          const int gm = m0 + mm, gk = k0 + kk;
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+      // global -> registers for the k-slice at k0
+      auto fetch = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < TM; ++r) {
+          const int gk = k0 + ka[r];
           T v = T(0);
-          if (gm < M && gk < K) {
-            const long long kr = kidx ? kidx[gk] : gk;
-            v = A[gm * sam + kr * sak];
+          if (oa[r] >= 0 && gk < K) {
+            v = A[oa[r] + (long long)(kidx ? kidx[gk] : gk) * sak];
             if (kscale) v = T(double(v) * kscale[gk]);
           }
-          As[kk * BM + mm] = v;
+          ra[r] = v;
         }
 #pragma unroll
-        for (int r = 0; r < (BN * BK) / kBlock; ++r) {
-          const int e = tid + r * kBlock;
-          int kk, nn;
-          if (b_k_contig) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
-          const int gn = n0 + nn, gk = k0 + kk;
-          T v = T(0);
-          if (gn < N && gk < K) {
-            const long long kr = kidx_b ? kidx_b[gk] : gk;
-            v = T(B[gn * sbn + kr * sbk]);
-          }
-          Bs[kk * BN + nn] = v;
+        for (int r = 0; r < TN; ++r) {
+          const int gk = k0 + kb[r];
+          rb[r] = (ob[r] >= 0 && gk < K) ? T(B[ob[r] + (long long)(kidx_b ? kidx_b[gk] : gk) * sbk]) : T(0);
         }
+      };
+      fetch(0);
+      for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int r = 0; r < TM; ++r) As[sa[r]] = ra[r];
+#pragma unroll
+        for (int r = 0; r < TN; ++r) Bs[sb[r]] = rb[r];
         __syncthreads();
+        if (k0 + BK < K) fetch(k0 + BK);   // in flight during the multiply
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-          T a[4], b[4];
+          T a[TM], b[TN];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = As[kk * BM + ty * 4 + i];
+          for (int i = 0; i < TM; ++i) a[i] = As[kk * LDA + ty * TM + i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = Bs[kk * BN + tx * 4 + j];
+          for (int j = 0; j < TN; ++j) b[j] = Bs[kk * LDB + tx * TN + j];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + ty * 4 + i;
+      for (int i = 0; i < TM; ++i) {
+        const int gm = m0 + ty * TM + i;
         if (gm >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gn = n0 + tx * 4 + j;
+        for (int j = 0; j < TN; ++j) {
+          const int gn = n0 + tx * TN + j;
           if (gn < N) C[gm * ldc + gn] = acc[i][j];
         }
       }
     }
   }
   __syncthreads();
+}
+
+// micro-tile (4 or 5 per thread: tile edge 64 or 80) with the least padding
+// of a dimension d, the smaller on ties
+__device__ __forceinline__ int gemm_micro(int d) {
+  const int p4 = (d + 63) / 64 * 64, p5 = (d + 79) / 80 * 80;
+  return p5 < p4 ? 5 : 4;
+}
+
+template <typename T, typename TB = T>
+__device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long long sam, long long sak,
+                           const TB* __restrict__ B, long long sbn, long long sbk, T* __restrict__ C,
+                           long long ldc, const int* __restrict__ kidx, const int* __restrict__ kidx_b,
+                           const double* __restrict__ kscale, T* smem) {
+  const int tm = gemm_micro(M), tn = gemm_micro(N);
+#define FMO_GEMM_CASE(a, b)                                                                              \
+  if (tm == a && tn == b) {                                                                              \
+    block_gemm_tile<T, TB, a, b>(M, N, K, A, sam, sak, B, sbn, sbk, C, ldc, kidx, kidx_b, kscale, smem); \
+    return;                                                                                              \
+  }
+  FMO_GEMM_CASE(4, 4) FMO_GEMM_CASE(4, 5) FMO_GEMM_CASE(5, 4) FMO_GEMM_CASE(5, 5)
+#undef FMO_GEMM_CASE
 }
 
 // ---------------------------------------------------------------------------

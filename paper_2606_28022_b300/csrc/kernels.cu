@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kBlock) lowdin_kernel(const Nmer* __restrict__
   T* A;
   if (a_in_smem) { A = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)npad * npad; }
   else A = Ag + nm.apad;  // global scratch, npad*npad per n-mer
-  T* gemm = reinterpret_cast<T*>(sp); sp += sizeof(T) * 2 * 16 * 64;
+  T* gemm = reinterpret_cast<T*>(sp); sp += sizeof(T) * kGemmSmemElems;
   double* red = reinterpret_cast<double*>(sp); sp += sizeof(double) * 32;
   double* scale = reinterpret_cast<double*>(sp); sp += sizeof(double) * npad;
   JacobiScratch<T> js;
@@ -336,16 +336,15 @@ __global__ void warm_start_kernel(const Nmer* __restrict__ nmers, const Nmer* __
   int off[4] = {0, n, n, n};
   for (int k = 0; k < nm.nfrag; ++k) off[k + 1] = off[k] + mono[nm.frag[k]].n;
   float* C = ct + nm.mat;
-  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
-    const int r = int(e / n), c = int(e % n);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = wid; r < n; r += nw) {
     const int kr = (r >= off[1]) + (r >= off[2]);
-    const int kc = (c >= off[1]) + (c >= off[2]);
-    float v = 0.f;
-    if (kr == kc) {
-      const Nmer& m = mono[nm.frag[kr]];
-      v = mono_ct[m.mat + (long long)(r - off[kr]) * m.n + (c - off[kc])];
+    const Nmer& m = mono[nm.frag[kr]];
+    const long long row0 = m.mat + (long long)(r - off[kr]) * m.n;
+    for (int c = lane; c < n; c += 32) {
+      const int kc = (c >= off[1]) + (c >= off[2]);
+      C[(long long)r * n + c] = (kr == kc) ? mono_ct[row0 + (c - off[kr])] : 0.f;
     }
-    C[e] = v;
   }
 }
 
@@ -442,7 +441,7 @@ __host__ __device__ inline size_t scc_smem_bytes(int max_n, int max_nsh, int max
   const int npad = max_n + (max_n & 1);
   size_t b = 0;
   b += align16((size_t)a_bytes);
-  b += align16(sizeof(double) * 2 * 16 * 64);
+  b += align16(sizeof(double) * kGemmSmemElems);
   b += align16(sizeof(double) * 32);
   b += 7 * align16(sizeof(double) * max_nsh);          // sig dqin dqout esp q0 + spare
   b += 2 * align16(sizeof(double) * max_nat);          // dqat g3
@@ -467,7 +466,7 @@ __device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, i
   unsigned char* p = base;
   auto take = [&](size_t bytes) { unsigned char* r = p; p += align16(bytes); return (void*)r; };
   s.A = take(a_bytes);
-  s.gemm = take(sizeof(double) * 2 * 16 * 64);
+  s.gemm = take(sizeof(double) * kGemmSmemElems);
   s.red = (double*)take(sizeof(double) * 32);
   s.sig = (double*)take(sizeof(double) * max_nsh);
   s.dqin = (double*)take(sizeof(double) * max_nsh);
@@ -497,7 +496,17 @@ __device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, i
   return s;
 }
 
-// Fermi level by bisection (warp 0), occupations, -T S_el, occupied list.
+// Fermi occupations of Eq. 6 (closed shell: f_i = 2 / (exp((eps_i - eF)/kT)
+// + 1)) for the orbital energies sm.eps, eF by bisection on sum_i f_i = N
+// (warp 0), and -TS of Eq. 2.  T is the working precision of the SCC
+// iteration: the FP32 phase needs its occupations only to FP32 accuracy
+// (the bisection stops at |sum f - N| < 1e-6 there, 1e-13 in FP64).
+// Lists (ascending orbital index, built with warp ballots): occ = rows that
+// enter the density (f > 1e-30), the occupied ones (f > 1) first; virt =
+// rows with f <= 1.  misc[0] = |virt|, misc[2] = number of rows with f > 1,
+// misc[1] = 1 iff every occupation is 2 or 0 to within 1e-14 (the
+// orbital-rotation update is allowed).  Returns -TS; *n_occ_out = |occ|.
+template <typename T>
 __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_occ_out) {
   __shared__ double s_mts;
   __shared__ int s_nocc;
@@ -509,52 +518,65 @@ __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_o
     hi = warp_max(hi);
     lo -= 50.0 * kT + 1.0;
     hi += 50.0 * kT + 1.0;
+    const T ikT = T(1.0 / kT);
+    const T xmax = T(sizeof(T) == 8 ? 700.0 : 80.0);
+    const double ntol = sizeof(T) == 8 ? 1e-13 : 1e-6;
     double ef = 0.5 * (lo + hi);
     for (int it = 0; it < 400; ++it) {
       ef = 0.5 * (lo + hi);
-      double tot = 0.0;
+      T tot = T(0);
       for (int i = lane; i < n; i += 32) {
-        const double x = fmin(fmax((sm.eps[i] - ef) / kT, -700.0), 700.0);
-        tot += 2.0 / (exp(x) + 1.0);
+        const T x = fmin(fmax(T(sm.eps[i] - ef) * ikT, -xmax), xmax);
+        tot += T(2) / (exp(x) + T(1));
       }
-      tot = warp_sum(tot);
-      if (fabs(tot - nel) < 1e-13 || hi - lo < 1e-15) break;
-      if (tot > nel) hi = ef; else lo = ef;
+      const double tsum = warp_sum(double(tot));
+      if (fabs(tsum - nel) < ntol || hi - lo < 1e-15) break;
+      if (tsum > nel) hi = ef; else lo = ef;
     }
-    double mts = 0.0;
+    T mts = T(0);
+    double fo_min = 2.0, fv_max = 0.0;
     for (int i = lane; i < n; i += 32) {
-      const double x = fmin(fmax((sm.eps[i] - ef) / kT, -700.0), 700.0);
-      const double f = 2.0 / (exp(x) + 1.0);
-      sm.focc[i] = f;
-      const double h = 0.5 * f;
-      double t = 0.0;
-      if (h > 1e-300) t += h * log(h);
-      if (1.0 - h > 1e-300) t += (1.0 - h) * log(1.0 - h);
+      const T x = fmin(fmax(T(sm.eps[i] - ef) * ikT, -xmax), xmax);
+      const T f = T(2) / (exp(x) + T(1));
+      sm.focc[i] = double(f);
+      const T h = T(0.5) * f;
+      T t = T(0);
+      if (h > T(1e-30)) t += h * log(h);
+      if (T(1) - h > T(1e-30)) t += (T(1) - h) * log(T(1) - h);
       mts += t;
+      if (f > T(1)) fo_min = fmin(fo_min, double(f)); else fv_max = fmax(fv_max, double(f));
     }
-    mts = warp_sum(mts);
-    if (lane == 0) s_mts = 2.0 * kT * mts;
+    const double mts_sum = warp_sum(double(mts));
+    fo_min = -warp_max(-fo_min);
+    fv_max = warp_max(fv_max);
     __syncwarp();
+    int k = 0, v = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      const double f = (i < n) ? sm.focc[i] : 0.0;
+      const bool po = (i < n) && f > 1.0;
+      const bool pv = (i < n) && !(f > 1.0);
+      const unsigned bo = __ballot_sync(0xffffffffu, po), bv = __ballot_sync(0xffffffffu, pv);
+      if (po) sm.occ[k + __popc(bo & below)] = i;
+      if (pv) sm.virt[v + __popc(bv & below)] = i;
+      k += __popc(bo);
+      v += __popc(bv);
+    }
+    const int nro = k;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      const double f = (i < n) ? sm.focc[i] : 0.0;
+      const bool pt = (i < n) && f <= 1.0 && f > 1e-30;
+      const unsigned bt = __ballot_sync(0xffffffffu, pt);
+      if (pt) sm.occ[k + __popc(bt & below)] = i;
+      k += __popc(bt);
+    }
     if (lane == 0) {
-      // occ: rows entering the density (occupation above 1e-30), the
-      // occupied ones (f > 1) first; virt: rows with f <= 1.  The
-      // orbital-rotation update partitions at f = 1 and is allowed only when
-      // every occupation is 2 or 0 to within 1e-14.
-      int k = 0, v = 0;
-      double f_occ_min = 2.0, f_vir_max = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const double f = sm.focc[i];
-        if (f > 1.0) { sm.occ[k++] = i; f_occ_min = fmin(f_occ_min, f); }
-        else { sm.virt[v++] = i; f_vir_max = fmax(f_vir_max, f); }
-      }
-      const int nro = k;
-      for (int i = 0; i < n; ++i) {
-        const double f = sm.focc[i];
-        if (f <= 1.0 && f > 1e-30) sm.occ[k++] = i;
-      }
+      s_mts = 2.0 * kT * mts_sum;
       s_nocc = k;
       sm.misc[0] = v;
-      sm.misc[1] = (nro > 0 && v > 0 && f_occ_min > 2.0 - 1e-14 && f_vir_max < 1e-14) ? 1 : 0;
+      sm.misc[1] = (nro > 0 && v > 0 && fo_min > 2.0 - 1e-14 && fv_max < 1e-14) ? 1 : 0;
       sm.misc[2] = nro;
     }
   }
@@ -698,6 +720,35 @@ struct PrecPtrs {
   int lda;
 };
 
+// 1/d in precision T: FP32 division, or for FP64 the FP32 reciprocal
+// refined by one Newton step r <- r (2 - d r) (relative error ~1e-7 -> ~1e-14).
+template <typename T>
+__device__ __forceinline__ T recip(double d);
+template <>
+__device__ __forceinline__ float recip<float>(double d) { return 1.0f / float(d); }
+template <>
+__device__ __forceinline__ double recip<double>(double d) {
+  const double r = double(1.0f / float(d));
+  return r * (2.0 - d * r);
+}
+
+// max |X - I| over an m x n row-major matrix (a warp per row); optionally
+// stores X - I in FP32 into out.  Block-uniform result.
+template <typename T>
+__device__ double max_dev_from_identity(const T* X, int m, int n, double* red, float* out = nullptr) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double err = 0.0;
+  for (int i = wid; i < m; i += nw) {
+    const T* row = X + (long long)i * n;
+    for (int j = lane; j < n; j += 32) {
+      const double d = double(row[j]) - (i == j ? 1.0 : 0.0);
+      if (out) out[(long long)i * n + j] = float(d);
+      err = fmax(err, fabs(d));
+    }
+  }
+  return block_max(err, red);
+}
+
 // One SCC iteration in precision T.  Returns E_el; writes dq_out, eps.
 // Rotation of the rows CT (type T) by the generator K (n_o x n_v, type TG,
 // stored at Kg): C_o += K C_v - 1/2 K K^T C_o, C_v += -K^T C_o - 1/2 K^T K C_v
@@ -713,13 +764,18 @@ __device__ void rotate_rows(int n, int no, int nv, const int* occ, const int* vi
   block_gemm<TG>(nv, n, no, Kg, 1, nv, src, 1, n, Dv, n, nullptr, occ, nullptr, gemm);
   block_gemm<TG>(no, n, nv, Kg, nv, 1, Dv, 1, n, Yo, n, nullptr, nullptr, nullptr, gemm);
   block_gemm<TG>(nv, n, no, Kg, 1, nv, dCo, 1, n, yv, n, nullptr, nullptr, nullptr, gemm);
-  for (long long e = threadIdx.x; e < (long long)no * n; e += blockDim.x) {
-    const long long r = (long long)occ[e / n] * n + e % n;
-    CT[r] = CT[r] + T(dCo[e] - TG(0.5) * Yo[e]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < no; i += nw) {
+    T* row = CT + (long long)occ[i] * n;
+    const TG* d = dCo + (long long)i * n;
+    const TG* y = Yo + (long long)i * n;
+    for (int j = lane; j < n; j += 32) row[j] = row[j] + T(d[j] - TG(0.5) * y[j]);
   }
-  for (long long e = threadIdx.x; e < (long long)nv * n; e += blockDim.x) {
-    const long long r = (long long)virt[e / n] * n + e % n;
-    CT[r] = CT[r] - T(Dv[e] + TG(0.5) * yv[e]);
+  for (int a = wid; a < nv; a += nw) {
+    T* row = CT + (long long)virt[a] * n;
+    const TG* d = Dv + (long long)a * n;
+    const TG* y = yv + (long long)a * n;
+    for (int j = lane; j < n; j += 32) row[j] = row[j] - T(d[j] + TG(0.5) * y[j]);
   }
   __syncthreads();
 }
@@ -732,6 +788,13 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   const double* Sm = ar.S + nm.mat;
   const double* Hm = ar.H0 + nm.mat;
   const double* G = ar.gam + nm.gam;
+  // diagnostic trace: SM cycles per part of the iteration, summed over the
+  // iterations of the first block (thread 0 reads the clock after a barrier)
+  const bool tr = ar.trace && blockIdx.x == 0 && threadIdx.x == 0;
+  long long tmark = tr ? clock64() : 0;
+  auto mark = [&](int j) {
+    if (tr) { const long long t = clock64(); ar.trace[kTraceParts + j] += double(t - tmark); tmark = t; }
+  };
   // atomic charges and shell shifts (Eq. 7 and the ESP of Eq. 21)
   for (int a = threadIdx.x; a < nat; a += blockDim.x) sm.dqat[a] = 0.0;
   __syncthreads();
@@ -752,11 +815,16 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     }
   }
   __syncthreads();
-  // Fock matrix F = H0 + 1/2 S (sig_mu + sig_nu), into W1
-  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
-    const int i = int(e / n), j = int(e % n);
-    const double f = Hm[e] + 0.5 * Sm[e] * (sm.sig[sm.mp.ao_sh[i]] + sm.sig[sm.mp.ao_sh[j]]);
-    pp.W1[e] = T(f);
+  // Fock matrix F = H0 + 1/2 S (sig_mu + sig_nu), into W1 (a warp per row)
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < n; i += nw) {
+      const double si = sm.sig[sm.mp.ao_sh[i]];
+      const double* hr = Hm + (long long)i * n;
+      const double* sr = Sm + (long long)i * n;
+      T* fr = pp.W1 + (long long)i * n;
+      for (int j = lane; j < n; j += 32) fr[j] = T(hr[j] + 0.5 * sr[j] * (si + sm.sig[sm.mp.ao_sh[j]]));
+    }
   }
   // zero the padding row/column of A
   if (n != npad) {
@@ -767,9 +835,11 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   }
   __syncthreads();
   T* gemm = reinterpret_cast<T*>(sm.gemm);
+  mark(0);
   // U = CT F  (W2), then A = U CT^T: the Fock matrix in the current MO basis
   block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
   block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, nullptr, gemm);
+  mark(1);
   int nocc = 0;
   double mts = 0.0;
   bool rotated = false;
@@ -784,22 +854,30 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     // fixed point A_ia = 0, so the fixed point is unchanged.
     for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
     __syncthreads();
-    mts = fermi_step(n, nm.nel, ar.g.kT, sm, &nocc);
+    mts = fermi_step<T>(n, nm.nel, ar.g.kT, sm, &nocc);
     if (sm.misc[1]) {
       const int no = sm.misc[2], nv = sm.misc[0];
       T* K = pp.W2;                                 // no x nv
       double kmax = 0.0;
-      for (long long e = threadIdx.x; e < (long long)no * nv; e += blockDim.x) {
-        const int i = sm.occ[e / nv], a = sm.virt[e % nv];
-        const double k = double(pp.A[(long long)i * pp.lda + a]) / (sm.eps[i] - sm.eps[a]);
-        K[e] = T(k);
-        kmax = fmax(kmax, fabs(k));
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int r = wid; r < no; r += nw) {
+        const int i = sm.occ[r];
+        const double ei = sm.eps[i];
+        const T* arow = pp.A + (long long)i * pp.lda;
+        T* krow = K + (long long)r * nv;
+        for (int c = lane; c < nv; c += 32) {
+          const int a = sm.virt[c];
+          const T k = arow[a] * recip<T>(ei - sm.eps[a]);
+          krow[c] = k;
+          kmax = fmax(kmax, fabs(double(k)));
+        }
       }
       kmax = block_max(kmax, sm.red);
       // (1 + k + k^2/2) keeps orthonormality up to k^4/4: rotate only while
       // that stays below the working precision, otherwise diagonalise
       rotated = kmax <= (sizeof(T) == 8 ? 1e-4 : 2e-2);
     }
+    mark(2);
     if (rotated) {
       const int no = sm.misc[2], nv = sm.misc[0];
       if (sizeof(T) == 8 && f_ct) {
@@ -823,14 +901,16 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     if (threadIdx.x == 0) sm.misc[3] = sw;   // sweeps (diagnostic trace)
     for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
     __syncthreads();
-    mts = fermi_step(n, nm.nel, ar.g.kT, sm, &nocc);
+    mts = fermi_step<T>(n, nm.nel, ar.g.kT, sm, &nocc);
   }
+  mark(3);
   // compacted occupations
   double* fc = reinterpret_cast<double*>(sm.jsc);   // js scratch is free here (npad doubles)
   for (int k = threadIdx.x; k < nocc; k += blockDim.x) fc[k] = sm.focc[sm.occ[k]];
   __syncthreads();
   // density P = sum_occ f_i c_i c_i^T  (W1)
   block_gemm<T>(n, n, nocc, pp.CT, 1, n, pp.CT, 1, n, pp.W1, n, sm.occ, sm.occ, fc, gemm);
+  mark(4);
   // Mulliken shell populations (Eq. 3) and the band energy sum P H0, one warp per shell
   double eb_local = 0.0;
   {
@@ -854,7 +934,10 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   }
   __syncthreads();
   (void)eb_local;
-  return energy_of_output(nm, ar, sm, diff_out) + mts;
+  mark(5);
+  const double e_out = energy_of_output(nm, ar, sm, diff_out) + mts;
+  mark(6);
+  return e_out;
 }
 
 // CT <- (M^{-1/2}) CT with M = CT S CT^T, by Newton-Schulz steps
@@ -871,10 +954,7 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
   for (int step = 0; step < max_steps; ++step) {
     block_gemm<T, double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);   // V = CT S
     block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.W1, n, nullptr, nullptr, nullptr, gemm);       // M = V CT^T
-    double err = 0.0;
-    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
-      err = fmax(err, fabs(double(pp.W1[e]) - ((e / n) == (e % n) ? 1.0 : 0.0)));
-    err = block_max(err, sm.red);
+    const double err = max_dev_from_identity(pp.W1, n, n, sm.red);
     if (err < tol) break;
     block_gemm<T>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, nullptr, gemm);       // M CT
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
@@ -896,13 +976,7 @@ __device__ void reortho_handover(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
   const double* Sm = ar.S + nm.mat;
   block_gemm<double>(n, n, n, pd.CT, n, 1, Sm, n, 1, pd.W2, n, nullptr, nullptr, nullptr, gemm);   // V = CT S
   block_gemm<double>(n, n, n, pd.W2, n, 1, pd.CT, n, 1, pd.W1, n, nullptr, nullptr, nullptr, gemm);  // M
-  double err = 0.0;
-  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
-    const double d = pd.W1[e] - ((e / n) == (e % n) ? 1.0 : 0.0);
-    wf1[e] = float(d);
-    err = fmax(err, fabs(d));
-  }
-  err = block_max(err, sm.red);
+  const double err = max_dev_from_identity(pd.W1, n, n, sm.red, wf1);
   float* gf = reinterpret_cast<float*>(sm.gemm);
   block_gemm<float>(n, n, n, wf1, n, 1, ct32, 1, n, wf2, n, nullptr, nullptr, nullptr, gf);   // (M - I) CT
   for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] -= 0.5 * double(wf2[e]);
@@ -929,13 +1003,19 @@ __device__ double fp64_energy_of_rows(const Nmer& nm, const SccArgs& ar, SccSmem
   const double* Sm = ar.S + nm.mat;
   const double* Hm = ar.H0 + nm.mat;
   int no = 0;
-  const double mts = fermi_step(n, nm.nel, ar.g.kT, sm, &no);   // occupations of the last FP32 iteration
+  const double mts = fermi_step<double>(n, nm.nel, ar.g.kT, sm, &no);   // occupations of the last FP32 iteration
   double* Co = pd.CT;   // no x n
   double* W = pd.W1;    // no x n
   double* Y = pd.W2;    // no x n
   double* M = pd.A;     // no x no
-  for (long long e = threadIdx.x; e < (long long)no * n; e += blockDim.x)
-    Co[e] = double(ct32[(long long)sm.occ[e / n] * n + e % n]);
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k < no; k += nw) {
+      const float* src = ct32 + (long long)sm.occ[k] * n;
+      double* dst = Co + (long long)k * n;
+      for (int j = lane; j < n; j += 32) dst[j] = double(src[j]);
+    }
+  }
   __syncthreads();
   double* gemm = reinterpret_cast<double*>(sm.gemm);
   float* gf = reinterpret_cast<float*>(sm.gemm);
@@ -944,13 +1024,7 @@ __device__ double fp64_energy_of_rows(const Nmer& nm, const SccArgs& ar, SccSmem
   double err0 = 0.0;
   for (int step = 0; step < 2; ++step) {
     block_gemm<double>(no, no, n, W, n, 1, Co, n, 1, M, no, nullptr, nullptr, nullptr, gemm);   // M = C_o S C_o^T
-    double err = 0.0;
-    for (long long e = threadIdx.x; e < (long long)no * no; e += blockDim.x) {
-      const double d = M[e] - ((e / no) == (e % no) ? 1.0 : 0.0);
-      wf1[e] = float(d);
-      err = fmax(err, fabs(d));
-    }
-    err = block_max(err, sm.red);
+    const double err = max_dev_from_identity(M, no, no, sm.red, wf1);
     if (step == 0) err0 = err;
     else if (err0 <= 1e-8) break;   // one step left ~err0^2: done
     double* X[3] = {Co, W, Y};
@@ -1013,8 +1087,8 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   __syncthreads();
   // repulsion energy inside the n-mer (Eq. 11), unordered atom pairs
   double er = 0.0;
-  for (long long e = threadIdx.x; e < (long long)nat * nat; e += blockDim.x) {
-    const int i = int(e / nat), j = int(e % nat);
+  for (int e = threadIdx.x; e < nat * nat; e += blockDim.x) {
+    const int i = e / nat, j = e % nat;
     if (j >= i) continue;
     const int ga = sm.mp.at_glob[i], gb = sm.mp.at_glob[j];
     const DevElem& EA = ar.el[ar.elem[ga]];
@@ -1601,7 +1675,7 @@ static size_t lowdin_smem(int max_n, int elem_bytes, int a_in_smem) {
   const int npad = max_n + (max_n & 1);
   size_t b = 0;
   if (a_in_smem) b += (size_t)elem_bytes * npad * npad;
-  b += (size_t)elem_bytes * 2 * 16 * 64 + sizeof(double) * 32 + sizeof(double) * npad + 3 * sizeof(int) * npad;
+  b += (size_t)elem_bytes * kGemmSmemElems + sizeof(double) * 32 + sizeof(double) * npad + 3 * sizeof(int) * npad;
   b = (b + 15) & ~size_t(15);
   b += 2 * (size_t)elem_bytes * npad + 16;
   return b;

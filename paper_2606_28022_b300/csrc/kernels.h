@@ -13,6 +13,16 @@ constexpr int FMO_SCC_NAN_CODE = 2;
 constexpr int FMO_SCC_TIMEOUT_CODE = 3;
 constexpr int FMO_SCC_JACOBI_CODE = 4;
 
+// Layout of the diagnostic trace buffer (kTraceLen doubles) of the first
+// block of an SCC launch: [1, 512) residual per iteration, [512, 1024)
+// Jacobi sweeps, [1024, 1536) SM cycles per iteration ([1024] the setup,
+// [1535] the FP64 energy finish), then kTraceNParts sums of the cycles of the
+// parts of an SCC iteration (Fock, MO-basis transform, occupations and
+// rotation generator, rotation or Jacobi, density, populations, energy).
+constexpr int kTraceParts = 1536;
+constexpr int kTraceNParts = 7;
+constexpr int kTraceLen = kTraceParts + kTraceNParts;
+
 struct SccLaunch {
   const Nmer* nmers;
   const int* order;
