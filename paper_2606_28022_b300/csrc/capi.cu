@@ -110,6 +110,8 @@ struct fmo_ctx {
   std::vector<double> f_nel, h_sh_inv_eta;
   DevBuf d_xyz, d_xyz_in, d_perm, d_elem, d_cn, d_atom_sh0, d_sh_atom, d_sh_inv_eta;
   DevBuf d_f_atom0, d_f_nat, d_f_sh0, d_f_nsh, d_f_ao0, d_f_nao;
+  DevBuf d_gam_full;                      // gamma of all shell pairs (when it fits)
+  bool gam_full_ok = false;
   DevBuf d_trace, d_dq_mono, d_phi, d_phi_part, d_bounds, d_rmin, d_scalar, d_t0, d_mix_hist, d_mix_state;
   DevBuf d_pair_scc, d_dE_pair, d_esdim_pairs, d_esdim_idx, d_tri_frag, d_dE3, d_corr, d_totals;
   std::vector<double> guess;
@@ -358,6 +360,20 @@ void stage(cudaStream_t st, const char* what, int k = -1) {
   fflush(stderr);
 }
 
+// Supersystem potential phi = gamma dq_mono of the current monomer charges:
+// a matrix-vector product over the stored gamma of all shell pairs when it is
+// held, else evaluated pair by pair (use_float: FP32 estimate).
+constexpr size_t kGammaFullMaxBytes = size_t(32) << 30;
+
+cudaError_t compute_phi(fmo_ctx* ctx, cudaStream_t st, int use_float) {
+  if (ctx->gam_full_ok)
+    return launch_phi_gemv(st, ctx->n_sh, ctx->d_gam_full.as<double>(), ctx->d_dq_mono.as<double>(),
+                           ctx->d_phi.as<double>());
+  return launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
+                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>(),
+                    use_float);
+}
+
 fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& sp, bool with_phi,
                    int pass_id, cudaStream_t st, int single_step = 0, int step_phase = 1, int reortho = 0,
                    int cold = 1, int reortho32 = 0, double jac_hint = 1.0) {
@@ -449,6 +465,12 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
             tr[kTraceParts] * 1e-6, tr[kTraceParts + 1] * 1e-6, tr[kTraceParts + 2] * 1e-6,
             tr[kTraceParts + 3] * 1e-6, tr[kTraceParts + 4] * 1e-6, tr[kTraceParts + 5] * 1e-6,
             tr[kTraceParts + 6] * 1e-6);
+    unsigned long long slow = 0, njac = 0;
+    std::memcpy(&slow, &tr[kTraceSlowest], 8);
+    std::memcpy(&njac, &tr[kTraceJacobi], 8);
+    const int sb = int(slow & 0xFFFFF);
+    fprintf(stderr, "[fmo] slowest block %d (n = %d): %.2f Mcycles; Jacobi eigen-solves in the launch: %llu\n", sb,
+            sb < (int)P.order.size() ? P.nm[P.order[sb]].n : -1, double(slow >> 20) * 1e-6, njac);
   }
   ctx->stats.scc_launches[pass_id] += 1;
   for (int i = 0; i < nn; ++i) {
@@ -539,7 +561,7 @@ void fmo_destroy(fmo_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_prim, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
                     &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
-                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
+                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_gam_full, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
                     &ctx->d_totals})
@@ -762,6 +784,19 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
                ctx->d_cn.as<double>()));
   ctx->stats.kernel_launches += 2;
   stage(st, "cn");
+  // gamma of all shell pairs, kept in HBM while it fits the budget
+  {
+    const size_t gbytes = sizeof(double) * (size_t)ctx->n_sh * (size_t)ctx->n_sh;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    ctx->gam_full_ok = gbytes <= kGammaFullMaxBytes && (gbytes <= ctx->d_gam_full.cap || gbytes <= free_b / 4);
+    if (ctx->gam_full_ok) {
+      CK(ctx->d_gam_full.ensure(gbytes));
+      CK(launch_gamma_full(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(),
+                           ctx->d_sh_inv_eta.as<double>(), ctx->g, ctx->d_gam_full.as<double>()));
+      ctx->stats.kernel_launches += 1;
+    }
+  }
   // ---- monomer pass
   {
     std::vector<std::array<int, 3>> tu(nf);
@@ -794,9 +829,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     struct { double e_prev, diff, e1; int have_prev, hcount, hhead, converged, count; } hs{};
     for (outer = 1; outer <= o.max_outer; ++outer) {
       // the FP32 phase works with an FP32 estimate of the potential
-      CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>(),
-                    phase == 0 ? 1 : 0));
+      CK(compute_phi(ctx, st, phase == 0 ? 1 : 0));
       stage(st, "phi", outer);
       fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 1, phase, reortho, outer == 1 ? 1 : 0,
                    (phase == 0 && outer > 1 && outer % 4 == 0) ? 1 : 0, outer == 1 ? 1.0 : hs.diff);
@@ -824,8 +857,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     ctx->stats.n_monomer_solves = nf;
   } else {
   for (outer = 1; outer <= o.max_outer; ++outer) {
-    CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                  ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
+    CK(compute_phi(ctx, st, 0));
     stage(st, "phi", outer);
     fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 0, 1, 0, outer == 1 ? 1 : 0);
     if (fs != FMO_OK) return fs;
@@ -845,8 +877,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (outer > o.max_outer) outer = o.max_outer;
   ctx->stats.outer_iterations = outer;
   // frozen ESP of the final monomer charges
-  CK(launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_phi.as<double>(), ctx->d_phi_part.as<double>()));
+  CK(compute_phi(ctx, st, 0));
   ctx->stats.kernel_launches += 1;
   cudaEventRecord(ev[2], st);
   sr.set("fmo_select");

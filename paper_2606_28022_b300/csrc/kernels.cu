@@ -7,6 +7,7 @@
 //   Eq. 11       repulsion                CN definition in the gradient section
 //   Eqs. 12-15   FMO2, dE^V, ddq, ES-DIM  Eqs. 16-19 FMO3
 //   Eqs. 20-21   embedding Fock matrix V^I from the other fragments' charges
+#include <algorithm>
 #include <cstdio>
 
 #include "fmo_device.cuh"
@@ -899,6 +900,7 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
     if (sw < 0 && sizeof(T) == 8) *jac_fail = 1;
     if (threadIdx.x == 0) sm.misc[3] = sw;   // sweeps (diagnostic trace)
+    if (ar.trace && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(ar.trace + kTraceJacobi), 1ULL);
     for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
     __syncthreads();
     mts = fermi_step<T>(n, nm.nel, ar.g.kT, sm, &nocc);
@@ -1285,6 +1287,10 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) ar.eps[nm.aov + i] = sm.eps[i];
   dev = block_sum(dev, sm.red);
+  if (ar.trace && threadIdx.x == 0) {
+    const unsigned long long cyc = (unsigned long long)(clock64() - t_start);
+    atomicMax(reinterpret_cast<unsigned long long*>(ar.trace + kTraceSlowest), (cyc << 20) | blockIdx.x);
+  }
   if (threadIdx.x == 0) {
     ar.energy[idx] = e_el + e_rep;
     ar.e_el[idx] = e_el;
@@ -1349,6 +1355,45 @@ __global__ void __launch_bounds__(256) phi_kernel(int n_sh, int chunk, const dou
     __syncthreads();
   }
   if (mu < n_sh) part[(size_t)blockIdx.y * n_sh + mu] = double(acc);
+}
+
+// gamma of Eqs. 4-5 between every pair of shells of the system, row-major
+// n_sh x n_sh.  With it held in HBM the supersystem potential of each
+// monomer-loop step is a matrix-vector product (HBM-bound) instead of n_sh^2
+// FP64 kernel evaluations.  Block (x: 256 columns lambda, y: every gridDim.y-th
+// row mu).
+__global__ void __launch_bounds__(256) gamma_full_kernel(int n_sh, const double* __restrict__ xyz,
+                                                         const int* __restrict__ sh_atom,
+                                                         const double* __restrict__ sh_inv_eta, GParams g,
+                                                         double* __restrict__ gam) {
+  const int lam = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lam >= n_sh) return;
+  const int b = sh_atom[lam];
+  const double xb = xyz[3 * b], yb = xyz[3 * b + 1], zb = xyz[3 * b + 2], ieb = sh_inv_eta[lam];
+  for (int mu = blockIdx.y; mu < n_sh; mu += gridDim.y) {
+    const int a = sh_atom[mu];
+    const double dx = xyz[3 * a] - xb, dy = xyz[3 * a + 1] - yb, dz = xyz[3 * a + 2] - zb;
+    gam[(size_t)mu * n_sh + lam] = gamma_fn(dx * dx + dy * dy + dz * dz, sh_inv_eta[mu], ieb, g.k_g);
+  }
+}
+
+// phi_mu = sum_lambda gamma_mu,lambda dq_lambda from the stored matrix, one
+// warp per row (fixed summation order).
+__global__ void __launch_bounds__(256) phi_gemv_kernel(int n_sh, const double* __restrict__ gam,
+                                                       const double* __restrict__ dq, double* __restrict__ phi) {
+  const int lane = threadIdx.x & 31;
+  const int mu = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (mu >= n_sh) return;
+  const double* row = gam + (size_t)mu * n_sh;
+  double s0 = 0.0, s1 = 0.0;
+  int l = lane;
+  for (; l + 32 < n_sh; l += 64) {
+    s0 = fma(row[l], dq[l], s0);
+    s1 = fma(row[l + 32], dq[l + 32], s1);
+  }
+  if (l < n_sh) s0 = fma(row[l], dq[l], s0);
+  const double v = warp_sum(s0 + s1);
+  if (lane == 0) phi[mu] = v;
 }
 
 __global__ void phi_reduce_kernel(int n_sh, int n_chunk, const double* __restrict__ part,
@@ -1755,6 +1800,22 @@ cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* 
   else phi_kernel<double><<<grid, 256, 0, st>>>(n_sh, chunk, xyz, sh_atom, sh_inv_eta, dq, g, part);
   LAUNCH_CHECK();
   phi_reduce_kernel<<<(n_sh + 255) / 256, 256, 0, st>>>(n_sh, ncu, part, phi);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_gamma_full(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom,
+                              const double* sh_inv_eta, GParams g, double* gam) {
+  if (n_sh == 0) return cudaSuccess;
+  const dim3 grid((n_sh + 255) / 256, std::min(n_sh, 4096));
+  gamma_full_kernel<<<grid, 256, 0, st>>>(n_sh, xyz, sh_atom, sh_inv_eta, g, gam);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_phi_gemv(cudaStream_t st, int n_sh, const double* gam, const double* dq, double* phi) {
+  if (n_sh == 0) return cudaSuccess;
+  phi_gemv_kernel<<<(int)(((long long)n_sh * 32 + 255) / 256), 256, 0, st>>>(n_sh, gam, dq, phi);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

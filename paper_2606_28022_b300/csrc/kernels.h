@@ -21,7 +21,11 @@ constexpr int FMO_SCC_JACOBI_CODE = 4;
 // rotation generator, rotation or Jacobi, density, populations, energy).
 constexpr int kTraceParts = 1536;
 constexpr int kTraceNParts = 7;
-constexpr int kTraceLen = kTraceParts + kTraceNParts;
+// two 64-bit counters over all blocks follow: (cycles << 20 | block) of the
+// slowest block, and the number of Jacobi eigen-solves
+constexpr int kTraceSlowest = kTraceParts + kTraceNParts;
+constexpr int kTraceJacobi = kTraceSlowest + 1;
+constexpr int kTraceLen = kTraceJacobi + 1;
 
 struct SccLaunch {
   const Nmer* nmers;
@@ -99,6 +103,9 @@ cudaError_t launch_warm_start(cudaStream_t st, int n_nmer, const Nmer* nmers, co
 int phi_chunks(int n_sh);
 cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom, const double* sh_inv_eta,
                        const double* dq, GParams g, double* phi, double* part, int use_float = 0);
+cudaError_t launch_gamma_full(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom,
+                              const double* sh_inv_eta, GParams g, double* gam);
+cudaError_t launch_phi_gemv(cudaStream_t st, int n_sh, const double* gam, const double* dq, double* phi);
 cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);
 cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, const double* bounds,
                                  double cut, double* rmin);

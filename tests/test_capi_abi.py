@@ -39,13 +39,15 @@ def test_struct_layout_matches_c(tmp_path):
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fmo_xtb.h"\n'
                    'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(fmo_element), sizeof(fmo_params),'
                    ' sizeof(fmo_options), sizeof(fmo_stats), offsetof(fmo_params, k_ab),'
-                   ' offsetof(fmo_options, dimer_cut) + 1000 * offsetof(fmo_options, mixed_finish));return 0;}\n')
+                   ' offsetof(fmo_options, dimer_cut) + 1000 * offsetof(fmo_options, mixed_finish)'
+                   ' + 1000000 * offsetof(fmo_options, nmer_finish));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [C.sizeof(fmo.FmoElement), C.sizeof(fmo.FmoParams), C.sizeof(fmo.FmoOptions),
                     C.sizeof(fmo.FmoStats), fmo.FmoParams.k_ab.offset,
-                    fmo.FmoOptions.dimer_cut.offset + 1000 * fmo.FmoOptions.mixed_finish.offset]
+                    fmo.FmoOptions.dimer_cut.offset + 1000 * fmo.FmoOptions.mixed_finish.offset
+                    + 1000000 * fmo.FmoOptions.nmer_finish.offset]
 
 
 def test_defaults_and_argument_errors(lib):

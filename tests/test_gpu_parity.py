@@ -146,3 +146,32 @@ def test_anthracene32_monomer_loop_fp64_and_mixed(gpu, params):
     assert np.max(np.abs(mono.shell_dq - np.concatenate(ref.dq_mono))) < DQ
     gpu.run(fmo.options(level=1, precision="mixed"))
     assert abs(gpu.energies()[0] - ref.e_fmo1) < E_TOT_MIXED
+
+
+def test_anthracene4_mixed_nmer_finish_iterate(gpu, params, anthracene4):
+    # the FP64-iteration finish of mixed-precision dimers reaches the same
+    # totals as the default FP64 energy of the FP32 density
+    ref = ofmo.fmo(anthracene4, params, ofmo.FMOOptions(all_dimers_scc=True))
+    g = run_gpu(gpu, anthracene4, all_dimers_scc=1, precision="mixed", nmer_finish="iterate")
+    e_it = g.energies()
+    assert abs(e_it[1] - ref.e_fmo2) < E_TOT_MIXED
+    g = run_gpu(gpu, anthracene4, all_dimers_scc=1, precision="mixed")
+    assert abs(g.energies()[1] - e_it[1]) < E_TOT_MIXED
+
+
+@pytest.fixture(scope="module")
+def pentacene4():
+    s, _ = G.pentacene_cluster(660, 4)
+    # molecule 0 and its three nearest neighbours of the seeded crystal: every
+    # pair is an SCC dimer and the trimers have n = 348 basis functions
+    return s.subsystem([0, 2, 93, 1])
+
+
+def test_pentacene4_fmo3_fp64_and_mixed(gpu, params, pentacene4):
+    ref = ofmo.fmo(pentacene4, params, ofmo.FMOOptions(level=3))
+    assert len(ref.trimers) > 0
+    compare(run_gpu(gpu, pentacene4, level=3), ref, level=3)
+    g = run_gpu(gpu, pentacene4, level=3, precision="mixed")
+    e1, e2, e3 = g.energies()
+    assert abs(e3 - ref.e_fmo3) < E_TOT_MIXED
+    assert abs(e2 - ref.e_fmo2) < E_TOT_MIXED
