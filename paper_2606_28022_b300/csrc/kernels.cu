@@ -501,7 +501,8 @@ __device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, i
 // + 1)) for the orbital energies sm.eps, eF by bisection on sum_i f_i = N
 // (warp 0), and -TS of Eq. 2.  T is the working precision of the SCC
 // iteration: the FP32 phase needs its occupations only to FP32 accuracy
-// (the bisection stops at |sum f - N| < 1e-6 there, 1e-13 in FP64).
+// (the bisection stops at |sum f - N| < 1e-6 there, 1e-13 in FP64); with a
+// gap wider than 70 kT eF is then placed mid-gap.
 // Lists (ascending orbital index, built with warp ballots): occ = rows that
 // enter the density (f > 1e-30), the occupied ones (f > 1) first; virt =
 // rows with f <= 1.  misc[0] = |virt|, misc[2] = number of rows with f > 1,
@@ -533,6 +534,22 @@ __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_o
       const double tsum = warp_sum(double(tot));
       if (fabs(tsum - nel) < ntol || hi - lo < 1e-15) break;
       if (tsum > nel) hi = ef; else lo = ef;
+    }
+    {
+      // a gap much wider than kT with exactly N/2 levels below eF: the root
+      // of sum f = N lies mid-gap (the frontier levels' tails balance), and
+      // there every occupation is 2 or 0 to ~2 exp(-gap/2kT).  The bisection
+      // stops anywhere in the gap once |sum f - N| is small enough.
+      double elo = -1e300, ehi = 1e300;
+      int cnt = 0;
+      for (int i = lane; i < n; i += 32) {
+        const double e = sm.eps[i];
+        if (e <= ef) { elo = fmax(elo, e); ++cnt; } else { ehi = fmin(ehi, e); }
+      }
+      elo = warp_max(elo);
+      ehi = -warp_max(-ehi);
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      if (fabs(2.0 * cnt - nel) < 1e-9 && ehi - elo > 70.0 * kT) ef = 0.5 * (elo + ehi);
     }
     T mts = T(0);
     double fo_min = 2.0, fv_max = 0.0;
