@@ -502,12 +502,12 @@ __device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, i
 // (warp 0), and -TS of Eq. 2.  T is the working precision of the SCC
 // iteration: the FP32 phase needs its occupations only to FP32 accuracy
 // (the bisection stops at |sum f - N| < 1e-6 there, 1e-13 in FP64); with a
-// gap wider than 70 kT eF is then placed mid-gap.
+// gap wider than 40 kT eF is then set from the balance of the Boltzmann tails.
 // Lists (ascending orbital index, built with warp ballots): occ = rows that
 // enter the density (f > 1e-30), the occupied ones (f > 1) first; virt =
 // rows with f <= 1.  misc[0] = |virt|, misc[2] = number of rows with f > 1,
-// misc[1] = 1 iff every occupation is 2 or 0 to within 1e-14 (the
-// orbital-rotation update is allowed).  Returns -TS; *n_occ_out = |occ|.
+// misc[1] = 1 iff every occupation is 2 or 0 to within 1e-6 (FP32) or 1e-10
+// (FP64) (the orbital-rotation update is allowed).  Returns -TS; *n_occ_out = |occ|.
 template <typename T>
 __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_occ_out) {
   __shared__ double s_mts;
@@ -536,10 +536,13 @@ __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_o
       if (tsum > nel) hi = ef; else lo = ef;
     }
     {
-      // a gap much wider than kT with exactly N/2 levels below eF: the root
-      // of sum f = N lies mid-gap (the frontier levels' tails balance), and
-      // there every occupation is 2 or 0 to ~2 exp(-gap/2kT).  The bisection
-      // stops anywhere in the gap once |sum f - N| is small enough.
+      // a gap much wider than kT with exactly N/2 levels below eF: the
+      // bisection stops anywhere in the gap once |sum f - N| is small
+      // enough.  There the root of sum f = N balances the Boltzmann tails
+      // (holes 2 exp((e_i - eF)/kT) below, electrons 2 exp((eF - e_a)/kT)
+      // above): eF = (elo + ehi)/2 + kT/2 ln(S_h / S_e) with
+      // S_h = sum_i exp((e_i - elo)/kT), S_e = sum_a exp((ehi - e_a)/kT),
+      // exact to a relative exp(-gap/2kT) in each tail.
       double elo = -1e300, ehi = 1e300;
       int cnt = 0;
       for (int i = lane; i < n; i += 32) {
@@ -549,7 +552,16 @@ __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_o
       elo = warp_max(elo);
       ehi = -warp_max(-ehi);
       cnt = __reduce_add_sync(0xffffffffu, cnt);
-      if (fabs(2.0 * cnt - nel) < 1e-9 && ehi - elo > 70.0 * kT) ef = 0.5 * (elo + ehi);
+      if (fabs(2.0 * cnt - nel) < 1e-9 && ehi - elo > 40.0 * kT) {
+        T sh = T(0), se = T(0);
+        for (int i = lane; i < n; i += 32) {
+          const double e = sm.eps[i];
+          if (e <= elo) sh += exp(fmax(T((e - elo) / kT), -xmax));
+          else se += exp(fmax(T((ehi - e) / kT), -xmax));
+        }
+        const double shs = warp_sum(double(sh)), ses = warp_sum(double(se));
+        ef = 0.5 * (elo + ehi) + 0.5 * kT * (log(shs) - log(ses));
+      }
     }
     T mts = T(0);
     double fo_min = 2.0, fv_max = 0.0;
@@ -594,7 +606,12 @@ __device__ double fermi_step(int n, double nel, double kT, SccSmem& sm, int* n_o
       s_mts = 2.0 * kT * mts_sum;
       s_nocc = k;
       sm.misc[0] = v;
-      sm.misc[1] = (nro > 0 && v > 0 && fo_min > 2.0 - 1e-14 && fv_max < 1e-14) ? 1 : 0;
+      // tails below ftol (1e-6 in FP32, 1e-10 in FP64) count as integer:
+      // the virtual block is not re-diagonalised by the rotation update, so
+      // a tail occupation f enters the density only through f times the
+      // small residual virtual-virtual rotation
+      const double ftol = sizeof(T) == 8 ? 1e-10 : 1e-6;
+      sm.misc[1] = (nro > 0 && v > 0 && fo_min > 2.0 - ftol && fv_max < ftol) ? 1 : 0;
       sm.misc[2] = nro;
     }
   }
