@@ -341,7 +341,6 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
                      use_f ? P.CTf.p : P.CTd.p, use_f ? P.W1f.p : P.W1d.p, use_f ? P.Agf.p : P.Agd.p,
                      use_f ? 1 : 0, a_in, P.status.as<int>()));
   }
-  ctx->stats.kernel_launches += 3;
   return FMO_OK;
 }
 
@@ -434,7 +433,6 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   cudaEventRecord(e0, st);
   CK(launch_scc(st, nn, L));
   cudaEventRecord(e1, st);
-  ctx->stats.kernel_launches += 1;
   // iteration counts of this launch -> algorithmic flops of the pass
   P.h_iters.resize(nn);
   P.h_iters32.resize(nn);
@@ -770,6 +768,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   cudaSetDevice(ctx->device);
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
   std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+  const long long launches0 = launch_count();
   ctx->have_result = false;
   const int nf = ctx->n_frag;
   ctx->d2h_bytes = 0;
@@ -782,7 +781,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   // ---- coordination numbers of the whole system
   CK(launch_cn(st, ctx->n_atoms, ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(), ctx->d_el.as<DevElem>(), ctx->g,
                ctx->d_cn.as<double>()));
-  ctx->stats.kernel_launches += 2;
   stage(st, "cn");
   // gamma of all shell pairs, kept in HBM while it fits the budget
   {
@@ -794,7 +792,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       CK(ctx->d_gam_full.ensure(gbytes));
       CK(launch_gamma_full(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(),
                            ctx->d_sh_inv_eta.as<double>(), ctx->g, ctx->d_gam_full.as<double>()));
-      ctx->stats.kernel_launches += 1;
     }
   }
   // ---- monomer pass
@@ -840,7 +837,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
                            o.outer_tol, o.e_tol, phase == 1));
       CK(d2h(&hs, ctx->d_mix_state.p, sizeof(hs), st));
       CK(sync_stream(st));
-      ctx->stats.kernel_launches += 2;
       stage(st, "global mix", outer);
       change = hs.converged ? 0.0 : hs.diff;
       if (!(hs.diff == hs.diff)) break;
@@ -867,7 +863,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     CK(cudaMemcpyAsync(ctx->d_dq_mono.p, ctx->mono.dq.p, sizeof(double) * ctx->n_sh, cudaMemcpyDeviceToDevice, st));
     CK(d2h(h_change, ctx->d_scalar.p, sizeof(double), st));
     CK(sync_stream(st));
-    ctx->stats.kernel_launches += 2;
     ctx->stats.n_monomer_solves += nf;
     change = *h_change;
     if (!(change == change)) break;
@@ -878,7 +873,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   ctx->stats.outer_iterations = outer;
   // frozen ESP of the final monomer charges
   CK(compute_phi(ctx, st, 0));
-  ctx->stats.kernel_launches += 1;
   cudaEventRecord(ev[2], st);
   sr.set("fmo_select");
   // ---- n-mer selection
@@ -894,7 +888,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     CK(launch_frag_bounds(st, nf, ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_bounds.as<double>()));
     CK(launch_pair_distance(st, nf, ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_bounds.as<double>(),
                             std::max(o.dimer_cut, o.trimer_cut), ctx->d_rmin.as<double>()));
-    ctx->stats.kernel_launches += 2;
     CK(d2h(rmin.data(), ctx->d_rmin.p, sizeof(double) * npair, st));
     CK(sync_stream(st));
     long long p = 0;
@@ -954,7 +947,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     CK(launch_esdim(st, int(es_pairs.size()), ctx->d_esdim_pairs.as<int2>(), ctx->d_esdim_idx.as<long long>(),
                     ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
                     ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_dE_pair.as<double>()));
-    ctx->stats.kernel_launches += 1;
   }
   cudaEventRecord(ev[4], st);
   sr.set("fmo_trimers");
@@ -983,7 +975,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
                     int(tri_tu.size()), ctx->d_tri_frag.as<int>(), ctx->tri.energy.as<double>(),
                     ctx->tri.dEV.as<double>(), ctx->d_dE3.as<double>(), ctx->d_corr.as<double>(),
                     ctx->d_totals.as<double>()));
-  ctx->stats.kernel_launches += 1;
   stage(st, "fmo sum");
   // ---- results to the host
   ctx->r_e_mono.resize(nf);
@@ -1025,6 +1016,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   ctx->stats.ms_dimer = now_ms(ev[3], ev[4]);
   ctx->stats.ms_trimer = now_ms(ev[4], ev[5]);
   ctx->stats.ms_reduce = now_ms(ev[5], ev[6]);
+  ctx->stats.kernel_launches = launch_count() - launches0;
   for (auto& e : ev) cudaEventDestroy(e);
   // per-pair host arrays in lexicographic order
   ctx->r_pair_scc.assign(npair, 0);

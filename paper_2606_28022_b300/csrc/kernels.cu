@@ -8,6 +8,7 @@
 //   Eqs. 12-15   FMO2, dE^V, ddq, ES-DIM  Eqs. 16-19 FMO3
 //   Eqs. 20-21   embedding Fock matrix V^I from the other fragments' charges
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "fmo_device.cuh"
@@ -1713,7 +1714,17 @@ __global__ void gather_xyz_kernel(int n_atoms, const int* __restrict__ perm, con
 // ---------------------------------------------------------------------------
 // launch wrappers
 
-#define LAUNCH_CHECK() do { cudaError_t e_ = cudaGetLastError(); if (e_ != cudaSuccess) return e_; } while (0)
+// every kernel launch of the library goes through a launch_* wrapper and is
+// followed by exactly one LAUNCH_CHECK, which also counts it
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+
+#define LAUNCH_CHECK()                                   \
+  do {                                                   \
+    g_launches.fetch_add(1, std::memory_order_relaxed);  \
+    cudaError_t e_ = cudaGetLastError();                 \
+    if (e_ != cudaSuccess) return e_;                    \
+  } while (0)
 
 cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int* elem, const DevElem* el,
                       GParams g, double* cn) {

@@ -116,6 +116,8 @@ cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t);
 cudaError_t launch_global_mix(cudaStream_t st, int n, double* x, const double* xo, int nf, const double* e,
                               double* hist, void* state, double tol, double etol, int allow_converge);
 size_t mix_state_bytes();
+// number of kernels launched by this library so far (all threads and contexts)
+long long launch_count();
 cudaError_t launch_maxdiff(cudaStream_t st, int n, const double* a, const double* b, double* out);
 cudaError_t launch_fmo_sum(cudaStream_t st, int n_frag, const double* e_mono, long long n_pair, const int* pair_scc,
                            const double* e_dim, const double* dEV_dim, double* dE_pair, int n_tri,
