@@ -38,6 +38,10 @@ UNIT = "fragment-SCC/s"
 # peaks for the ALU-bound SCC kernel (148 SMs; clocks from the profiling recipe)
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # FP32 FMA lanes x 2 flops x max SM clock
 FP64_PEAK_TFLOPS = 1.25                                 # nominal B300 FP64 rate
+# DRAM bytes (read + write) of the dimer-pass SCC launch of this workload, from
+# one ncu capture of the current kernel (profiles/scc_kernel_anthracene128_fmo2.md);
+# None whenever the kernel has changed since that capture
+DIMER_SCC_DRAM_BYTES = 832445440 + 555923200
 
 
 def workload(rank: int, n_mol: int = 128):
@@ -289,7 +293,8 @@ def main():
     achieved = (f32 + f64) / t_meas / 1e12 if t_meas > 0 else 0.0
     peak = (f32 + f64) / t_min / 1e12 if t_min > 0 else 0.0
     roofline = {"bound": "alu", "kernel": "scc_kernel (dimer pass)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak if peak else 0.0, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak if peak else 0.0,
+                "traffic": DIMER_SCC_DRAM_BYTES if args.n_mol == 128 else None,
                 "peak_basis": f"FP32 {FP32_PEAK_TFLOPS:.1f} TF/s (148 SM x 128 lanes x 2 x 2.032 GHz) and "
                               f"FP64 {FP64_PEAK_TFLOPS} TF/s nominal, weighted by the kernel's FP32/FP64 flops",
                 "flops_fp32": f32, "flops_fp64": f64, "kernel_ms": ms_scc[1],
