@@ -28,11 +28,14 @@ __global__ void cn_kernel(int n_atoms, const double* __restrict__ xyz, const int
   if (a >= n_atoms) return;
   const double xa = xyz[3 * a], ya = xyz[3 * a + 1], za = xyz[3 * a + 2];
   const double ra = el[elem[a]].rcov;
+  const double cut2 = g.cn_cutoff * g.cn_cutoff * (1.0 + 1e-12);   // exact test on r below
   double s = 0.0;
   for (int b = lane; b < n_atoms; b += 32) {
     if (b == a) continue;
     const double dx = xyz[3 * b] - xa, dy = xyz[3 * b + 1] - ya, dz = xyz[3 * b + 2] - za;
-    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= cut2) continue;
+    const double r = sqrt(r2);
     if (r >= g.cn_cutoff) continue;
     const double arg = -g.cn_k1 * (g.cn_k2 * (ra + el[elem[b]].rcov) / r - 1.0);
     s += 1.0 / (1.0 + exp(arg));
@@ -126,9 +129,8 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
     for (int k = 0; k < nm.nfrag; ++k) {
       const Nmer& m = mono[nm.frag[k]];
       const int o = s_foff[k], nk = m.n;
-      for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)nk * nk;
-           e += (long long)gridDim.x * blockDim.x) {
-        const int u = int(e / nk), v = int(e % nk);
+      for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nk * nk; e += gridDim.x * blockDim.x) {
+        const int u = e / nk, v = e - u * nk;
         S[nm.mat + (long long)(o + u) * n + (o + v)] = mono_S[m.mat + e];
         H0[nm.mat + (long long)(o + u) * n + (o + v)] = mono_H0[m.mat + e];
       }
@@ -1539,6 +1541,7 @@ __device__ void neumaier_add(double& s, double& c, double x) {
 struct MixState {
   double e_prev, diff, e1;
   int have_prev, hcount, hhead, converged, count;
+  double gram[kHist * kHist];   // dF_k . dF_l by history slot (each pair formed once)
 };
 
 __global__ void global_mix_kernel(int n, double* __restrict__ x, const double* __restrict__ xo, int nf,
@@ -1565,6 +1568,7 @@ __global__ void global_mix_kernel(int n, double* __restrict__ x, const double* _
   }
   int hcount = st->hcount, hhead = st->hhead;
   const int step = st->count;
+  int new_slot = -1;   // history slot written in this step
   if (step > 0) {
     double nn = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -1580,6 +1584,7 @@ __global__ void global_mix_kernel(int n, double* __restrict__ x, const double* _
         U[(size_t)slot * n + i] = alpha * d + (x[i] - px[i]) / norm;
       }
       if (hcount < kHist) ++hcount; else hhead = (hhead + 1) % kHist;
+      new_slot = slot;
     }
     __syncthreads();
   }
@@ -1590,19 +1595,38 @@ __global__ void global_mix_kernel(int n, double* __restrict__ x, const double* _
   double* c = sa + kHist * kHist;
   double* gv = c + kHist;
   {
-    // the m^2 + m dot products, one warp each (fixed order: deterministic)
+    // dot products, one warp each (fixed order: deterministic): c_k = dF_k . F
+    // for every history vector, and dF_new . dF_k for the vector written in this
+    // step; the other Gram entries are kept in the state from earlier steps
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int q = wid; q < m * m + m; q += nw) {
-      double v = 0.0;
-      if (q < m * m) {
-        const int k = (hhead + q / m) % kHist, l = (hhead + q % m) % kHist;
-        for (int i = lane; i < n; i += 32) v += dF[(size_t)k * n + i] * dF[(size_t)l * n + i];
-      } else {
-        const int k = (hhead + (q - m * m)) % kHist;
-        for (int i = lane; i < n; i += 32) v += dF[(size_t)k * n + i] * pF[i];
+    const int nd = m + (new_slot >= 0 ? m : 0);
+    for (int q = wid; q < nd; q += nw) {
+      const int k = (hhead + (q % m)) % kHist;
+      const double* va = dF + (size_t)k * n;
+      const double* vb = (q < m) ? pF : dF + (size_t)new_slot * n;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int i = lane;
+      for (; i + 96 < n; i += 128) {
+        s0 = fma(va[i], vb[i], s0);
+        s1 = fma(va[i + 32], vb[i + 32], s1);
+        s2 = fma(va[i + 64], vb[i + 64], s2);
+        s3 = fma(va[i + 96], vb[i + 96], s3);
       }
-      v = warp_sum(v);
-      if (lane == 0) { if (q < m * m) a[q] = v; else c[q - m * m] = v; }
+      for (; i < n; i += 32) s0 = fma(va[i], vb[i], s0);
+      const double v = warp_sum((s0 + s1) + (s2 + s3));
+      if (lane == 0) {
+        if (q < m) {
+          c[q] = v;
+        } else {
+          st->gram[new_slot * kHist + k] = v;
+          st->gram[k * kHist + new_slot] = v;
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+      const int k = (hhead + q / m) % kHist, l = (hhead + q % m) % kHist;
+      a[q] = st->gram[k * kHist + l];
     }
   }
   __syncthreads();
