@@ -25,6 +25,14 @@ READINGS (listed in the design notes):
        SCC trimer iff all three pair distances < trimer_cut.
   C-11 E^V_{X,Y} sums over fragments K not in the n-mer Y.
   C-12 only SCC trimers contribute; their sub-pair terms are the FMO2 ones.
+  C-13 hybrid orbital projection (HOP) at cut covalent bonds: V_HOP =
+       params.v_hop (1e6 Eh); the detached BDA keeps its basis and nucleus but
+       its reference occupations are scaled to one electron less; its ghost in
+       the BAA's fragment has the BDA's element, basis, position and
+       supersystem CN, q0 = (1/4, 3/4) on its s and p shell, real gamma and
+       third-order terms but no repulsion; both hybrids point from BDA to
+       BAA; p functions in x, y, z order.  A bond is healed in every n-mer
+       holding both of its fragments.
 """
 from __future__ import annotations
 
@@ -76,29 +84,62 @@ class FMOResult:
     dimer_iters: np.ndarray
 
 
+C_S, C_P = 0.5, np.sqrt(3.0) / 2.0   # sp3 hybrid coefficients of the HOP hybrid
+
+
 class _Frags:
-    """Per-fragment atoms, shell positions and shell hardnesses."""
+    """Per-fragment atom records, shell positions and shell hardnesses.
+
+    A record is (atom, bond): a real atom of the fragment (bond = -1) or the
+    ghost of a cut bond's detachment atom (BDA) hosted by the fragment of its
+    attachment atom (BAA): a copy of the BDA at its position (Sec. "Covalent
+    bond fragmentation", hybrid orbital projection).  A monomer holds every
+    record of its fragment; in an n-mer a bond whose BDA and BAA fragments
+    are both present is healed (its ghost is left out, the BDA is a normal
+    atom), any other cut bond stays detached."""
 
     def __init__(self, system, params):
         self.system = system
         self.params = params
-        self.atoms = [np.nonzero(system.frag == f)[0] for f in range(system.n_frag)]
+        nf = system.n_frag
+        self.atoms = [np.nonzero(system.frag == f)[0] for f in range(nf)]
         self.cn = xtb.coordination_numbers(system.Z, system.xyz, params)
-        self.sh_pos, self.sh_eta, self.n_sh = [], [], []
-        for f in range(system.n_frag):
-            Z = system.Z[self.atoms[f]]
-            b = xtb.make_basis(Z, params)
-            self.sh_pos.append(system.xyz[self.atoms[f]][b.sh_atom])
-            self.sh_eta.append(xtb.shell_hardness(Z, b, params))
-            self.n_sh.append(b.n_sh)
+        self.cut = np.asarray(system.cut_bonds, dtype=np.int64).reshape(-1, 2)
+        self.bond_frag = [(int(system.frag[a]), int(system.frag[b])) for a, b in self.cut]
+        self.recs = []
+        for f in range(nf):
+            r = [(int(a), -1) for a in self.atoms[f]]
+            r += [(int(self.cut[k, 0]), k) for k in range(len(self.cut)) if self.bond_frag[k][1] == f]
+            self.recs.append(r)
+        self.sh_pos, self.sh_eta, self.n_sh, self.sh_rec = [], [], [], []
+        for f in range(nf):
+            at = np.array([a for a, _ in self.recs[f]], dtype=np.int64)
+            Z = system.Z[at]
+            bas = xtb.make_basis(Z, params)
+            self.sh_pos.append(system.xyz[at][bas.sh_atom])
+            self.sh_eta.append(xtb.shell_hardness(Z, bas, params))
+            self.n_sh.append(bas.n_sh)
+            self.sh_rec.append(bas.sh_atom.copy())     # record of each monomer shell
 
     def gamma(self, I, J):
         return xtb.gamma_between(self.sh_pos[I], self.sh_eta[I], self.sh_pos[J], self.sh_eta[J],
                                  self.params.k_g)
 
-    def esp(self, nmer, dq_mono):
-        """ESP^{not X}_mu on the shells of n-mer X from the monomer charges of
-        every fragment K outside X (Eq. 21 / READING C-11)."""
+    def present(self, nmer):
+        """Per fragment of the n-mer: mask of its records present in the n-mer
+        (healed ghosts absent)."""
+        return [np.array([bond < 0 or self.bond_frag[bond][0] not in nmer for _, bond in self.recs[f]])
+                for f in nmer]
+
+    def shell_mask(self, nmer):
+        """Mask over the concatenated monomer shells of the n-mer's fragments:
+        True where the shell is also an n-mer shell."""
+        pres = self.present(nmer)
+        return np.concatenate([pres[k][self.sh_rec[f]] for k, f in enumerate(nmer)])
+
+    def esp_full(self, nmer, dq_mono):
+        """ESP^{not X} on every monomer shell of the n-mer's fragments, from the
+        monomer charges of every fragment K outside X (Eq. 21 / READING C-11)."""
         out = []
         for I in nmer:
             v = np.zeros(self.n_sh[I])
@@ -109,18 +150,81 @@ class _Frags:
             out.append(v)
         return np.concatenate(out)
 
+    def esp(self, nmer, dq_mono):
+        """ESP^{not X} on the shells of n-mer X."""
+        return self.esp_full(nmer, dq_mono)[self.shell_mask(nmer)]
+
     def closest(self, I, J):
         a = self.system.xyz[self.atoms[I]]
         b = self.system.xyz[self.atoms[J]]
         return float(np.sqrt(((a[:, None, :] - b[None, :, :]) ** 2).sum(-1)).min())
 
+    def problem(self, nmer, esp=None):
+        """The SCC problem of n-mer X: real atoms of its fragments plus the
+        ghosts of its detached bonds, with (READING C-13)
+          - a detached BDA: its reference occupations q0 scaled so that they
+            sum to one electron less, and the projector D^BDA = V h h^T;
+          - a ghost: the BDA's element, basis, position and supersystem CN,
+            q0 = (c_s^2, c_p^2) = (1/4, 3/4) on its s and p shell, no
+            repulsion, projector D^ghost = V (1_sp - h h^T);
+          - h = c_s s + c_p (b . p) with b the unit vector from BDA to BAA;
+        and V^HOP = sum over projected atoms of S[:, atom] D S[atom, :] added to
+        the Fock matrix but kept out of the energy (Eqs. of the HOP section)."""
+        s, p = self.system, self.params
+        recs = [r for k, f in enumerate(nmer) for r, keep in zip(self.recs[f], self.present(nmer)[k]) if keep]
+        at = np.array([a for a, _ in recs], dtype=np.int64)
+        Z, xyz, cn = s.Z[at], s.xyz[at], self.cn[at]
+        bas = xtb.make_basis(Z, p)
+        q0 = xtb.shell_param(Z, bas, p, "q0_l")
+        rep_mask = np.array([bond < 0 for _, bond in recs])
+        proj = []                                   # (record index, bond, kind)
+        for i, (a, bond) in enumerate(recs):
+            if bond >= 0:
+                proj.append((i, bond, "ghost"))
+            else:
+                for k in range(len(self.cut)):
+                    if self.cut[k, 0] == a and self.bond_frag[k][1] not in nmer:
+                        proj.append((i, k, "bda"))
+        extra = None
+        for i, bond, kind in proj:
+            sh = np.nonzero(bas.sh_atom == i)[0]
+            ls = bas.sh_l[sh]
+            if sorted(ls.tolist()) != [0, 1]:
+                raise ValueError("a HOP boundary atom needs exactly one s and one p shell")
+            s_sh, p_sh = sh[ls == 0][0], sh[ls == 1][0]
+            if kind == "ghost":
+                q0[s_sh], q0[p_sh] = C_S ** 2, C_P ** 2
+            else:
+                q0[sh] *= (np.sum(q0[sh]) - 1.0) / np.sum(q0[sh])
+            bvec = s.xyz[self.cut[bond, 1]] - s.xyz[self.cut[bond, 0]]
+            bvec = bvec / np.linalg.norm(bvec)
+            idx = np.concatenate([[bas.sh_ao0[s_sh]], bas.sh_ao0[p_sh] + np.arange(3)])
+            h = np.concatenate([[C_S], C_P * bvec])
+            D = p.v_hop * (np.outer(h, h) if kind == "bda" else np.eye(4) - np.outer(h, h))
+            if extra is None:
+                S = xtb.overlap_matrix(Z, xyz, p, bas)
+                extra = np.zeros_like(S)
+            extra += S[:, idx] @ D @ S[idx, :]
+        charge = float(sum(s.frag_charge[f] for f in nmer))
+        return xtb.SCCProblem(Z, xyz, p, cn, esp=esp, charge=charge, extra_fock=extra,
+                              n_el=float(np.sum(q0)) - charge, q0=q0, rep_mask=rep_mask)
+
     def solve(self, nmer, esp, guess, opts):
-        idx = np.concatenate([self.atoms[f] for f in nmer])
-        s = self.system
         mixer = xtb.Broyden() if opts.mixer == "broyden" else xtb.LinearMixer(0.4)
-        return xtb.scc(s.Z[idx], s.xyz[idx], self.params, self.cn[idx], esp=esp, guess=guess,
-                       charge=float(sum(s.frag_charge[f] for f in nmer)), tol=opts.scc_tol,
-                       e_tol=opts.e_tol, max_iter=opts.max_iter, mixer=mixer)
+        return xtb.solve_problem(self.problem(nmer, esp), guess=guess, tol=opts.scc_tol, e_tol=opts.e_tol,
+                                 max_iter=opts.max_iter, mixer=mixer)
+
+
+def _embedding_correction(fr, nmer, dq, dq_mono):
+    """dE^V_X = sum_mu ddq^X_mu ESP^{not X}_mu (Eqs. 13-14, 18) over the
+    monomer shells of X: ddq = dq^X - dq^mono on shells of the n-mer, and
+    ddq = -dq^mono on the ghost shells of bonds healed in X (the charge the
+    ghost carried in its monomer, HOP section)."""
+    mask = fr.shell_mask(nmer)
+    mono = np.concatenate([dq_mono[f] for f in nmer])
+    full = np.zeros_like(mono)
+    full[mask] = dq
+    return float((full - mono) @ fr.esp_full(nmer, dq_mono))
 
 
 def _global_monomer_loop(fr, opts):
@@ -131,9 +235,7 @@ def _global_monomer_loop(fr, opts):
     nf = s.n_frag
     probs = []
     for I in range(nf):
-        idx = fr.atoms[I]
-        probs.append(xtb.SCCProblem(s.Z[idx], s.xyz[idx], fr.params, fr.cn[idx],
-                                    charge=float(s.frag_charge[I])))
+        probs.append(fr.problem((I,)))
     bounds = np.concatenate([[0], np.cumsum(fr.n_sh)])
     split = lambda x: [x[bounds[I]:bounds[I + 1]] for I in range(nf)]
     x = np.zeros(bounds[-1])
@@ -221,16 +323,15 @@ def fmo(system, params, opts: FMOOptions | None = None) -> FMOResult:
         jobs, where = [], []
         for k, (I, J) in enumerate(pairs):
             if scc_pair[k]:
-                esp = fr.esp((I, J), dq_mono)
-                jobs.append(((I, J), esp, np.concatenate([dq_mono[I], dq_mono[J]])))
+                mask = fr.shell_mask((I, J))
+                esp = fr.esp_full((I, J), dq_mono)
+                jobs.append(((I, J), esp[mask], np.concatenate([dq_mono[I], dq_mono[J]])[mask]))
                 where.append(k)
             else:
                 dE[k] = float(dq_mono[I] @ fr.gamma(I, J) @ dq_mono[J])       # Eq. 15
         for k, (job, (e, dq, it, ok)) in zip(where, zip(jobs, run_many(jobs))):
             I, J = pairs[k]
-            esp = job[1]
-            ddq = dq - np.concatenate([dq_mono[I], dq_mono[J]])              # Eq. 14
-            dEV[k] = float(ddq @ esp)                                        # Eq. 13
+            dEV[k] = _embedding_correction(fr, (int(I), int(J)), dq, dq_mono)   # Eqs. 13-14
             e_dim[k] = e
             dE[k] = e - e_mono[I] - e_mono[J] + dEV[k]                       # Eq. 12
             d_iters[k] = it
@@ -248,14 +349,13 @@ def fmo(system, params, opts: FMOOptions | None = None) -> FMOResult:
                    if (t[0], t[1]) in near and (t[0], t[2]) in near and (t[1], t[2]) in near]
             trimers = np.array(tri, dtype=np.int64).reshape(-1, 3)
             jobs = [(tuple(t), fr.esp(tuple(t), dq_mono),
-                     np.concatenate([dq_mono[f] for f in t])) for t in tri]
+                     np.concatenate([dq_mono[f] for f in t])[fr.shell_mask(tuple(t))]) for t in tri]
             res = run_many(jobs)
             dE3 = np.zeros(len(tri))
             corr = np.zeros(len(tri))
             for k, (t, job, (e, dq, it, ok)) in enumerate(zip(tri, jobs, res)):
                 I, J, K = t
-                ddq = dq - np.concatenate([dq_mono[f] for f in t])
-                dEV3 = float(ddq @ job[1])                                   # Eq. 18 / C-11
+                dEV3 = _embedding_correction(fr, tuple(int(f) for f in t), dq, dq_mono)   # Eq. 18 / C-11
                 dE3[k] = e - e_mono[I] - e_mono[J] - e_mono[K] + dEV3        # Eq. 17
                 corr[k] = (dE3[k] - dE[pair_index[(I, J)]] - dE[pair_index[(I, K)]]
                            - dE[pair_index[(J, K)]])                         # Eq. 16

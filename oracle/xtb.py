@@ -366,16 +366,24 @@ class SCCProblem:
     the map from input shell charges to the output density and energy: one
     iteration of the SCC loop (Eqs. 2, 3, 6, 7 and the ESP of Eq. 24)."""
 
-    def __init__(self, Z, xyz, params, cn, esp=None, charge=0.0, extra_fock=None, n_el=None):
+    def __init__(self, Z, xyz, params, cn, esp=None, charge=0.0, extra_fock=None, n_el=None, q0=None,
+                 rep_mask=None):
         self.Z, self.xyz, self.params = Z, xyz, params
         self.kT = 3.166811563e-6 * params.t_el
         self.basis = b = make_basis(Z, params)
         self.S = overlap_matrix(Z, xyz, params, b)
         self.H0 = h0_matrix(Z, xyz, params, self.S, cn, b)
         self.gam = gamma_matrix(Z, xyz, params, b)
-        self.q0 = shell_param(Z, b, params, "q0_l")
+        # q0: per-shell reference occupations (default: the element's); rep_mask:
+        # atoms that take part in the repulsion (default: all) -- both differ
+        # from the defaults only at HOP boundaries (oracle/fmo.py)
+        self.q0 = shell_param(Z, b, params, "q0_l") if q0 is None else np.asarray(q0, dtype=np.float64)
         self.g3 = atom_param(Z, params, "gamma3")
-        self.e_rep = repulsion_energy(Z, xyz, params)
+        if rep_mask is None:
+            self.e_rep = repulsion_energy(Z, xyz, params)
+        else:
+            m = np.asarray(rep_mask, dtype=bool)
+            self.e_rep = repulsion_energy(np.asarray(Z)[m], np.asarray(xyz)[m], params)
         self.n_el = n_electrons(Z, params, charge) if n_el is None else n_el
         self.esp = np.zeros(b.n_sh) if esp is None else np.asarray(esp, dtype=np.float64)
         self.extra_fock = extra_fock
@@ -425,6 +433,12 @@ def scc(Z, xyz, params, cn, esp=None, guess=None, charge=0.0, tol=1e-10, e_tol=1
     density (READING C-2).
     """
     prob = SCCProblem(Z, xyz, params, cn, esp=esp, charge=charge, extra_fock=extra_fock, n_el=n_el)
+    return solve_problem(prob, guess=guess, tol=tol, e_tol=e_tol, max_iter=max_iter, mixer=mixer)
+
+
+def solve_problem(prob: "SCCProblem", guess=None, tol=1e-10, e_tol=1e-10, max_iter=300,
+                  mixer=None) -> SCCResult:
+    """The SCC loop of scc() on an already assembled SCCProblem."""
     dq = np.zeros(prob.basis.n_sh) if guess is None else np.asarray(guess, dtype=np.float64).copy()
     mixer = Broyden() if mixer is None else mixer
     e_prev = None

@@ -57,9 +57,13 @@ class System:
         frags = list(frags)
         idx = np.concatenate([np.nonzero(self.frag == f)[0] for f in frags])
         remap = {f: i for i, f in enumerate(frags)}
+        new_of = {int(a): i for i, a in enumerate(idx)}
+        cuts = [(new_of[int(a)], new_of[int(b)]) for a, b in self.cut_bonds
+                if int(a) in new_of and int(b) in new_of]     # cut bonds inside the subsystem
         return System(Z=self.Z[idx].copy(), xyz=self.xyz[idx].copy(),
                       frag=np.array([remap[f] for f in self.frag[idx]], dtype=np.int32),
-                      frag_charge=self.frag_charge[frags].copy(), name=self.name + "-sub")
+                      frag_charge=self.frag_charge[frags].copy(),
+                      cut_bonds=np.array(cuts, dtype=np.int32).reshape(-1, 2), name=self.name + "-sub")
 
 
 def _random_rotation(rng) -> np.ndarray:
@@ -263,3 +267,88 @@ def separated(system: System, distance_A: float) -> System:
     for f in range(system.n_frag):
         xyz[system.frag == f, 0] += f * distance_A * ANGSTROM
     return dataclasses.replace(system, xyz=xyz)
+
+
+# --------------------------------------------------------------------------
+# alpha-helical polyalanine with covalent fragment boundaries (C3 stand-in)
+
+
+def _place(a, b, c, r, theta_deg, chi_deg):
+    """Position of atom d bonded to c with |cd| = r, angle b-c-d = theta and
+    dihedral a-b-c-d = chi (internal coordinates to Cartesian)."""
+    bc = (c - b) / np.linalg.norm(c - b)
+    n = np.cross(b - a, bc)
+    n /= np.linalg.norm(n)
+    m = np.cross(n, bc)
+    th, ch = np.radians(theta_deg), np.radians(chi_deg)
+    d = np.array([-r * np.cos(th), r * np.sin(th) * np.cos(ch), r * np.sin(th) * np.sin(ch)])
+    return c + d[0] * bc + d[1] * m + d[2] * n
+
+
+def polyalanine_helix(n_res: int, phi=-57.0, psi=-47.0, omega=180.0, seed: int | None = None,
+                      frag_sizes=(1, 2, 3)):
+    """H-(Ala)n-OH as an ideal helix from standard bond lengths and angles
+    (N-CA 1.458, CA-C 1.525, C-N 1.329, C=O 1.231, N-H 1.01, C-H 1.09,
+    CA-CB 1.53 A; N-CA-C 111.2, CA-C-N 116.2, C-N-CA 121.7 deg).
+
+    Residue units are cut at the CA-C(O) bonds: unit i holds C(i-1), O(i-1),
+    N(i), H(i), CA(i), HA(i), CB(i) and its three H; the first unit carries
+    the N-terminal H, the last the C-terminal C(=O)-OH.  Consecutive units are
+    joined into fragments of 1, 2 or 3 residues drawn from the seed (seed None:
+    one residue per fragment); every CA-C bond between two fragments is a cut
+    bond with the CA as detachment atom (BDA) and the C as attachment atom."""
+    rng = np.random.default_rng(seed) if seed is not None else None
+    xyz, Z, unit = [], [], []
+
+    def add(z, p, u):
+        Z.append(z)
+        xyz.append(np.asarray(p, dtype=np.float64))
+        unit.append(u)
+        return len(Z) - 1
+
+    # backbone N, CA, C of every residue
+    N = [np.array([0.0, 0.0, 0.0])]
+    CA = [np.array([1.458, 0.0, 0.0])]
+    C = [_place(np.array([0.0, 1.0, 0.0]), N[0], CA[0], 1.525, 111.2, 0.0)]
+    for i in range(1, n_res):
+        N.append(_place(N[i - 1], CA[i - 1], C[i - 1], 1.329, 116.2, psi))
+        CA.append(_place(CA[i - 1], C[i - 1], N[i], 1.458, 121.7, omega))
+        C.append(_place(C[i - 1], N[i], CA[i], 1.525, 111.2, phi))
+    ca_idx, c_idx = [], []
+    for i in range(n_res):
+        if i > 0:   # the previous residue's carbonyl belongs to this unit
+            c_idx.append(add(6, C[i - 1], i))
+            add(8, _place(N[i - 1], CA[i - 1], C[i - 1], 1.231, 120.5, psi + 180.0), i)
+            add(1, _place(CA[i - 1], C[i - 1], N[i], 1.01, 119.5, 0.0), i)            # H on N
+        else:
+            add(1, _place(C[0], CA[0], N[0], 1.01, 109.5, 60.0), 0)                  # N-terminal H
+            add(1, _place(C[0], CA[0], N[0], 1.01, 109.5, -60.0), 0)
+        add(7, N[i], i)
+        ca_idx.append(add(6, CA[i], i))
+        ref = C[i - 1] if i > 0 else _place(C[0], CA[0], N[0], 1.0, 109.5, 180.0)
+        cb = _place(ref, N[i], CA[i], 1.53, 110.5, phi - 120.0 if i > 0 else 180.0 - 120.0)
+        add(6, cb, i)
+        add(1, _place(ref, N[i], CA[i], 1.09, 109.5, phi + 120.0 if i > 0 else 180.0 + 120.0), i)   # HA
+        for chi in (60.0, 180.0, 300.0):
+            add(1, _place(N[i], CA[i], cb, 1.09, 109.5, chi), i)
+    last = n_res - 1
+    c_idx.append(add(6, C[last], last))
+    add(8, _place(N[last], CA[last], C[last], 1.231, 120.5, psi + 180.0), last)
+    ot = _place(N[last], CA[last], C[last], 1.34, 116.2, psi)
+    add(8, ot, last)
+    add(1, _place(CA[last], C[last], ot, 0.97, 107.0, 180.0), last)
+    # fragments of 1-3 consecutive residues
+    frag_of_res, f, i = [], 0, 0
+    while i < n_res:
+        k = 1 if rng is None else int(rng.choice(frag_sizes))
+        for _ in range(min(k, n_res - i)):
+            frag_of_res.append(f)
+        i += k
+        f += 1
+    frag = np.array([frag_of_res[u] for u in unit], dtype=np.int32)
+    # cut bonds CA(i)-C(i) between fragments: BDA = CA(i), BAA = C(i) (unit i+1)
+    cuts = [(ca_idx[i], c_idx[i]) for i in range(n_res - 1) if frag_of_res[i] != frag_of_res[i + 1]]
+    xyz = np.array(xyz) * ANGSTROM
+    return System(Z=np.array(Z, dtype=np.int32), xyz=xyz, frag=frag,
+                  frag_charge=np.zeros(f, dtype=np.int32),
+                  cut_bonds=np.array(cuts, dtype=np.int32).reshape(-1, 2), name=f"ala{n_res}-helix")

@@ -401,3 +401,79 @@ def test_ddq_of_neutral_dimers_sums_to_zero(params, water64):
     # the charge moved between I and J on dimer formation is conserved: the
     # dimer and the two monomers carry the same total charge
     assert np.all(np.isfinite(r.dE_dimer))
+
+
+# ---------------------------------------------------------------------------
+# hybrid orbital projection (HOP) boundaries
+
+
+def test_polyalanine_generator_sizes_and_closed_shells(params):
+    s = G.polyalanine_helix(300, seed=11)
+    assert s.n_atoms == 3003 and 100 <= s.n_frag <= 300
+    assert len(s.cut_bonds) == s.n_frag - 1
+    for f in range(s.n_frag):
+        ne = sum(params.elements[int(z)].n_valence for z in s.Z[s.frag == f])
+        ne += np.sum(s.frag[s.cut_bonds[:, 1]] == f) - np.sum(s.frag[s.cut_bonds[:, 0]] == f)
+        assert ne % 2 == 0
+    d = np.linalg.norm(s.xyz[s.cut_bonds[:, 0]] - s.xyz[s.cut_bonds[:, 1]], axis=1) / ANGSTROM
+    assert np.allclose(d, 1.525)
+
+
+def test_hop_two_fragments_fmo2_equals_full_scc(params):
+    # with N = 2 the only dimer heals the cut bond and sees no environment,
+    # so FMO2 is the SCC of the whole molecule, whatever the monomers hold
+    s = G.polyalanine_helix(2)
+    full = xtb.single_point(s, params)
+    r = fmo.fmo(s, params, fmo.FMOOptions(level=2))
+    assert abs(r.e_fmo2 - full.energy) < 1e-9
+    assert abs(r.e_fmo1 - full.energy) > 1e-3       # the monomers alone miss the bond
+
+
+def test_hop_three_fragments_fmo3_equals_full_scc(params):
+    s = G.polyalanine_helix(3)
+    full = xtb.single_point(s, params)
+    r = fmo.fmo(s, params, fmo.FMOOptions(level=3, all_dimers_scc=True, trimer_cut=1e9))
+    assert len(r.trimers) == 1
+    assert abs(r.e_fmo3 - full.energy) < 1e-9
+
+
+def _hop_monomer(params, v_hop=None):
+    import dataclasses
+    p = params if v_hop is None else dataclasses.replace(params, v_hop=v_hop)
+    s = G.polyalanine_helix(3)
+    fr = fmo._Frags(s, p)
+    prob = fr.problem((1,))           # middle residue: one ghost and one detached BDA
+    return s, fr, prob, xtb.solve_problem(prob)
+
+
+def test_hop_projectors_empty_their_orbitals(params):
+    s, fr, prob, res = _hop_monomer(params)
+    assert res.converged
+    assert abs(np.sum(res.dq)) < 1e-9 and abs(np.sum(prob.q0) - prob.n_el) < 1e-12
+    b = prob.basis
+    recs = [r for r in fr.recs[1]]
+    for i, (a, bond) in enumerate(recs):
+        bda, baa = fr.cut[bond] if bond >= 0 else (a, None)
+        if bond < 0 and not any(fr.cut[k, 0] == a for k in range(len(fr.cut))):
+            continue
+        k = bond if bond >= 0 else [k for k in range(len(fr.cut)) if fr.cut[k, 0] == a][0]
+        u = s.xyz[fr.cut[k, 1]] - s.xyz[fr.cut[k, 0]]
+        u /= np.linalg.norm(u)
+        sh = np.nonzero(b.sh_atom == i)[0]
+        idx = np.concatenate([[b.sh_ao0[sh[0]]], b.sh_ao0[sh[1]] + np.arange(3)])
+        h = np.concatenate([[fmo.C_S], fmo.C_P * u])
+        if bond < 0:                   # detached BDA: the bond hybrid is empty
+            vecs = h[None, :]
+        else:                          # ghost: everything but the bond hybrid is empty
+            q, _ = np.linalg.qr(np.column_stack([h, np.eye(4)]))
+            vecs = q[:, 1:4].T
+        for v in vecs:
+            w = prob.S[:, idx] @ v
+            assert w @ res.P @ w < 1e-4
+
+
+def test_hop_energy_converges_as_one_over_v(params):
+    e = [_hop_monomer(params, v)[3].energy for v in (1e5, 1e6, 1e7)]
+    d1, d2 = e[0] - e[1], e[1] - e[2]
+    assert abs(d2) < 1e-5
+    assert 7.0 < d1 / d2 < 13.0
