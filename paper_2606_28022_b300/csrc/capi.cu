@@ -46,10 +46,12 @@ struct Pass {
   long long tot_mat = 0, tot_sh = 0, tot_gam = 0, tot_ao = 0, tot_hist = 0, tot_apad = 0;
   DevBuf d_nm, d_order, S, H0, gam, CTd, W1d, W2d, Agd, CTf, W1f, W2f, Agf, esp, dq, eps, hist;
   DevBuf energy, e_el, e_rep, dEV, iters, iters32, status;
+  DevBuf V;                               // hybrid orbital projectors (n x n per n-mer)
+  int max_healed_sh = 0, max_projected = 0;
   std::vector<int> h_iters, h_iters32;
   void release() {
     for (DevBuf* b : {&d_nm, &d_order, &S, &H0, &gam, &CTd, &W1d, &W2d, &Agd, &CTf, &W1f, &W2f, &Agf, &esp, &dq,
-                      &eps, &hist, &energy, &e_el, &e_rep, &dEV, &iters, &iters32, &status})
+                      &eps, &hist, &energy, &e_el, &e_rep, &dEV, &iters, &iters32, &status, &V})
       b->release();
   }
 };
@@ -104,6 +106,14 @@ struct fmo_ctx {
   // system
   bool have_system = false;
   int n_atoms = 0, n_frag = 0, n_sh = 0, n_ao = 0;
+  // hybrid orbital projection: cut bonds, and the internal atom list (real
+  // atoms, then per fragment the ghosts of the bonds whose BAA it holds)
+  int n_cut = 0, n_int = 0;
+  std::vector<int> h_ghost_frag, h_ghost_src, h_bda_baa_frag, h_hop_baa;
+  struct GhostInfo { int bda_frag, nsh, nao; };
+  std::vector<std::vector<GhostInfo>> f_ghosts;   // per hosting fragment
+  std::vector<std::vector<int>> f_bda_baa_frag;   // per fragment: BAA fragment of each of its BDAs
+  DevBuf d_ghost_frag, d_ghost_src, d_bda_baa_frag, d_hop_baa;
   std::vector<int> perm;                  // internal atom i <- input atom perm[i]
   std::vector<int> h_elem, h_atom_sh0, h_sh_atom;
   std::vector<int> f_atom0, f_nat, f_sh0, f_nsh, f_ao0, f_nao;
@@ -131,8 +141,15 @@ struct fmo_ctx {
   int64_t h2d_bytes = 0, d2h_bytes = 0;
 
   FragTab ftab() const {
-    return FragTab{d_f_atom0.as<int>(), d_f_nat.as<int>(), d_f_sh0.as<int>(),
-                   d_f_nsh.as<int>(), d_f_ao0.as<int>(), d_f_nao.as<int>()};
+    FragTab t{d_f_atom0.as<int>(), d_f_nat.as<int>(), d_f_sh0.as<int>(),
+              d_f_nsh.as<int>(), d_f_ao0.as<int>(), d_f_nao.as<int>()};
+    if (n_cut > 0) {
+      t.ghost_frag = d_ghost_frag.as<int>();
+      t.ghost_src = d_ghost_src.as<int>();
+      t.bda_baa_frag = d_bda_baa_frag.as<int>();
+      t.hop_baa = d_hop_baa.as<int>();
+    }
+    return t;
   }
 };
 
@@ -218,6 +235,7 @@ cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3
                       const std::vector<int>& nf, bool monomer_layout, int precision, cudaStream_t st) {
   P.nm.clear();
   P.max_n = P.max_nsh = P.max_nat = P.max_pairs = 0;
+  P.max_healed_sh = P.max_projected = 0;
   long long mat = 0, sh = 0, gam = 0, ao = 0, hist = 0, apad = 0;
   for (size_t t = 0; t < tuples.size(); ++t) {
     Nmer m{};
@@ -225,13 +243,26 @@ cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3
     int n = 0, ns = 0, na = 0;
     double nel = 0.0;
     for (int k = 0; k < 3; ++k) m.frag[k] = (k < m.nfrag) ? tuples[t][k] : -1;
+    int healed_sh = 0, projected = 0;
     for (int k = 0; k < m.nfrag; ++k) {
       const int f = tuples[t][k];
       n += ctx->f_nao[f];
       ns += ctx->f_nsh[f];
       na += ctx->f_nat[f];
       nel += ctx->f_nel[f];
+      if (ctx->n_cut == 0) continue;
+      // ghosts of bonds healed here leave the n-mer; healing moves the
+      // ghost's electron back to the BDA, so the electron count is unchanged
+      for (const auto& gh : ctx->f_ghosts[f]) {
+        const bool healed = std::find(m.frag, m.frag + m.nfrag, gh.bda_frag) != m.frag + m.nfrag;
+        if (healed) { n -= gh.nao; ns -= gh.nsh; na -= 1; healed_sh += gh.nsh; }
+        else ++projected;
+      }
+      for (int baa_f : ctx->f_bda_baa_frag[f])
+        if (std::find(m.frag, m.frag + m.nfrag, baa_f) == m.frag + m.nfrag) ++projected;
     }
+    P.max_healed_sh = std::max(P.max_healed_sh, healed_sh);
+    P.max_projected = std::max(P.max_projected, projected);
     m.n = n; m.nsh = ns; m.nat = na; m.npad = n + (n & 1); m.nel = nel;
     m.mat = mat; m.gam = gam; m.aov = ao; m.hist = hist; m.apad = apad;
     m.shv = monomer_layout ? ctx->f_sh0[tuples[t][0]] : sh;
@@ -278,6 +309,7 @@ cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3
   ENS(P.iters, sizeof(int) * nn);
   ENS(P.iters32, sizeof(int) * nn);
   ENS(P.status, sizeof(int) * nn);
+  if (ctx->n_cut > 0) ENS(P.V, sizeof(double) * std::max<long long>(mat, 1));
 #undef ENS
   if ((e = upload(P.d_nm, P.nm, st)) != cudaSuccess) return e;
   if ((e = upload(P.d_order, P.order, st)) != cudaSuccess) return e;
@@ -290,7 +322,10 @@ struct SmemPlan {
 };
 
 // Limits of the fixed-size index maps of the integral and gamma kernels.
-bool pass_fits(const Pass& P) { return P.max_nat <= 512 && P.max_nsh <= 1024 && P.max_n <= 4000; }
+bool pass_fits(const Pass& P) {
+  return P.max_nat <= 512 && P.max_nsh <= 1024 && P.max_n <= 4000 && P.max_healed_sh <= kMaxHealedShells &&
+         P.max_projected <= kMaxProjected;
+}
 
 SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision) {
   const int npad = P.max_n + (P.max_n & 1);
@@ -312,14 +347,20 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
   const int nn = int(P.nm.size());
   if (nn == 0) return FMO_OK;
   const SmemPlan& s = sp;
+  // the monomer S/H0 blocks are reused in the n-mers unless ghost atoms make
+  // the fragment blocks of the two passes differ
+  const bool reuse = warm_from != nullptr && ctx->n_cut == 0;
   if (!s.a_d) CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
   if (precision == FMO_PREC_MIXED && !s.a_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
   CK(launch_integrals(st, nn, P.max_pairs, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
                       ctx->d_elem.as<int>(), ctx->d_atom_sh0.as<int>(), ctx->d_cn.as<double>(),
                       ctx->d_el.as<DevElem>(), ctx->d_kab.as<double>(), ctx->ne, ctx->g, P.S.as<double>(),
-                      P.H0.as<double>(), warm_from ? warm_from->d_nm.as<Nmer>() : nullptr,
-                      warm_from ? warm_from->S.as<double>() : nullptr,
-                      warm_from ? warm_from->H0.as<double>() : nullptr, ctx->d_prim.as<PrimPair>()));
+                      P.H0.as<double>(), reuse ? warm_from->d_nm.as<Nmer>() : nullptr,
+                      reuse ? warm_from->S.as<double>() : nullptr,
+                      reuse ? warm_from->H0.as<double>() : nullptr, ctx->d_prim.as<PrimPair>()));
+  if (ctx->n_cut > 0)
+    CK(launch_hop_projector(st, nn, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(),
+                            ctx->d_el.as<DevElem>(), ctx->params.v_hop, P.S.as<double>(), P.V.as<double>()));
   CK(launch_gamma(st, nn, P.max_nsh, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
                   ctx->d_elem.as<int>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(), ctx->g,
                   P.gam.as<double>()));
@@ -386,6 +427,7 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.CTd = P.CTd.as<double>(); L.W1d = P.W1d.as<double>(); L.W2d = P.W2d.as<double>(); L.Agd = P.Agd.as<double>();
   L.CTf = P.CTf.as<float>(); L.W1f = P.W1f.as<float>(); L.W2f = P.W2f.as<float>(); L.Agf = P.Agf.as<float>();
   L.phi = with_phi ? ctx->d_phi.as<double>() : nullptr;
+  L.vhop = ctx->n_cut > 0 ? P.V.as<double>() : nullptr;
   L.dq_mono = ctx->d_dq_mono.as<double>();
   L.esp = P.esp.as<double>(); L.dq = P.dq.as<double>(); L.eps = P.eps.as<double>(); L.hist = P.hist.as<double>();
   L.energy = P.energy.as<double>(); L.e_el = P.e_el.as<double>(); L.e_rep = P.e_rep.as<double>();
@@ -559,7 +601,7 @@ void fmo_destroy(fmo_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_prim, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
                     &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
-                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_gam_full, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
+                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_gam_full, &ctx->d_ghost_frag, &ctx->d_ghost_src, &ctx->d_bda_baa_frag, &ctx->d_hop_baa, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
                     &ctx->d_totals})
@@ -579,10 +621,9 @@ fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const
                           const int32_t* bda_baa) {
   g_ctx = ctx;
   if (!ctx) return FMO_ERR_ARG;
-  (void)bda_baa;
   if (n_atoms <= 0 || n_frag <= 0 || !Z || !xyz || !frag_of_atom || !frag_charge)
     return fail(ctx, FMO_ERR_ARG, "empty system or NULL input");
-  if (n_cut != 0) return fail(ctx, FMO_ERR_UNSUPPORTED, "covalent boundaries (HOP) are not supported");
+  if (n_cut < 0 || (n_cut > 0 && !bda_baa)) return fail(ctx, FMO_ERR_ARG, "cut-bond list missing");
   cudaSetDevice(ctx->device);
   const fmo_params& p = ctx->params;
   // elements present -> compact table
@@ -636,34 +677,86 @@ fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const
   ctx->g.kT = 3.166811563e-6 * p.t_el;
   if (!(ctx->g.kT > 0)) return fail(ctx, FMO_ERR_ARG, "electronic temperature must be positive");
 
-  // atoms grouped by fragment (stable)
+  // cut bonds (hybrid orbital projection): BDA and BAA in different
+  // fragments, the BDA with one s and one p shell, detached at most once
+  std::vector<int> bda_bond(n_atoms, -1);
+  for (int k = 0; k < n_cut; ++k) {
+    const int a = bda_baa[2 * k], b = bda_baa[2 * k + 1];
+    if (a < 0 || a >= n_atoms || b < 0 || b >= n_atoms)
+      return fail(ctx, FMO_ERR_ARG, "cut bond " + std::to_string(k) + ": atom index out of range");
+    if (frag_of_atom[a] == frag_of_atom[b])
+      return fail(ctx, FMO_ERR_ARG, "cut bond " + std::to_string(k) + ": both atoms in one fragment");
+    if (bda_bond[a] >= 0)
+      return fail(ctx, FMO_ERR_UNSUPPORTED, "cut bond " + std::to_string(k) + ": atom is already a BDA");
+    bda_bond[a] = k;
+    const fmo_element& e = p.el[Z[a]];
+    int n_s = 0, n_p = 0;
+    for (int sh = 0; sh < e.n_shell; ++sh) { n_s += (e.l[sh] == 0); n_p += (e.l[sh] == 1); }
+    if (n_s != 1 || n_p != 1)
+      return fail(ctx, FMO_ERR_UNSUPPORTED, "cut bond " + std::to_string(k) + ": the BDA needs one s and one p shell");
+  }
+  // internal atoms: per fragment its real atoms (input order), then the
+  // ghosts (copies of the BDA at its position) of the bonds whose BAA it holds
   ctx->n_atoms = n_atoms;
   ctx->n_frag = n_frag;
-  ctx->perm.resize(n_atoms);
-  for (int i = 0; i < n_atoms; ++i) ctx->perm[i] = i;
-  std::stable_sort(ctx->perm.begin(), ctx->perm.end(),
-                   [&](int a, int b) { return frag_of_atom[a] < frag_of_atom[b]; });
+  ctx->n_cut = n_cut;
+  ctx->n_int = n_atoms + n_cut;
+  const int n_int = ctx->n_int;
+  std::vector<std::vector<int>> real_of(n_frag), ghost_of(n_frag);
+  for (int i = 0; i < n_atoms; ++i) real_of[frag_of_atom[i]].push_back(i);
+  for (int k = 0; k < n_cut; ++k) ghost_of[frag_of_atom[bda_baa[2 * k + 1]]].push_back(k);
+  ctx->perm.clear();
+  std::vector<int> bond_of(n_int, -1), internal_of(n_atoms, -1);
+  for (int f = 0; f < n_frag; ++f) {
+    for (int a : real_of[f]) { internal_of[a] = int(ctx->perm.size()); ctx->perm.push_back(a); }
+    for (int k : ghost_of[f]) { bond_of[ctx->perm.size()] = k; ctx->perm.push_back(bda_baa[2 * k]); }
+  }
+  ctx->h_ghost_frag.assign(n_int, -1); ctx->h_ghost_src.assign(n_int, -1);
+  ctx->h_bda_baa_frag.assign(n_int, -1); ctx->h_hop_baa.assign(n_int, -1);
+  ctx->f_ghosts.assign(n_frag, {});
+  ctx->f_bda_baa_frag.assign(n_frag, {});
+  for (int i = 0; i < n_int; ++i) {
+    const int src = ctx->perm[i];
+    if (bond_of[i] >= 0) {
+      const int k = bond_of[i];
+      ctx->h_ghost_frag[i] = frag_of_atom[bda_baa[2 * k]];
+      ctx->h_ghost_src[i] = internal_of[bda_baa[2 * k]];
+      ctx->h_hop_baa[i] = internal_of[bda_baa[2 * k + 1]];
+    } else if (bda_bond[src] >= 0) {
+      const int k = bda_bond[src];
+      ctx->h_bda_baa_frag[i] = frag_of_atom[bda_baa[2 * k + 1]];
+      ctx->h_hop_baa[i] = internal_of[bda_baa[2 * k + 1]];
+      ctx->f_bda_baa_frag[frag_of_atom[src]].push_back(ctx->h_bda_baa_frag[i]);
+    }
+  }
   ctx->f_atom0.assign(n_frag, 0); ctx->f_nat.assign(n_frag, 0); ctx->f_sh0.assign(n_frag, 0);
   ctx->f_nsh.assign(n_frag, 0); ctx->f_ao0.assign(n_frag, 0); ctx->f_nao.assign(n_frag, 0);
   ctx->f_nel.assign(n_frag, 0.0);
-  ctx->h_elem.resize(n_atoms);
-  ctx->h_atom_sh0.resize(n_atoms);
+  ctx->h_elem.resize(n_int);
+  ctx->h_atom_sh0.resize(n_int);
   ctx->h_sh_atom.clear();
   ctx->h_sh_inv_eta.clear();
   int sh = 0, ao = 0;
-  std::vector<double> xyz_int(3 * (size_t)n_atoms);
-  for (int i = 0; i < n_atoms; ++i) {
+  std::vector<double> xyz_int(3 * (size_t)n_int);
+  int fprev = -1;
+  for (int i = 0; i < n_int; ++i) {
     const int src = ctx->perm[i];
-    const int f = frag_of_atom[src];
-    if (i == 0 || frag_of_atom[ctx->perm[i - 1]] != f) { ctx->f_atom0[f] = i; ctx->f_sh0[f] = sh; ctx->f_ao0[f] = ao; }
+    const bool ghost = bond_of[i] >= 0;
+    const int f = ghost ? frag_of_atom[bda_baa[2 * bond_of[i] + 1]] : frag_of_atom[src];
+    if (f != fprev) { ctx->f_atom0[f] = i; ctx->f_sh0[f] = sh; ctx->f_ao0[f] = ao; fprev = f; }
     const int e = ctx->z_to_e[Z[src]];
     ctx->h_elem[i] = e;
     ctx->h_atom_sh0[i] = sh;
     const DevElem& d = ctx->h_el[e];
-    for (int s = 0; s < d.nsh; ++s) {
+    for (int s2 = 0; s2 < d.nsh; ++s2) {
       ctx->h_sh_atom.push_back(i);
-      ctx->h_sh_inv_eta.push_back(1.0 / d.eta_sh[s]);
-      ctx->f_nel[f] += d.q0[s];
+      ctx->h_sh_inv_eta.push_back(1.0 / d.eta_sh[s2]);
+      if (!ghost) ctx->f_nel[f] += d.q0[s2];
+    }
+    if (ghost) {
+      ctx->f_nel[f] += 1.0;                                    // the ghost's electron
+      ctx->f_nel[frag_of_atom[src]] -= 1.0;                    // taken from the BDA's fragment
+      ctx->f_ghosts[f].push_back({frag_of_atom[src], d.nsh, elem_nao(d)});
     }
     ctx->f_nat[f] += 1;
     ctx->f_nsh[f] += d.nsh;
@@ -691,7 +784,13 @@ fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const
   CK(upload(ctx->d_perm, ctx->perm, st));
   CK(ctx->d_xyz_in.ensure(sizeof(double) * 3 * n_atoms));
   CK(upload(ctx->d_elem, ctx->h_elem, st));
-  CK(ctx->d_cn.ensure(sizeof(double) * n_atoms));
+  CK(ctx->d_cn.ensure(sizeof(double) * n_int));
+  if (n_cut > 0) {
+    CK(upload(ctx->d_ghost_frag, ctx->h_ghost_frag, st));
+    CK(upload(ctx->d_ghost_src, ctx->h_ghost_src, st));
+    CK(upload(ctx->d_bda_baa_frag, ctx->h_bda_baa_frag, st));
+    CK(upload(ctx->d_hop_baa, ctx->h_hop_baa, st));
+  }
   CK(upload(ctx->d_atom_sh0, ctx->h_atom_sh0, st));
   CK(upload(ctx->d_sh_atom, ctx->h_sh_atom, st));
   CK(upload(ctx->d_sh_inv_eta, ctx->h_sh_inv_eta, st));
@@ -724,7 +823,7 @@ fmo_status fmo_set_coordinates(fmo_ctx* ctx, const double* xyz) {
     if (!std::isfinite(xyz[i])) return fail(ctx, FMO_ERR_ARG, "non-finite coordinate");
   cudaStream_t st = ctx->own_stream;
   CK(h2d(ctx->d_xyz_in.p, xyz, sizeof(double) * 3 * ctx->n_atoms, st));
-  CK(launch_gather_xyz(st, ctx->n_atoms, ctx->d_perm.as<int>(), ctx->d_xyz_in.as<double>(), ctx->d_xyz.as<double>()));
+  CK(launch_gather_xyz(st, ctx->n_int, ctx->d_perm.as<int>(), ctx->d_xyz_in.as<double>(), ctx->d_xyz.as<double>()));
   CK(sync_stream(st));   // a later fmo_run may use another stream
   ctx->have_result = false;
   return FMO_OK;
@@ -736,7 +835,7 @@ fmo_status fmo_set_coordinates_device(fmo_ctx* ctx, const double* xyz_dev, void*
   if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
   cudaSetDevice(ctx->device);
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
-  CK(launch_gather_xyz(st, ctx->n_atoms, ctx->d_perm.as<int>(), xyz_dev, ctx->d_xyz.as<double>()));
+  CK(launch_gather_xyz(st, ctx->n_int, ctx->d_perm.as<int>(), xyz_dev, ctx->d_xyz.as<double>()));
   if (!cuda_stream) CK(sync_stream(st));
   ctx->have_result = false;
   return FMO_OK;
@@ -765,6 +864,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     return fail(ctx, FMO_ERR_ARG, "unknown monomer loop");
   if (o.nmer_finish != FMO_NMER_FINISH_ENERGY && o.nmer_finish != FMO_NMER_FINISH_ITERATE)
     return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
+  if (ctx->n_cut > 0 && o.precision != FMO_PREC_FP64)
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "cut bonds (hybrid orbital projection) need precision FP64");
   cudaSetDevice(ctx->device);
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
   std::memset(&ctx->stats, 0, sizeof(ctx->stats));
@@ -779,8 +880,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   sr.set("fmo_setup");
   CK(launch_stamp(st, ctx->d_t0.as<unsigned long long>()));
   // ---- coordination numbers of the whole system
-  CK(launch_cn(st, ctx->n_atoms, ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(), ctx->d_el.as<DevElem>(), ctx->g,
-               ctx->d_cn.as<double>()));
+  CK(launch_cn(st, ctx->n_int, ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(), ctx->d_el.as<DevElem>(), ctx->g,
+               ctx->d_cn.as<double>(), ctx->n_cut > 0 ? ctx->d_ghost_src.as<int>() : nullptr));
   stage(st, "cn");
   // gamma of all shell pairs, kept in HBM while it fits the budget
   {

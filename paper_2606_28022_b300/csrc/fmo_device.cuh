@@ -47,7 +47,28 @@ struct FragTab {
   const int* nsh;
   const int* ao0;     // first global AO
   const int* nao;
+  // hybrid orbital projection at cut bonds (all null without cut bonds); per
+  // internal atom:
+  const int* ghost_frag;     // ghost: fragment of its detachment atom (BDA); else -1
+  const int* ghost_src;      // ghost: internal index of its BDA; else -1
+  const int* bda_baa_frag;   // BDA: fragment of its attachment atom (BAA); else -1
+  const int* hop_baa;        // BDA or ghost: internal index of the BAA; else -1
 };
+
+constexpr int kMaxHealedShells = 32;   // ghost shells of bonds healed in one n-mer
+constexpr int kMaxProjected = 16;      // hybrid-orbital-projected atoms in one n-mer
+
+__device__ __forceinline__ bool frag_in_nmer(int nfrag, const int* frags, int f) {
+  for (int k = 0; k < nfrag; ++k)
+    if (frags[k] == f) return true;
+  return false;
+}
+
+// a ghost belongs to an n-mer unless its bond is healed there (the BDA's
+// fragment is part of the n-mer too); real atoms always do
+__device__ __forceinline__ bool atom_in_nmer(const FragTab& ft, int nfrag, const int* frags, int ga) {
+  return !ft.ghost_frag || ft.ghost_frag[ga] < 0 || !frag_in_nmer(nfrag, frags, ft.ghost_frag[ga]);
+}
 
 // One n-mer (monomer, dimer or trimer) of a pass.
 struct Nmer {
@@ -309,7 +330,12 @@ __device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol
   int round = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double dmax = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) dmax = fmax(dmax, fabs(double(A[i * lda + i])));
+    // scale of the threshold: the largest |A_ii| below 1e3 Eh (levels shifted
+    // by a hybrid-orbital projector, ~1e6 Eh, would make it meaningless)
+    for (int i = tid; i < n; i += blockDim.x) {
+      const double d = fabs(double(A[i * lda + i]));
+      if (d < 1e3) dmax = fmax(dmax, d);
+    }
     dmax = block_max(dmax, red);
     const double thr = tol * fmax(dmax, 1e-30);
     int rotations = 0;

@@ -21,7 +21,8 @@ namespace fmo {
 // cutoff are not counted).
 
 __global__ void cn_kernel(int n_atoms, const double* __restrict__ xyz, const int* __restrict__ elem,
-                          const DevElem* __restrict__ el, GParams g, double* __restrict__ cn) {
+                          const DevElem* __restrict__ el, GParams g, const int* __restrict__ ghost_src,
+                          double* __restrict__ cn) {
   // one warp per atom a, lanes over the partners b
   const int lane = threadIdx.x & 31;
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -30,8 +31,11 @@ __global__ void cn_kernel(int n_atoms, const double* __restrict__ xyz, const int
   const double ra = el[elem[a]].rcov;
   const double cut2 = g.cn_cutoff * g.cn_cutoff * (1.0 + 1e-12);   // exact test on r below
   double s = 0.0;
+  // a ghost (a copy of a bond-detachment atom at its position) gets that
+  // atom's CN: ghosts are never partners, and its BDA is skipped like itself
+  const int self2 = ghost_src ? ghost_src[a] : -1;
   for (int b = lane; b < n_atoms; b += 32) {
-    if (b == a) continue;
+    if (b == a || b == self2 || (ghost_src && ghost_src[b] >= 0)) continue;
     const double dx = xyz[3 * b] - xa, dy = xyz[3 * b + 1] - ya, dz = xyz[3 * b + 2] - za;
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= cut2) continue;
@@ -61,6 +65,7 @@ __device__ void build_maps(const Nmer& nm, const FragTab ft, const int* __restri
       const int a0 = ft.atom0[f], na = ft.nat[f];
       for (int i = 0; i < na; ++i) {
         const int ga = a0 + i;
+        if (!atom_in_nmer(ft, nm.nfrag, nm.frag, ga)) continue;   // ghost of a healed bond
         mp.at_glob[la] = ga;
         const DevElem& e = el[elem[ga]];
         for (int s = 0; s < e.nsh; ++s) {
@@ -112,6 +117,7 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
       s_foff[k] = lao;
       for (int i = 0; i < ft.nat[f]; ++i) {
         const int ga = ft.atom0[f] + i;
+        if (!atom_in_nmer(ft, nm.nfrag, nm.frag, ga)) continue;   // ghost of a healed bond
         s_glob[la] = ga;
         s_ao0[la] = lao;
         s_fk[la] = (unsigned char)k;
@@ -236,6 +242,76 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
   }
 }
 
+// Hybrid orbital projection of an n-mer's cut-bond atoms (HOP section):
+// V^HOP = sum over projected atoms A of S[:, A] D_A S[A, :] with
+// D = V h h^T on a bond-detachment atom (BDA) whose attachment atom (BAA) is
+// outside the n-mer, D = V (1_sp - h h^T) on a ghost, h = c_s s + c_p (b . p)
+// (c_s = 1/2, c_p = sqrt(3)/2), b the unit vector from the BDA to the BAA.
+// One block per n-mer; local AOs in the order of build_maps.
+__global__ void hop_projector_kernel(const Nmer* __restrict__ nmers, FragTab ft, const double* __restrict__ xyz,
+                                     const int* __restrict__ elem, const DevElem* __restrict__ el, double v_hop,
+                                     const double* __restrict__ S, double* __restrict__ V) {
+  const Nmer nm = nmers[blockIdx.x];
+  __shared__ int s_np;
+  __shared__ int s_idx[kMaxProjected][4];
+  __shared__ double s_D[kMaxProjected][16];
+  if (threadIdx.x == 0) {
+    int np = 0, lao = 0;
+    for (int kf = 0; kf < nm.nfrag; ++kf) {
+      const int f = nm.frag[kf];
+      for (int i = 0; i < ft.nat[f]; ++i) {
+        const int ga = ft.atom0[f] + i;
+        if (!atom_in_nmer(ft, nm.nfrag, nm.frag, ga)) continue;
+        const DevElem& e = el[elem[ga]];
+        int kind = 0;   // 1: detached BDA, 2: ghost
+        if (ft.ghost_frag[ga] >= 0) kind = 2;
+        else if (ft.bda_baa_frag[ga] >= 0 && !frag_in_nmer(nm.nfrag, nm.frag, ft.bda_baa_frag[ga])) kind = 1;
+        if (kind && np < kMaxProjected) {
+          int ao = lao, is = -1, ip = -1;
+          for (int k = 0; k < e.nsh; ++k) {
+            if (e.l[k] == 0 && is < 0) is = ao;
+            if (e.l[k] == 1 && ip < 0) ip = ao;
+            ao += 2 * e.l[k] + 1;
+          }
+          const int baa = ft.hop_baa[ga];
+          double b[3] = {xyz[3 * baa] - xyz[3 * ga], xyz[3 * baa + 1] - xyz[3 * ga + 1],
+                         xyz[3 * baa + 2] - xyz[3 * ga + 2]};
+          const double inv = 1.0 / sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+          const double cp = 0.5 * sqrt(3.0);
+          const double h[4] = {0.5, cp * b[0] * inv, cp * b[1] * inv, cp * b[2] * inv};
+          for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 4; ++c)
+              s_D[np][4 * a + c] = v_hop * (kind == 1 ? h[a] * h[c] : (a == c ? 1.0 : 0.0) - h[a] * h[c]);
+          s_idx[np][0] = is;
+          s_idx[np][1] = ip;
+          s_idx[np][2] = ip + 1;
+          s_idx[np][3] = ip + 2;
+          ++np;
+        }
+        for (int k = 0; k < e.nsh; ++k) lao += 2 * e.l[k] + 1;
+      }
+    }
+    s_np = np;
+  }
+  __syncthreads();
+  const int n = nm.n, np = s_np;
+  const double* Sm = S + nm.mat;
+  double* Vm = V + nm.mat;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    double v = 0.0;
+    for (int k = 0; k < np; ++k) {
+      for (int a = 0; a < 4; ++a) {
+        const double si = Sm[(long long)i * n + s_idx[k][a]];
+        double t = 0.0;
+        for (int c = 0; c < 4; ++c) t += s_D[k][4 * a + c] * Sm[(long long)s_idx[k][c] * n + j];
+        v += si * t;
+      }
+    }
+    Vm[e] = v;
+  }
+}
+
 // x^(-1/2) in FP64 from the FP32 hardware estimate y0 and one third-order
 // correction: with r = 1 - x y0^2 (|r| ~ 1e-7; y0^2 is exact in FP64),
 // y = y0 (1 + r/2 + 3r^2/8) has relative error O(r^3), below FP64 rounding.
@@ -264,7 +340,8 @@ __global__ void gamma_kernel(const Nmer* __restrict__ nmers, FragTab ft, const d
     int ls = 0;
     for (int k = 0; k < nm.nfrag; ++k) {
       const int f = nm.frag[k];
-      for (int i = 0; i < ft.nsh[f]; ++i) s_sh[ls++] = ft.sh0[f] + i;
+      for (int i = 0; i < ft.nsh[f]; ++i)
+        if (atom_in_nmer(ft, nm.nfrag, nm.frag, sh_atom[ft.sh0[f] + i])) s_sh[ls++] = ft.sh0[f] + i;
     }
   }
   __syncthreads();
@@ -377,6 +454,7 @@ struct SccArgs {
   float* W2f;
   float* Agf;
   const double* phi;       // supersystem potential sum_lambda gamma dq_mono (or null)
+  const double* vhop;      // per-n-mer hybrid orbital projector V^HOP (n x n, or null)
   const double* dq_mono;   // monomer charges, global shell order
   double* esp;             // out: the n-mer's embedding potential
   double* dq;              // in: guess (if !guess_from_mono), out: charges
@@ -462,6 +540,13 @@ __host__ __device__ inline size_t scc_smem_bytes(int max_n, int max_nsh, int max
   b += 3 * align16(sizeof(int) * npad);                // js p q act
   b += 2 * align16(sizeof(double) * npad);             // js c s
   return b;
+}
+
+// gamma between shell k_b of atom b and a shell (1/eta = ie_a) of atom a
+__device__ __forceinline__ double shell_gamma(const SccArgs& ar, int a, double ie_a, int b, int k_b) {
+  const double dx = ar.xyz[3 * a] - ar.xyz[3 * b], dy = ar.xyz[3 * a + 1] - ar.xyz[3 * b + 1],
+               dz = ar.xyz[3 * a + 2] - ar.xyz[3 * b + 2];
+  return gamma_fn(dx * dx + dy * dy + dz * dz, ie_a, 1.0 / ar.el[ar.elem[b]].eta_sh[k_b], ar.g.k_g);
 }
 
 __device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, int max_nat, int a_bytes) {
@@ -856,12 +941,18 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   // Fock matrix F = H0 + 1/2 S (sig_mu + sig_nu), into W1 (a warp per row)
   {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* Vm = ar.vhop ? ar.vhop + nm.mat : nullptr;   // hybrid orbital projectors, if any
     for (int i = wid; i < n; i += nw) {
       const double si = sm.sig[sm.mp.ao_sh[i]];
       const double* hr = Hm + (long long)i * n;
       const double* sr = Sm + (long long)i * n;
       T* fr = pp.W1 + (long long)i * n;
-      for (int j = lane; j < n; j += 32) fr[j] = T(hr[j] + 0.5 * sr[j] * (si + sm.sig[sm.mp.ao_sh[j]]));
+      if (Vm) {
+        const double* vr = Vm + (long long)i * n;
+        for (int j = lane; j < n; j += 32) fr[j] = T(hr[j] + 0.5 * sr[j] * (si + sm.sig[sm.mp.ao_sh[j]]) + vr[j]);
+      } else {
+        for (int j = lane; j < n; j += 32) fr[j] = T(hr[j] + 0.5 * sr[j] * (si + sm.sig[sm.mp.ao_sh[j]]));
+      }
     }
   }
   // zero the padding row/column of A
@@ -1115,12 +1206,45 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   SccSmem sm = carve_scc_smem(smem_raw, ar.max_n, ar.max_nsh, ar.max_nat, a_bytes);
   const long long t_start = clock64();
   build_maps(nm, ar.ft, ar.elem, ar.atom_sh0, ar.el, sm.mp);
+  // ghosts of cut bonds healed in this n-mer (hybrid orbital projection):
+  // not in its basis, but their monomer charges leave its embedding potential
+  // and enter dE^V as the charge transfer -dq_mono
+  __shared__ int s_hg_sh[kMaxHealedShells], s_hg_at[kMaxHealedShells], s_hg_k[kMaxHealedShells];
+  __shared__ int s_nhg;
+  if (threadIdx.x == 0) {
+    int c = 0;
+    if (ar.ft.ghost_frag) {
+      for (int kf = 0; kf < nm.nfrag; ++kf) {
+        const int f = nm.frag[kf];
+        for (int i = 0; i < ar.ft.nat[f]; ++i) {
+          const int ga = ar.ft.atom0[f] + i;
+          if (atom_in_nmer(ar.ft, nm.nfrag, nm.frag, ga)) continue;
+          const DevElem& e = ar.el[ar.elem[ga]];
+          for (int k = 0; k < e.nsh && c < kMaxHealedShells; ++k, ++c) {
+            s_hg_sh[c] = ar.atom_sh0[ga] + k;
+            s_hg_at[c] = ga;
+            s_hg_k[c] = k;
+          }
+        }
+      }
+    }
+    s_nhg = c;
+  }
   // per-shell / per-atom constants
   for (int s = threadIdx.x; s < nsh; s += blockDim.x) {
     const int ga = sm.mp.at_glob[sm.mp.sh_at[s]];
     const DevElem& e = ar.el[ar.elem[ga]];
     const int k = sm.mp.sh_glob[s] - ar.atom_sh0[ga];
-    sm.q0[s] = e.q0[k];
+    double q = e.q0[k];
+    if (ar.ft.ghost_frag && ar.ft.ghost_frag[ga] >= 0) {
+      q = (e.l[k] == 0) ? 0.25 : 0.75;          // ghost: one electron, c_s^2 and c_p^2 of the hybrid
+    } else if (ar.ft.bda_baa_frag && ar.ft.bda_baa_frag[ga] >= 0 &&
+               !frag_in_nmer(nm.nfrag, nm.frag, ar.ft.bda_baa_frag[ga])) {
+      double tot = 0.0;                         // detached BDA: one electron less, shared
+      for (int kk = 0; kk < e.nsh; ++kk) tot += e.q0[kk];   // in proportion to q0
+      q *= (tot - 1.0) / tot;
+    }
+    sm.q0[s] = q;
   }
   for (int a = threadIdx.x; a < nat; a += blockDim.x) sm.g3[a] = ar.el[ar.elem[sm.mp.at_glob[a]]].gamma3;
   __syncthreads();
@@ -1130,6 +1254,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     const int i = e / nat, j = e % nat;
     if (j >= i) continue;
     const int ga = sm.mp.at_glob[i], gb = sm.mp.at_glob[j];
+    if (ar.ft.ghost_frag && (ar.ft.ghost_frag[ga] >= 0 || ar.ft.ghost_frag[gb] >= 0)) continue;   // ghosts: none
     const DevElem& EA = ar.el[ar.elem[ga]];
     const DevElem& EB = ar.el[ar.elem[gb]];
     const double dx = ar.xyz[3 * ga] - ar.xyz[3 * gb], dy = ar.xyz[3 * ga + 1] - ar.xyz[3 * gb + 1],
@@ -1146,6 +1271,12 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       double v = 0.0;
       if (ar.phi) {
         for (int t = lane; t < nsh; t += 32) v += G[(size_t)s * nsh + t] * ar.dq_mono[sm.mp.sh_glob[t]];
+        if (s_nhg > 0) {
+          const int ga = sm.mp.at_glob[sm.mp.sh_at[s]];
+          const double ie = 1.0 / ar.el[ar.elem[ga]].eta_sh[sm.mp.sh_glob[s] - ar.atom_sh0[ga]];
+          for (int t = lane; t < s_nhg; t += 32)
+            v += shell_gamma(ar, ga, ie, s_hg_at[t], s_hg_k[t]) * ar.dq_mono[s_hg_sh[t]];
+        }
         v = warp_sum(v);
         v = ar.phi[sm.mp.sh_glob[s]] - v;
       }
@@ -1322,6 +1453,24 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     ar.dq[nm.shv + s] = sm.dqout[s];
     if (ar.phi) dev += (sm.dqout[s] - ar.dq_mono[sm.mp.sh_glob[s]]) * sm.esp[s];   // Eq. 13
   }
+  if (ar.phi && s_nhg > 0) {
+    // healed ghost shells: charge transfer -dq_mono in the ESP of the n-mer's
+    // environment, phi_g - sum over all monomer shells of the n-mer's fragments
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int h = wid; h < s_nhg; h += nw) {
+      const int gat = s_hg_at[h];
+      const double ie = 1.0 / ar.el[ar.elem[gat]].eta_sh[s_hg_k[h]];
+      double v = 0.0;
+      for (int t = lane; t < nsh; t += 32) {
+        const int tat = sm.mp.at_glob[sm.mp.sh_at[t]];
+        v += shell_gamma(ar, gat, ie, tat, sm.mp.sh_glob[t] - ar.atom_sh0[tat]) * ar.dq_mono[sm.mp.sh_glob[t]];
+      }
+      for (int t = lane; t < s_nhg; t += 32)
+        v += shell_gamma(ar, gat, ie, s_hg_at[t], s_hg_k[t]) * ar.dq_mono[s_hg_sh[t]];
+      v = warp_sum(v);
+      if (lane == 0) dev += -ar.dq_mono[s_hg_sh[h]] * (ar.phi[s_hg_sh[h]] - v);
+    }
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) ar.eps[nm.aov + i] = sm.eps[i];
   dev = block_sum(dev, sm.red);
   if (ar.trace && threadIdx.x == 0) {
@@ -1494,6 +1643,7 @@ __global__ void pair_distance_kernel(int n_frag, FragTab ft, const double* __res
     double best = 1e300;
     for (int k = lane; k < na * nb; k += 32) {
       const int a = a0 + k / nb, b = b0 + k % nb;
+      if (ft.ghost_frag && (ft.ghost_frag[a] >= 0 || ft.ghost_frag[b] >= 0)) continue;   // ghosts are not atoms
       const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
                    dz = xyz[3 * a + 2] - xyz[3 * b + 2];
       best = fmin(best, dx * dx + dy * dy + dz * dz);
@@ -1751,8 +1901,8 @@ long long launch_count() { return g_launches.load(); }
   } while (0)
 
 cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int* elem, const DevElem* el,
-                      GParams g, double* cn) {
-  cn_kernel<<<(int)(((long long)n_atoms * 32 + 255) / 256), 256, 0, st>>>(n_atoms, xyz, elem, el, g, cn);
+                      GParams g, double* cn, const int* ghost_src) {
+  cn_kernel<<<(int)(((long long)n_atoms * 32 + 255) / 256), 256, 0, st>>>(n_atoms, xyz, elem, el, g, ghost_src, cn);
   LAUNCH_CHECK();
   return cudaSuccess;
 }
@@ -1824,7 +1974,7 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.atom_sh0 = L.atom_sh0; ar.el = L.el; ar.g = L.g; ar.S = L.S; ar.H0 = L.H0; ar.gam = L.gam;
   ar.CTd = L.CTd; ar.W1d = L.W1d; ar.W2d = L.W2d; ar.Agd = L.Agd;
   ar.CTf = L.CTf; ar.W1f = L.W1f; ar.W2f = L.W2f; ar.Agf = L.Agf;
-  ar.phi = L.phi; ar.dq_mono = L.dq_mono; ar.esp = L.esp; ar.dq = L.dq; ar.eps = L.eps; ar.hist = L.hist;
+  ar.phi = L.phi; ar.vhop = L.vhop; ar.dq_mono = L.dq_mono; ar.esp = L.esp; ar.dq = L.dq; ar.eps = L.eps; ar.hist = L.hist;
   ar.energy = L.energy; ar.e_el = L.e_el; ar.e_rep = L.e_rep; ar.dEV = L.dEV; ar.iters = L.iters; ar.iters32 = L.iters32;
   ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
@@ -1885,6 +2035,14 @@ cudaError_t launch_gamma_full(cudaStream_t st, int n_sh, const double* xyz, cons
 cudaError_t launch_phi_gemv(cudaStream_t st, int n_sh, const double* gam, const double* dq, double* phi) {
   if (n_sh == 0) return cudaSuccess;
   phi_gemv_kernel<<<(int)(((long long)n_sh * 32 + 255) / 256), 256, 0, st>>>(n_sh, gam, dq, phi);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_hop_projector(cudaStream_t st, int n_nmer, const Nmer* nmers, FragTab ft, const double* xyz,
+                                 const int* elem, const DevElem* el, double v_hop, const double* S, double* V) {
+  if (n_nmer == 0) return cudaSuccess;
+  hop_projector_kernel<<<n_nmer, 256, 0, st>>>(nmers, ft, xyz, elem, el, v_hop, S, V);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

@@ -48,6 +48,7 @@ struct SccLaunch {
   float* W2f;
   float* Agf;
   const double* phi;
+  const double* vhop;   // per-n-mer hybrid orbital projectors (null without cut bonds)
   const double* dq_mono;
   double* esp;
   double* dq;
@@ -85,7 +86,7 @@ struct SccLaunch {
 };
 
 cudaError_t launch_cn(cudaStream_t st, int n_atoms, const double* xyz, const int* elem, const DevElem* el,
-                      GParams g, double* cn);
+                      GParams g, double* cn, const int* ghost_src = nullptr);
 cudaError_t launch_integrals(cudaStream_t st, int n_nmer, int max_pairs, const Nmer* nmers, FragTab ft,
                              const double* xyz, const int* elem, const int* atom_sh0, const double* cn,
                              const DevElem* el, const double* kab, int ne, GParams g, double* S, double* H0,
@@ -106,6 +107,8 @@ cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* 
 cudaError_t launch_gamma_full(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom,
                               const double* sh_inv_eta, GParams g, double* gam);
 cudaError_t launch_phi_gemv(cudaStream_t st, int n_sh, const double* gam, const double* dq, double* phi);
+cudaError_t launch_hop_projector(cudaStream_t st, int n_nmer, const Nmer* nmers, FragTab ft, const double* xyz,
+                                 const int* elem, const DevElem* el, double v_hop, const double* S, double* V);
 cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);
 cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, const double* bounds,
                                  double cut, double* rmin);

@@ -273,7 +273,7 @@ def separated(system: System, distance_A: float) -> System:
 # alpha-helical polyalanine with covalent fragment boundaries (C3 stand-in)
 
 
-def _place(a, b, c, r, theta_deg, chi_deg):
+def _nerf(a, b, c, r, theta_deg, chi_deg):
     """Position of atom d bonded to c with |cd| = r, angle b-c-d = theta and
     dihedral a-b-c-d = chi (internal coordinates to Cartesian)."""
     bc = (c - b) / np.linalg.norm(c - b)
@@ -309,34 +309,34 @@ def polyalanine_helix(n_res: int, phi=-57.0, psi=-47.0, omega=180.0, seed: int |
     # backbone N, CA, C of every residue
     N = [np.array([0.0, 0.0, 0.0])]
     CA = [np.array([1.458, 0.0, 0.0])]
-    C = [_place(np.array([0.0, 1.0, 0.0]), N[0], CA[0], 1.525, 111.2, 0.0)]
+    C = [_nerf(np.array([0.0, 1.0, 0.0]), N[0], CA[0], 1.525, 111.2, 0.0)]
     for i in range(1, n_res):
-        N.append(_place(N[i - 1], CA[i - 1], C[i - 1], 1.329, 116.2, psi))
-        CA.append(_place(CA[i - 1], C[i - 1], N[i], 1.458, 121.7, omega))
-        C.append(_place(C[i - 1], N[i], CA[i], 1.525, 111.2, phi))
+        N.append(_nerf(N[i - 1], CA[i - 1], C[i - 1], 1.329, 116.2, psi))
+        CA.append(_nerf(CA[i - 1], C[i - 1], N[i], 1.458, 121.7, omega))
+        C.append(_nerf(C[i - 1], N[i], CA[i], 1.525, 111.2, phi))
     ca_idx, c_idx = [], []
     for i in range(n_res):
         if i > 0:   # the previous residue's carbonyl belongs to this unit
             c_idx.append(add(6, C[i - 1], i))
-            add(8, _place(N[i - 1], CA[i - 1], C[i - 1], 1.231, 120.5, psi + 180.0), i)
-            add(1, _place(CA[i - 1], C[i - 1], N[i], 1.01, 119.5, 0.0), i)            # H on N
+            add(8, _nerf(N[i - 1], CA[i - 1], C[i - 1], 1.231, 120.5, psi + 180.0), i)
+            add(1, _nerf(CA[i - 1], C[i - 1], N[i], 1.01, 119.5, 0.0), i)            # H on N
         else:
-            add(1, _place(C[0], CA[0], N[0], 1.01, 109.5, 60.0), 0)                  # N-terminal H
-            add(1, _place(C[0], CA[0], N[0], 1.01, 109.5, -60.0), 0)
+            add(1, _nerf(C[0], CA[0], N[0], 1.01, 109.5, 60.0), 0)                  # N-terminal H
+            add(1, _nerf(C[0], CA[0], N[0], 1.01, 109.5, -60.0), 0)
         add(7, N[i], i)
         ca_idx.append(add(6, CA[i], i))
-        ref = C[i - 1] if i > 0 else _place(C[0], CA[0], N[0], 1.0, 109.5, 180.0)
-        cb = _place(ref, N[i], CA[i], 1.53, 110.5, phi - 120.0 if i > 0 else 180.0 - 120.0)
+        ref = C[i - 1] if i > 0 else _nerf(C[0], CA[0], N[0], 1.0, 109.5, 180.0)
+        cb = _nerf(ref, N[i], CA[i], 1.53, 110.5, phi - 120.0 if i > 0 else 180.0 - 120.0)
         add(6, cb, i)
-        add(1, _place(ref, N[i], CA[i], 1.09, 109.5, phi + 120.0 if i > 0 else 180.0 + 120.0), i)   # HA
+        add(1, _nerf(ref, N[i], CA[i], 1.09, 109.5, phi + 120.0 if i > 0 else 180.0 + 120.0), i)   # HA
         for chi in (60.0, 180.0, 300.0):
-            add(1, _place(N[i], CA[i], cb, 1.09, 109.5, chi), i)
+            add(1, _nerf(N[i], CA[i], cb, 1.09, 109.5, chi), i)
     last = n_res - 1
     c_idx.append(add(6, C[last], last))
-    add(8, _place(N[last], CA[last], C[last], 1.231, 120.5, psi + 180.0), last)
-    ot = _place(N[last], CA[last], C[last], 1.34, 116.2, psi)
+    add(8, _nerf(N[last], CA[last], C[last], 1.231, 120.5, psi + 180.0), last)
+    ot = _nerf(N[last], CA[last], C[last], 1.34, 116.2, psi)
     add(8, ot, last)
-    add(1, _place(CA[last], C[last], ot, 0.97, 107.0, 180.0), last)
+    add(1, _nerf(CA[last], C[last], ot, 0.97, 107.0, 180.0), last)
     # fragments of 1-3 consecutive residues
     frag_of_res, f, i = [], 0, 0
     while i < n_res:

@@ -175,3 +175,30 @@ def test_pentacene4_fmo3_fp64_and_mixed(gpu, params, pentacene4):
     e1, e2, e3 = g.energies()
     assert abs(e3 - ref.e_fmo3) < E_TOT_MIXED
     assert abs(e2 - ref.e_fmo2) < E_TOT_MIXED
+
+
+@pytest.fixture(scope="module")
+def ala5():
+    # five residues of an alpha-helical polyalanine in fragments of 1-3
+    # residues, cut at CA-C(O) with hybrid orbital projection
+    return G.polyalanine_helix(5, seed=3)
+
+
+def test_polyalanine_hop_fmo2_fp64(gpu, params, ala5):
+    assert len(ala5.cut_bonds) >= 2
+    ref = ofmo.fmo(ala5, params, ofmo.FMOOptions(all_dimers_scc=True))
+    compare(run_gpu(gpu, ala5, all_dimers_scc=1), ref)
+
+
+def test_polyalanine_hop_fmo3_of_three_fragments_equals_full_scc(gpu, params):
+    s = G.polyalanine_helix(3)
+    full = xtb.single_point(s, params)
+    g = run_gpu(gpu, s, level=3, all_dimers_scc=1, trimer_cut=1e9)
+    assert abs(g.energies()[2] - full.energy) < E_TOT
+
+
+def test_hop_needs_fp64(gpu, params):
+    from paper_2606_28022_b300 import fmo
+    gpu.set_system(G.polyalanine_helix(3))
+    with pytest.raises(fmo.FMOError):
+        gpu.run(fmo.options(precision="mixed"))
