@@ -109,7 +109,9 @@ typedef struct fmo_options {
   int32_t all_dimers_scc;   /* 1: every pair gets an SCC dimer (no ES-DIM) */
   int32_t max_iter;         /* SCC iterations per n-mer solve */
   int32_t max_outer;        /* monomer ESP iterations */
-  int32_t guess;            /* 0 neutral charges, 2 user charges (fmo_set_guess) */
+  int32_t guess;            /* 0 neutral charges, 1 learned model (fmo_mlp_*;
+                               restarts from 0 if the monomer loop does not
+                               converge), 2 user charges (fmo_set_guess) */
   int32_t schedule;         /* 0 autotuned block size, 1 fixed block size */
   int32_t monomer_loop;     /* FMO_LOOP_GLOBAL (default): one SCC iteration of
                                every monomer per outer step, then one Broyden
@@ -201,6 +203,46 @@ fmo_status fmo_set_coordinates_device(fmo_ctx *ctx, const double *xyz_dev, void 
 /* User initial monomer shell charges (options.guess = 2), n_shell values in
  * the output order of fmo_get_monomers. */
 fmo_status fmo_set_guess(fmo_ctx *ctx, const double *shell_dq);
+
+/*
+ * Learned initial monomer charges (options.guess = 1).  The paper has no
+ * learned guess; this model is specific to this library: per-atom radial and
+ * angular descriptors within 6 A (32 + 40), the embedding potential of the
+ * other fragments' charges, the element one-hot (H, C, N, O), a 77-128-128-2
+ * SiLU network with FP16 weights and FP32 accumulation whose two outputs are
+ * the atom's two shell charges, shifted per fragment to minus its charge.
+ * Prediction takes two passes: zero potential, then the potential of the
+ * first pass's charges.  Every atom must have two shells, k_g = 2, no cut
+ * bonds; otherwise FMO_ERR_UNSUPPORTED.
+ *
+ * Weights: FMO_MLP_N_WEIGHTS floats: W1 (128 x 77), b1, W2 (128 x 128), b2,
+ * W3 (2 x 128), b3 (all row-major), then the feature mean and scale (77 each;
+ * features are standardised as (x - mean) * scale).
+ */
+#define FMO_MLP_N_WEIGHTS 26908
+/* Random initial weights (seeded), mean 0 / scale 1. */
+fmo_status fmo_mlp_init(fmo_ctx *ctx, uint64_t seed);
+/* Copy n = FMO_MLP_N_WEIGHTS host floats in; the Adam state is cleared. */
+fmo_status fmo_mlp_set_weights(fmo_ctx *ctx, const float *w, int64_t n);
+/* *n = FMO_MLP_N_WEIGHTS; with w non-NULL the weights are copied out. */
+fmo_status fmo_mlp_get_weights(fmo_ctx *ctx, float *w, int64_t *n);
+/* Two-pass prediction for the current coordinates: n_shell values in the
+ * output order of fmo_get_monomers. */
+fmo_status fmo_mlp_predict(fmo_ctx *ctx, double *shell_dq);
+/*
+ * Train on the GPU against converged monomer charges of the current system
+ * (same atoms, fragments and charges) at n_frames geometries:
+ *   xyz_frames  [n_frames][n_atoms][3] bohr, input atom order
+ *   shell_dq    [n_frames][n_shell], the order of fmo_get_monomers
+ * The feature mean and scale are set from the frames, then `epochs` passes
+ * of Adam (learning rate lr) over shuffled batches of batch_frames frames
+ * minimise the mean squared error of the two-pass prediction (the potential
+ * feature from the current model's first pass, held fixed in the gradient).
+ * loss_per_epoch (optional, [epochs]) receives the mean loss of each epoch.
+ * Device memory: about 2 GB per 1000 frames of 3000 atoms.
+ */
+fmo_status fmo_mlp_train(fmo_ctx *ctx, int32_t n_frames, const double *xyz_frames, const double *shell_dq,
+                         int32_t epochs, int32_t batch_frames, double lr, uint64_t seed, double *loss_per_epoch);
 
 /*
  * Run the FMO calculation (Sec. 2.3): coordination numbers of the whole

@@ -4,6 +4,7 @@
 // the frozen ESP, then the FMO sums).  Every arithmetic step of the method
 // runs in the kernels of kernels.cu.
 #include <algorithm>
+#include <random>
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -14,6 +15,7 @@
 
 #include "../../include/fmo_xtb.h"
 #include "kernels.h"
+#include "mlp.h"
 #include <nvtx3/nvToolsExt.h>
 
 using namespace fmo;
@@ -114,10 +116,17 @@ struct fmo_ctx {
   std::vector<std::vector<GhostInfo>> f_ghosts;   // per hosting fragment
   std::vector<std::vector<int>> f_bda_baa_frag;   // per fragment: BAA fragment of each of its BDAs
   DevBuf d_ghost_frag, d_ghost_src, d_bda_baa_frag, d_hop_baa;
+  // learned initial charges: weights (FP32 master + feature mean/scale, FP16
+  // copy), Adam moments, per-system tables and inference buffers
+  bool mlp_ready = false, mlp_tables_ok = false;
+  DevBuf d_mlp_W, d_mlp_W16, d_mlp_m, d_mlp_v;
+  DevBuf d_mlp_elem4, d_mlp_atom_frag, d_mlp_atom_ie, d_mlp_sh_ie, d_mlp_fcharge, d_mlp_err;
+  DevBuf d_mlp_X, d_mlp_y, d_mlp_q;
   std::vector<int> perm;                  // internal atom i <- input atom perm[i]
   std::vector<int> h_elem, h_atom_sh0, h_sh_atom;
   std::vector<int> f_atom0, f_nat, f_sh0, f_nsh, f_ao0, f_nao;
   std::vector<double> f_nel, h_sh_inv_eta;
+  std::vector<int> f_charge;
   DevBuf d_xyz, d_xyz_in, d_perm, d_elem, d_cn, d_atom_sh0, d_sh_atom, d_sh_inv_eta;
   DevBuf d_f_atom0, d_f_nat, d_f_sh0, d_f_nsh, d_f_ao0, d_f_nao;
   DevBuf d_gam_full;                      // gamma of all shell pairs (when it fits)
@@ -543,6 +552,72 @@ double now_ms(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
+// Per-system tables of the learned-guess model: element index (H, C, N, O),
+// fragment and 1/eta of the first shell of every atom, 1/eta of every shell,
+// fragment charges.  The model takes two shells per atom and k_g = 2.
+fmo_status mlp_tables(fmo_ctx* ctx) {
+  if (ctx->mlp_tables_ok) return FMO_OK;
+  if (ctx->n_cut > 0) return fail(ctx, FMO_ERR_UNSUPPORTED, "the learned guess takes no cut bonds");
+  if (ctx->g.k_g != 2.0) return fail(ctx, FMO_ERR_UNSUPPORTED, "the learned guess needs k_g = 2");
+  static const int kZ[4] = {1, 6, 7, 8};
+  std::vector<int> e4(ctx->n_int), afrag(ctx->n_int);
+  std::vector<float> aie(ctx->n_int), shie(ctx->h_sh_inv_eta.begin(), ctx->h_sh_inv_eta.end());
+  std::vector<int> ez(ctx->ne, -1);
+  for (int z = 0; z < FMO_MAX_Z; ++z)
+    if (ctx->z_to_e[z] >= 0)
+      for (int k = 0; k < 4; ++k)
+        if (kZ[k] == z) ez[ctx->z_to_e[z]] = k;
+  for (int f = 0; f < ctx->n_frag; ++f)
+    for (int i = ctx->f_atom0[f]; i < ctx->f_atom0[f] + ctx->f_nat[f]; ++i) {
+      const int e = ctx->h_elem[i];
+      if (ez[e] < 0) return fail(ctx, FMO_ERR_UNSUPPORTED, "the learned guess covers H, C, N and O only");
+      if (ctx->h_el[e].nsh != 2) return fail(ctx, FMO_ERR_UNSUPPORTED, "the learned guess needs two shells per atom");
+      e4[i] = ez[e];
+      afrag[i] = f;
+      aie[i] = float(1.0 / ctx->h_el[e].eta_sh[0]);
+    }
+  cudaStream_t st = ctx->own_stream;
+  CK(upload(ctx->d_mlp_elem4, e4, st));
+  CK(upload(ctx->d_mlp_atom_frag, afrag, st));
+  CK(upload(ctx->d_mlp_atom_ie, aie, st));
+  CK(upload(ctx->d_mlp_sh_ie, shie, st));
+  CK(upload(ctx->d_mlp_fcharge, ctx->f_charge, st));
+  CK(ctx->d_mlp_err.ensure(sizeof(int)));
+  CK(sync_stream(st));
+  ctx->mlp_tables_ok = true;
+  return FMO_OK;
+}
+
+// Two-pass prediction (pass 0 with ESP = 0, pass 1 with the ESP of the pass-0
+// charges) for the current coordinates into out (double, internal shell order).
+fmo_status mlp_predict_device(fmo_ctx* ctx, cudaStream_t st, double* out) {
+  fmo_status fs = mlp_tables(ctx);
+  if (fs != FMO_OK) return fs;
+  const int n = ctx->n_int;
+  CK(ctx->d_mlp_X.ensure(sizeof(float) * (size_t)n * kMlpStride));
+  CK(ctx->d_mlp_y.ensure(sizeof(float) * 2 * (size_t)n));
+  CK(ctx->d_mlp_q.ensure(sizeof(float) * 2 * (size_t)n));
+  CK(cudaMemsetAsync(ctx->d_mlp_err.p, 0, sizeof(int), st));
+  const float* W = ctx->d_mlp_W.as<float>();
+  const __half* W16 = ctx->d_mlp_W16.as<__half>();
+  const MlpCache none{nullptr, nullptr, nullptr, nullptr, nullptr};
+  CK(mlp_descriptors(st, 1, n, ctx->d_xyz.as<double>(), ctx->d_mlp_elem4.as<int>(), ctx->d_mlp_X.as<float>(),
+                     ctx->d_mlp_err.as<int>()));
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1)
+      CK(mlp_esp(st, 1, n, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_mlp_atom_frag.as<int>(),
+                 ctx->d_mlp_atom_ie.as<float>(), ctx->d_sh_atom.as<int>(), ctx->d_mlp_sh_ie.as<float>(),
+                 ctx->d_mlp_q.as<float>(), ctx->d_mlp_X.as<float>()));
+    CK(mlp_forward(st, n, ctx->d_mlp_X.as<float>(), W16, W + kMlpOffMean, W + kMlpOffScale, ctx->d_mlp_y.as<float>(),
+                   none));
+    CK(mlp_project(st, 1, ctx->n_frag, n, ctx->d_f_atom0.as<int>(), ctx->d_f_nat.as<int>(),
+                   ctx->d_mlp_fcharge.as<int>(), ctx->d_mlp_y.as<float>(), ctx->d_mlp_q.as<float>(), nullptr, 0.0,
+                   nullptr, nullptr));
+  }
+  CK(mlp_to_double(st, 2 * n, ctx->d_mlp_q.as<float>(), out));
+  return FMO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -601,7 +676,9 @@ void fmo_destroy(fmo_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (DevBuf* b : {&ctx->d_el, &ctx->d_kab, &ctx->d_prim, &ctx->d_xyz, &ctx->d_xyz_in, &ctx->d_perm, &ctx->d_elem, &ctx->d_cn,
                     &ctx->d_atom_sh0, &ctx->d_sh_atom, &ctx->d_sh_inv_eta, &ctx->d_f_atom0, &ctx->d_f_nat,
-                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_gam_full, &ctx->d_ghost_frag, &ctx->d_ghost_src, &ctx->d_bda_baa_frag, &ctx->d_hop_baa, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
+                    &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_gam_full, &ctx->d_mlp_W, &ctx->d_mlp_W16, &ctx->d_mlp_m, &ctx->d_mlp_v,
+                    &ctx->d_mlp_elem4, &ctx->d_mlp_atom_frag, &ctx->d_mlp_atom_ie, &ctx->d_mlp_sh_ie,
+                    &ctx->d_mlp_fcharge, &ctx->d_mlp_err, &ctx->d_mlp_X, &ctx->d_mlp_y, &ctx->d_mlp_q, &ctx->d_ghost_frag, &ctx->d_ghost_src, &ctx->d_bda_baa_frag, &ctx->d_hop_baa, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
                     &ctx->d_totals})
@@ -699,6 +776,7 @@ fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const
   // ghosts (copies of the BDA at its position) of the bonds whose BAA it holds
   ctx->n_atoms = n_atoms;
   ctx->n_frag = n_frag;
+  ctx->f_charge.assign(frag_charge, frag_charge + n_frag);
   ctx->n_cut = n_cut;
   ctx->n_int = n_atoms + n_cut;
   const int n_int = ctx->n_int;
@@ -811,6 +889,7 @@ fmo_status fmo_set_system(fmo_ctx* ctx, int32_t n_atoms, const int32_t* Z, const
   ctx->have_system = true;
   ctx->have_result = false;
   ctx->have_guess = false;
+  ctx->mlp_tables_ok = false;
   return FMO_OK;
 }
 
@@ -860,6 +939,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (o.max_iter < 1 || o.max_outer < 1 || !(o.scc_tol > 0) || !(o.e_tol > 0) || !(o.outer_tol > 0))
     return fail(ctx, FMO_ERR_ARG, "iteration limits and tolerances must be positive");
   if (o.guess == 2 && !ctx->have_guess) return fail(ctx, FMO_ERR_STATE, "guess = 2 needs fmo_set_guess");
+  if (o.guess == 1 && !ctx->mlp_ready) return fail(ctx, FMO_ERR_STATE, "guess = 1 needs model weights");
+  if (o.guess != 0 && o.guess != 1 && o.guess != 2) return fail(ctx, FMO_ERR_ARG, "unknown guess");
   if (o.monomer_loop != FMO_LOOP_GLOBAL && o.monomer_loop != FMO_LOOP_NESTED)
     return fail(ctx, FMO_ERR_ARG, "unknown monomer loop");
   if (o.nmer_finish != FMO_NMER_FINISH_ENERGY && o.nmer_finish != FMO_NMER_FINISH_ITERATE)
@@ -909,6 +990,10 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (fs != FMO_OK) return fs;
   stage(st, "monomer setup");
   if (o.guess == 2) CK(h2d(ctx->d_dq_mono.p, ctx->guess.data(), sizeof(double) * ctx->n_sh, st));
+  else if (o.guess == 1) {
+    fs = mlp_predict_device(ctx, st, ctx->d_dq_mono.as<double>());
+    if (fs != FMO_OK) return fs;
+  }
   else CK(cudaMemsetAsync(ctx->d_dq_mono.p, 0, sizeof(double) * ctx->n_sh, st));
   cudaEventRecord(ev[1], st);
   sr.set("fmo_monomers");
@@ -972,6 +1057,14 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   }
   if (outer > o.max_outer) outer = o.max_outer;
   ctx->stats.outer_iterations = outer;
+  if (o.guess == 1 && !(change < o.outer_tol)) {
+    // the learned guess did not lead to self-consistent monomers: start
+    // again from neutral charges
+    for (auto& e : ev) cudaEventDestroy(e);
+    fmo_options o2 = o;
+    o2.guess = 0;
+    return fmo_run(ctx, &o2, cuda_stream);
+  }
   // frozen ESP of the final monomer charges
   CK(compute_phi(ctx, st, 0));
   cudaEventRecord(ev[2], st);
@@ -1222,6 +1315,185 @@ fmo_status fmo_get_trimers(fmo_ctx* ctx, int64_t* n, int32_t* ijk, double* dE3, 
 fmo_status fmo_get_stats(fmo_ctx* ctx, fmo_stats* st) {
   if (!ctx || !st) return FMO_ERR_ARG;
   *st = ctx->stats;
+  return FMO_OK;
+}
+
+static_assert(kMlpWeights == FMO_MLP_N_WEIGHTS, "weight layout of the header");
+
+fmo_status fmo_mlp_init(fmo_ctx* ctx, uint64_t seed) {
+  g_ctx = ctx;
+  if (!ctx) return FMO_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  std::vector<float> w(kMlpWeights, 0.0f);
+  auto fill = [&](int off, int fo, int fi, double gain) {
+    for (int k = 0; k < fo * fi; ++k) w[off + k] = float(nd(rng) * std::sqrt(1.0 / fi) * gain);
+  };
+  fill(kMlpOffW1, kMlpHidden, kMlpIn, 1.0);
+  fill(kMlpOffW2, kMlpHidden, kMlpHidden, 1.0);
+  fill(kMlpOffW3, 2, kMlpHidden, 0.1);
+  for (int k = 0; k < kMlpIn; ++k) w[kMlpOffScale + k] = 1.0f;
+  return fmo_mlp_set_weights(ctx, w.data(), kMlpWeights);
+}
+
+fmo_status fmo_mlp_set_weights(fmo_ctx* ctx, const float* w, int64_t n) {
+  g_ctx = ctx;
+  if (!ctx || !w) return FMO_ERR_ARG;
+  if (n != kMlpWeights) return fail(ctx, FMO_ERR_ARG, "weight count must be " + std::to_string(kMlpWeights));
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->own_stream;
+  CK(ctx->d_mlp_W.ensure(sizeof(float) * kMlpWeights));
+  CK(ctx->d_mlp_W16.ensure(sizeof(__half) * kMlpTrained));
+  CK(ctx->d_mlp_m.ensure(sizeof(float) * kMlpTrained));
+  CK(ctx->d_mlp_v.ensure(sizeof(float) * kMlpTrained));
+  CK(h2d(ctx->d_mlp_W.p, w, sizeof(float) * kMlpWeights, st));
+  CK(cudaMemsetAsync(ctx->d_mlp_m.p, 0, sizeof(float) * kMlpTrained, st));
+  CK(cudaMemsetAsync(ctx->d_mlp_v.p, 0, sizeof(float) * kMlpTrained, st));
+  CK(mlp_to_half(st, kMlpTrained, ctx->d_mlp_W.as<float>(), ctx->d_mlp_W16.as<__half>()));
+  CK(sync_stream(st));
+  ctx->mlp_ready = true;
+  return FMO_OK;
+}
+
+fmo_status fmo_mlp_get_weights(fmo_ctx* ctx, float* w, int64_t* n) {
+  g_ctx = ctx;
+  if (!ctx || !n) return FMO_ERR_ARG;
+  *n = kMlpWeights;
+  if (!w) return FMO_OK;
+  if (!ctx->mlp_ready) return fail(ctx, FMO_ERR_STATE, "no model weights");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->own_stream;
+  CK(d2h(w, ctx->d_mlp_W.p, sizeof(float) * kMlpWeights, st));
+  CK(sync_stream(st));
+  return FMO_OK;
+}
+
+fmo_status fmo_mlp_predict(fmo_ctx* ctx, double* shell_dq) {
+  g_ctx = ctx;
+  if (!ctx || !shell_dq) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  if (!ctx->mlp_ready) return fail(ctx, FMO_ERR_STATE, "no model weights");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->own_stream;
+  DevBuf out;
+  CK(out.ensure(sizeof(double) * ctx->n_sh));
+  fmo_status fs = mlp_predict_device(ctx, st, out.as<double>());
+  if (fs != FMO_OK) { out.release(); return fs; }
+  int err = 0;
+  CK(d2h(&err, ctx->d_mlp_err.p, sizeof(int), st));
+  CK(d2h(shell_dq, out.p, sizeof(double) * ctx->n_sh, st));
+  CK(sync_stream(st));
+  out.release();
+  if (err) return fail(ctx, FMO_ERR_UNSUPPORTED, "more than 256 neighbours within 6 A of an atom");
+  return FMO_OK;
+}
+
+fmo_status fmo_mlp_train(fmo_ctx* ctx, int32_t n_frames, const double* xyz_frames, const double* shell_dq,
+                         int32_t epochs, int32_t batch_frames, double lr, uint64_t seed, double* loss_per_epoch) {
+  g_ctx = ctx;
+  if (!ctx || !xyz_frames || !shell_dq) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  if (!ctx->mlp_ready) return fail(ctx, FMO_ERR_STATE, "initialise or set the model weights first");
+  if (n_frames < 1 || epochs < 1 || batch_frames < 1 || !(lr > 0))
+    return fail(ctx, FMO_ERR_ARG, "frames, epochs, batch size and learning rate must be positive");
+  cudaSetDevice(ctx->device);
+  fmo_status fs = mlp_tables(ctx);
+  if (fs != FMO_OK) return fs;
+  cudaStream_t st = ctx->own_stream;
+  const int N = ctx->n_int, F = n_frames, B = std::min(batch_frames, n_frames), nsh = ctx->n_sh;
+  // frames in internal atom order, their features and targets (float)
+  DevBuf xyz_all, X_all, tgt_all, tmp;
+  CK(xyz_all.ensure(sizeof(double) * 3 * (size_t)N * F));
+  CK(X_all.ensure(sizeof(float) * (size_t)N * kMlpStride * F));
+  CK(tgt_all.ensure(sizeof(float) * (size_t)nsh * F));
+  CK(tmp.ensure(sizeof(double) * std::max((size_t)3 * ctx->n_atoms, (size_t)nsh)));
+  std::vector<float> tf(nsh);
+  for (int f = 0; f < F; ++f) {
+    CK(h2d(tmp.p, xyz_frames + (size_t)f * 3 * ctx->n_atoms, sizeof(double) * 3 * ctx->n_atoms, st));
+    CK(launch_gather_xyz(st, N, ctx->d_perm.as<int>(), tmp.as<double>(), xyz_all.as<double>() + (size_t)f * 3 * N));
+    for (int k = 0; k < nsh; ++k) tf[k] = float(shell_dq[(size_t)f * nsh + k]);
+    CK(h2d(tgt_all.as<float>() + (size_t)f * nsh, tf.data(), sizeof(float) * nsh, st));
+    CK(sync_stream(st));
+  }
+  CK(cudaMemsetAsync(ctx->d_mlp_err.p, 0, sizeof(int), st));
+  CK(mlp_descriptors(st, F, N, xyz_all.as<double>(), ctx->d_mlp_elem4.as<int>(), X_all.as<float>(),
+                     ctx->d_mlp_err.as<int>()));
+  float* W = ctx->d_mlp_W.as<float>();
+  CK(mlp_feature_stats(st, (long long)N * F, X_all.as<float>(), W + kMlpOffMean, W + kMlpOffScale));
+  {
+    // ESP feature: fixed scale 10 (potentials of ~0.01-0.1 Eh/e); one-hot as is
+    std::vector<float> ms = {0.0f, 10.0f, 0.0f, 1.0f, 0.0f, 1.0f, 0.0f, 1.0f, 0.0f, 1.0f};
+    for (int k = 72; k < kMlpIn; ++k) {
+      CK(h2d(W + kMlpOffMean + k, &ms[2 * (k - 72)], sizeof(float), st));
+      CK(h2d(W + kMlpOffScale + k, &ms[2 * (k - 72) + 1], sizeof(float), st));
+    }
+  }
+  CK(cudaMemsetAsync(ctx->d_mlp_m.p, 0, sizeof(float) * kMlpTrained, st));
+  CK(cudaMemsetAsync(ctx->d_mlp_v.p, 0, sizeof(float) * kMlpTrained, st));
+  CK(sync_stream(st));
+  // batch buffers
+  const size_t rows = (size_t)N * B;
+  const int chunk = 256, n_chunks = int((rows + chunk - 1) / chunk);
+  DevBuf Xb, xyzb, y, q, gy, tb, x0, z1, h1, z2, h2, gz1, gz2, part, lpart, idx;
+  CK(Xb.ensure(sizeof(float) * rows * kMlpStride));
+  CK(xyzb.ensure(sizeof(double) * rows * 3));
+  CK(y.ensure(sizeof(float) * rows * 2));
+  CK(q.ensure(sizeof(float) * rows * 2));
+  CK(gy.ensure(sizeof(float) * rows * 2));
+  CK(tb.ensure(sizeof(float) * rows * 2));
+  CK(x0.ensure(sizeof(float) * rows * kMlpStride));
+  for (DevBuf* b : {&z1, &h1, &z2, &h2, &gz1, &gz2}) CK(b->ensure(sizeof(float) * rows * kMlpHidden));
+  CK(part.ensure(sizeof(float) * (size_t)n_chunks * kMlpTrained));
+  CK(lpart.ensure(sizeof(double) * (size_t)B * ctx->n_frag));
+  CK(idx.ensure(sizeof(int) * B));
+  const MlpCache none{nullptr, nullptr, nullptr, nullptr, nullptr};
+  const MlpCache cache{x0.as<float>(), z1.as<float>(), h1.as<float>(), z2.as<float>(), h2.as<float>()};
+  std::mt19937_64 rng(seed);
+  std::vector<int> order(F);
+  for (int f = 0; f < F; ++f) order[f] = f;
+  std::vector<double> lp((size_t)B * ctx->n_frag);
+  int t = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    std::shuffle(order.begin(), order.end(), rng);
+    double lsum = 0.0;
+    long long lcount = 0;
+    for (int b0 = 0; b0 + B <= F; b0 += B) {
+      CK(h2d(idx.p, order.data() + b0, sizeof(int) * B, st));
+      CK(mlp_gather(st, B, N, idx.as<int>(), X_all.as<float>(), xyz_all.as<double>(), Xb.as<float>(),
+                    xyzb.as<double>()));
+      for (int k = 0; k < B; ++k)
+        CK(cudaMemcpyAsync(tb.as<float>() + (size_t)k * nsh, tgt_all.as<float>() + (size_t)order[b0 + k] * nsh,
+                           sizeof(float) * nsh, cudaMemcpyDeviceToDevice, st));
+      const __half* W16 = ctx->d_mlp_W16.as<__half>();
+      // pass 0 (ESP = 0), then the ESP of its charges, then pass 1 with cache
+      CK(mlp_forward(st, int(rows), Xb.as<float>(), W16, W + kMlpOffMean, W + kMlpOffScale, y.as<float>(), none));
+      CK(mlp_project(st, B, ctx->n_frag, N, ctx->d_f_atom0.as<int>(), ctx->d_f_nat.as<int>(),
+                     ctx->d_mlp_fcharge.as<int>(), y.as<float>(), q.as<float>(), nullptr, 0.0, nullptr, nullptr));
+      CK(mlp_esp(st, B, N, nsh, xyzb.as<double>(), ctx->d_mlp_atom_frag.as<int>(), ctx->d_mlp_atom_ie.as<float>(),
+                 ctx->d_sh_atom.as<int>(), ctx->d_mlp_sh_ie.as<float>(), q.as<float>(), Xb.as<float>()));
+      CK(mlp_forward(st, int(rows), Xb.as<float>(), W16, W + kMlpOffMean, W + kMlpOffScale, y.as<float>(), cache));
+      CK(mlp_project(st, B, ctx->n_frag, N, ctx->d_f_atom0.as<int>(), ctx->d_f_nat.as<int>(),
+                     ctx->d_mlp_fcharge.as<int>(), y.as<float>(), q.as<float>(), tb.as<float>(),
+                     1.0 / double(rows * 2), gy.as<float>(), lpart.as<double>()));
+      ++t;
+      CK(mlp_backward_step(st, int(rows), gy.as<float>(), W16, cache, gz2.as<float>(), gz1.as<float>(),
+                           part.as<float>(), chunk, W, ctx->d_mlp_m.as<float>(), ctx->d_mlp_v.as<float>(),
+                           ctx->d_mlp_W16.as<__half>(), float(lr), t));
+      CK(d2h(lp.data(), lpart.p, sizeof(double) * lp.size(), st));
+      CK(sync_stream(st));
+      for (double v : lp) lsum += v;
+      lcount += (long long)rows * 2;
+    }
+    if (loss_per_epoch) loss_per_epoch[ep] = lcount ? lsum / double(lcount) : 0.0;
+  }
+  int err = 0;
+  CK(d2h(&err, ctx->d_mlp_err.p, sizeof(int), st));
+  CK(sync_stream(st));
+  for (DevBuf* b : {&xyz_all, &X_all, &tgt_all, &tmp, &Xb, &xyzb, &y, &q, &gy, &tb, &x0, &z1, &h1, &z2, &h2, &gz1,
+                    &gz2, &part, &lpart, &idx})
+    b->release();
+  if (err) return fail(ctx, FMO_ERR_UNSUPPORTED, "more than 256 neighbours within 6 A of an atom");
   return FMO_OK;
 }
 

@@ -1892,6 +1892,7 @@ __global__ void gather_xyz_kernel(int n_atoms, const int* __restrict__ perm, con
 // followed by exactly one LAUNCH_CHECK, which also counts it
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 #define LAUNCH_CHECK()                                   \
   do {                                                   \

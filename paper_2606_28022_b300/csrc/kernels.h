@@ -121,6 +121,7 @@ cudaError_t launch_global_mix(cudaStream_t st, int n, double* x, const double* x
 size_t mix_state_bytes();
 // number of kernels launched by this library so far (all threads and contexts)
 long long launch_count();
+void note_launch();
 cudaError_t launch_maxdiff(cudaStream_t st, int n, const double* a, const double* b, double* out);
 cudaError_t launch_fmo_sum(cudaStream_t st, int n_frag, const double* e_mono, long long n_pair, const int* pair_scc,
                            const double* e_dim, const double* dEV_dim, double* dE_pair, int n_tri,

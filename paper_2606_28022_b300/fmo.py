@@ -26,7 +26,9 @@ PREC_FP64, PREC_MIXED = 0, 1
 SYMBOLS = ["fmo_options_default", "fmo_create", "fmo_set_system", "fmo_set_coordinates",
            "fmo_set_coordinates_device", "fmo_set_guess", "fmo_run", "fmo_get_energy",
            "fmo_get_sizes", "fmo_get_monomers", "fmo_get_dimers", "fmo_get_trimers",
-           "fmo_get_stats", "fmo_last_error", "fmo_destroy"]
+           "fmo_get_stats", "fmo_last_error", "fmo_destroy", "fmo_mlp_init", "fmo_mlp_set_weights",
+           "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train"]
+MLP_N_WEIGHTS = 26908
 
 
 class FmoElement(C.Structure):
@@ -107,6 +109,12 @@ def load_library(path: str | None = None):
     lib.fmo_get_dimers.argtypes = [vp, C.POINTER(i64), ip, dp, dp, dp, C.POINTER(C.c_uint8), ip]
     lib.fmo_get_trimers.argtypes = [vp, C.POINTER(i64), ip, dp, dp]
     lib.fmo_get_stats.argtypes = [vp, C.POINTER(FmoStats)]
+    fp = C.POINTER(C.c_float)
+    lib.fmo_mlp_init.argtypes = [vp, C.c_uint64]
+    lib.fmo_mlp_set_weights.argtypes = [vp, fp, i64]
+    lib.fmo_mlp_get_weights.argtypes = [vp, fp, C.POINTER(i64)]
+    lib.fmo_mlp_predict.argtypes = [vp, dp]
+    lib.fmo_mlp_train.argtypes = [vp, i32, dp, dp, i32, i32, C.c_double, C.c_uint64, dp]
     lib.fmo_last_error.argtypes = [vp]
     lib.fmo_last_error.restype = C.c_char_p
     lib.fmo_destroy.argtypes = [vp]
@@ -304,6 +312,36 @@ class FMO:
         d3, cr = np.zeros(max(m, 1)), np.zeros(max(m, 1))
         self._check(self.lib.fmo_get_trimers(self.h, C.byref(n), _ip(ijk), _dp(d3), _dp(cr)))
         return Trimers(ijk[:3 * m].reshape(-1, 3), d3[:m], cr[:m])
+
+    # learned initial charges (options guess=1)
+    def mlp_init(self, seed: int = 0):
+        self._check(self.lib.fmo_mlp_init(self.h, seed))
+
+    def mlp_set_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(self.lib.fmo_mlp_set_weights(self.h, w.ctypes.data_as(C.POINTER(C.c_float)), len(w)))
+
+    def mlp_get_weights(self) -> np.ndarray:
+        n = C.c_int64()
+        self._check(self.lib.fmo_mlp_get_weights(self.h, None, C.byref(n)))
+        w = np.zeros(n.value, dtype=np.float32)
+        self._check(self.lib.fmo_mlp_get_weights(self.h, w.ctypes.data_as(C.POINTER(C.c_float)), C.byref(n)))
+        return w
+
+    def mlp_predict(self) -> np.ndarray:
+        ns, _ = self.sizes()
+        q = np.zeros(ns)
+        self._check(self.lib.fmo_mlp_predict(self.h, _dp(q)))
+        return q
+
+    def mlp_train(self, xyz_frames: np.ndarray, shell_dq: np.ndarray, epochs: int, batch_frames: int = 8,
+                  lr: float = 1e-3, seed: int = 0) -> np.ndarray:
+        x = np.ascontiguousarray(xyz_frames, dtype=np.float64)
+        q = np.ascontiguousarray(shell_dq, dtype=np.float64)
+        loss = np.zeros(epochs)
+        self._check(self.lib.fmo_mlp_train(self.h, len(x), _dp(x.reshape(-1)), _dp(q.reshape(-1)), epochs,
+                                           batch_frames, lr, seed, _dp(loss)))
+        return loss
 
     def stats(self) -> dict:
         s = FmoStats()

@@ -1,0 +1,89 @@
+"""Learned initial charges on the GPU against the oracle (oracle/mlp.py):
+two-pass prediction with the same (FP16-rounded) weights, the loss of the
+first training epoch, and the guess inside fmo_run."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2606_28022_b300.inputs import geometry as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu(params):
+    from paper_2606_28022_b300 import build, fmo
+    build.build()
+    return fmo.FMO(params, 0)
+
+
+def _flat(p):
+    return np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(), p["b3"],
+                           p["mean"], p["scale"]]).astype(np.float32)
+
+
+def _fp16_params(seed, X):
+    p = mlp.init_params(seed)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        p[k] = p[k].astype(np.float16).astype(np.float64)
+    p["b1"] = (np.random.default_rng(seed + 1).normal(size=128) * 0.1).astype(np.float16).astype(np.float64)
+    p["mean"] = X.mean(0).astype(np.float32).astype(np.float64)
+    p["scale"] = (1.0 / (X.std(0) + 1.0)).astype(np.float32).astype(np.float64)
+    return p
+
+
+def test_prediction_matches_oracle(gpu, params, water64):
+    s = water64.subsystem(range(4))
+    X = mlp.features(s, params)
+    p = _fp16_params(7, X)
+    gpu.set_system(s)
+    gpu.mlp_set_weights(_flat(p))
+    q = gpu.mlp_predict()
+    ref = mlp.predict(p, s, params)
+    assert np.max(np.abs(q - ref)) < 1e-4
+    for f in range(s.n_frag):
+        assert abs(q[np.repeat(s.frag, 2) == f].sum()) < 1e-5
+
+
+def test_first_epoch_loss_matches_oracle(gpu, params, water64):
+    s = water64.subsystem(range(4))
+    frames = [G.jittered(s, 0.05, 100 + k) for k in range(2)]
+    rng = np.random.default_rng(3)
+    targets = rng.normal(size=(2, 2 * s.n_atoms)) * 0.1
+    geo = [mlp.features(f, params) for f in frames]
+    Xall = np.concatenate(geo)
+    p = _fp16_params(11, Xall)
+    # the trainer sets the feature statistics from the frames: columns 0-71
+    # mean and 1/(std + 1), the potential (0, 10), the one-hot (0, 1)
+    p["mean"][:72] = Xall[:, :72].mean(0).astype(np.float32)
+    p["scale"][:72] = (1.0 / (Xall[:, :72].std(0) + 1.0)).astype(np.float32)
+    p["mean"][72:], p["scale"][72:] = 0.0, np.array([10.0, 1, 1, 1, 1])
+    want = np.mean([np.mean((mlp.predict(p, f, params, geo=g) - t) ** 2) for f, g, t in zip(frames, geo, targets)])
+    gpu.set_system(s)
+    gpu.mlp_set_weights(_flat(p))
+    loss = gpu.mlp_train(np.stack([f.xyz for f in frames]), targets, epochs=1, batch_frames=2, lr=1e-3)
+    assert abs(loss[0] - want) < 1e-4 * want
+
+
+def test_learned_guess_in_fmo_run(gpu, params, water64):
+    from paper_2606_28022_b300 import fmo
+    s = water64.subsystem(range(8))
+    gpu.set_system(s)
+    frames, targets = [], []
+    for k in range(6):
+        f = G.jittered(s, 0.05, 200 + k)
+        gpu.set_coordinates(f.xyz)
+        gpu.run(fmo.options(level=1))
+        frames.append(f.xyz)
+        targets.append(gpu.monomers().shell_dq)
+    gpu.mlp_init(5)
+    loss = gpu.mlp_train(np.stack(frames), np.stack(targets), epochs=40, batch_frames=2, lr=3e-3)
+    assert loss[-1] < 0.5 * loss[0]
+    test = G.jittered(s, 0.05, 999)
+    gpu.set_coordinates(test.xyz)
+    gpu.run(fmo.options(level=2))
+    e0, it0 = gpu.energies(), gpu.stats()["outer_iterations"]
+    gpu.run(fmo.options(level=2, guess=1))
+    e1, it1 = gpu.energies(), gpu.stats()["outer_iterations"]
+    assert abs(e1[1] - e0[1]) < 1e-8 and abs(e1[0] - e0[0]) < 1e-8
+    assert (gpu.monomers().status == 0).all()
