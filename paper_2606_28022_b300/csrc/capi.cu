@@ -1024,6 +1024,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       CK(d2h(&hs, ctx->d_mix_state.p, sizeof(hs), st));
       CK(sync_stream(st));
       stage(st, "global mix", outer);
+      if (debug_level() >= 5)
+        fprintf(stderr, "[fmo] outer %d phase %d max|dq_out - dq_in| %.3e E1 %.12f\n", outer, phase, hs.diff, hs.e1);
       change = hs.converged ? 0.0 : hs.diff;
       if (!(hs.diff == hs.diff)) break;
       if (hs.converged) break;
