@@ -425,7 +425,7 @@ cudaError_t compute_phi(fmo_ctx* ctx, cudaStream_t st, int use_float) {
 
 fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& sp, bool with_phi,
                    int pass_id, cudaStream_t st, int single_step = 0, int step_phase = 1, int reortho = 0,
-                   int cold = 1, int reortho32 = 0, double jac_hint = 1.0) {
+                   int cold = 1, int reortho32 = 0, double jac_hint = 1.0, bool capture = false) {
   const int nn = int(P.nm.size());
   if (nn == 0) return FMO_OK;
   SccLaunch L{};
@@ -478,6 +478,14 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   if (!sp.a_d) CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
   if (o.precision == FMO_PREC_MIXED && !sp.a_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
   L.Agd = P.Agd.as<double>(); L.Agf = P.Agf.as<float>();
+  if (capture) {
+    // recorded into a CUDA graph: the previous step's residual is read on the
+    // device (mixer state), no timing or read-back
+    L.trace = nullptr;
+    L.jac_hint_dev = reinterpret_cast<const double*>(ctx->d_mix_state.p) + 1;
+    CK(launch_scc(st, nn, L));
+    return FMO_OK;
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -550,6 +558,75 @@ double now_ms(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
   return ms;
+}
+
+// The FP64 steps of the global monomer loop as one CUDA graph: a while node
+// whose body is phi, one single-step SCC launch of every monomer, the global
+// mixer and a control kernel that counts the step and clears the node's
+// condition on convergence, a NaN residual or the step limit.  No host round
+// trip per step.  `done` steps have run; on return *outer is the last step.
+cudaError_t run_monomer_graph(fmo_ctx* ctx, const fmo_options& o, const SmemPlan& sp, cudaStream_t st, int done,
+                              int* outer) {
+  const int nf = ctx->n_frag;
+  int* d_outer = reinterpret_cast<int*>(ctx->d_scalar.p);
+  cudaError_t e = h2d(d_outer, &done, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t g = nullptr, body = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t node;
+  const long long l0 = launch_count();
+  long long per_step = 0;
+  auto cleanup = [&]() {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+  };
+#define GK(x) do { e = (x); if (e != cudaSuccess) { cleanup(); return e; } } while (0)
+  GK(cudaGraphCreate(&g, 0));
+  GK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  GK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  body = cp.conditional.phGraph_out[0];
+  GK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  GK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  {
+    cudaError_t ce = compute_phi(ctx, cs, 0);
+    fmo_status fs = (ce == cudaSuccess) ? run_scc(ctx, ctx->mono, o, sp, true, 0, cs, 1, 1, 0, 0, 0, 1.0, true)
+                                        : FMO_ERR_CUDA;
+    if (ce == cudaSuccess && fs == FMO_OK)
+      ce = launch_global_mix(cs, ctx->n_sh, ctx->d_dq_mono.as<double>(), ctx->mono.dq.as<double>(), nf,
+                             ctx->mono.energy.as<double>(), ctx->d_mix_hist.as<double>(), ctx->d_mix_state.p,
+                             o.outer_tol, o.e_tol, 1);
+    if (ce == cudaSuccess && fs == FMO_OK) ce = launch_loop_control(cs, h, ctx->d_mix_state.p, d_outer, o.max_outer);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+    if (ce == cudaSuccess && fs != FMO_OK) ce = cudaErrorUnknown;
+    GK(ce);
+    GK(ee);
+  }
+  per_step = launch_count() - l0;
+  GK(cudaGraphInstantiate(&ge, g, 0));
+  GK(cudaGraphLaunch(ge, st));
+  GK(d2h(outer, d_outer, sizeof(int), st));
+  GK(sync_stream(st));
+  // the captured launches ran once per step
+  for (long long k = 0; k < per_step * (long long)(*outer - done - 1); ++k) note_launch();
+  const int steps = *outer - done;
+  for (const Nmer& m : ctx->mono.nm) {
+    const double n3 = 15.0 * double(m.n) * m.n * m.n;
+    ctx->stats.iters_fp64[0] += steps;
+    ctx->stats.flops_fp64[0] += n3 * steps;
+  }
+  ctx->stats.scc_launches[0] += steps;
+  cleanup();
+  return cudaSuccess;
+#undef GK
 }
 
 // Per-system tables of the learned-guess model: element index (H, C, N, O),
@@ -1010,7 +1087,21 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     int phase = (o.precision == FMO_PREC_MIXED) ? 0 : 1, reortho = 0, n32 = 0;
     const int cap32 = std::max(8, o.max_outer / 2);
     struct { double e_prev, diff, e1; int have_prev, hcount, hhead, converged, count; } hs{};
+    bool graph_ok = (o.schedule == 0);
     for (outer = 1; outer <= o.max_outer; ++outer) {
+      if (graph_ok && phase == 1 && reortho == 0 && outer > 1 && outer < o.max_outer) {
+        // the remaining FP64 steps run device-driven inside one CUDA graph
+        int last = outer - 1;
+        if (run_monomer_graph(ctx, o, sp_mono, st, outer - 1, &last) == cudaSuccess) {
+          CK(d2h(&hs, ctx->d_mix_state.p, sizeof(hs), st));
+          CK(sync_stream(st));
+          outer = last;
+          change = hs.converged ? 0.0 : hs.diff;
+          break;
+        }
+        graph_ok = false;                 // graphs unavailable: host-driven steps
+        cudaGetLastError();
+      }
       // the FP32 phase works with an FP32 estimate of the potential
       CK(compute_phi(ctx, st, phase == 0 ? 1 : 0));
       stage(st, "phi", outer);

@@ -477,6 +477,7 @@ struct SccArgs {
   int cold_refine;   // the vectors are the Loewdin start: restore S-orthonormality in FP64 first
   int reortho32;     // single step: one FP32 Newton-Schulz step before the iteration
   double jac_hint;   // SCC residual before this launch (sets the first Jacobi threshold)
+  const double* jac_hint_dev;   // if set: read jac_hint from the device (graph-launched steps)
   int fp64_finish;   // mixed: stop after this many FP64 iterations (0: converge in FP64)
   int energy_finish; // mixed n-mers: end with the FP64 energy of the FP32-converged density
   int cold_steps;    // Newton-Schulz steps allowed for the cold start (far from orthonormal: more)
@@ -1198,6 +1199,7 @@ __device__ __forceinline__ double jacobi_threshold(double last, double floor_tol
 
 __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (ar.jac_hint_dev) ar.jac_hint = *ar.jac_hint_dev;
   const int idx = ar.order[blockIdx.x];
   const Nmer nm = ar.nmers[idx];
   const int n = nm.n, nsh = nm.nsh, nat = nm.nat, npad = nm.npad;
@@ -1980,7 +1982,7 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
   ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho;
-  ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.trace = L.trace;
+  ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.jac_hint_dev = L.jac_hint_dev; ar.trace = L.trace;
   ar.fp64_finish = L.fp64_finish; ar.energy_finish = L.energy_finish; ar.first_jac_tol = L.first_jac_tol; ar.cold_steps = L.cold_steps; ar.first_rot = L.first_rot; ar.tol = L.tol; ar.etol = L.etol;
   ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
   ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
@@ -2044,6 +2046,24 @@ cudaError_t launch_hop_projector(cudaStream_t st, int n_nmer, const Nmer* nmers,
                                  const int* elem, const DevElem* el, double v_hop, const double* S, double* V) {
   if (n_nmer == 0) return cudaSuccess;
   hop_projector_kernel<<<n_nmer, 256, 0, st>>>(nmers, ft, xyz, elem, el, v_hop, S, V);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+// Device-side control of the monomer loop inside a CUDA graph: counts the
+// step and keeps the graph's while node running until the global mixer
+// reports convergence, a NaN residual or the step limit.
+__global__ void loop_control_kernel(cudaGraphConditionalHandle handle, const MixState* st, int* outer,
+                                    int max_outer) {
+  const int o = ++*outer;
+  const bool more = !st->converged && st->diff == st->diff && o < max_outer;
+  cudaGraphSetConditional(handle, more ? 1u : 0u);
+}
+
+cudaError_t launch_loop_control(cudaStream_t st, unsigned long long handle, const void* mix_state, int* outer,
+                                int max_outer) {
+  loop_control_kernel<<<1, 1, 0, st>>>((cudaGraphConditionalHandle)handle, (const MixState*)mix_state, outer,
+                                       max_outer);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

@@ -71,6 +71,7 @@ struct SccLaunch {
   int cold_refine;
   int reortho32;
   double jac_hint;
+  const double* jac_hint_dev;
   double* trace;
   int fp64_finish;
   int energy_finish;
@@ -109,6 +110,8 @@ cudaError_t launch_gamma_full(cudaStream_t st, int n_sh, const double* xyz, cons
 cudaError_t launch_phi_gemv(cudaStream_t st, int n_sh, const double* gam, const double* dq, double* phi);
 cudaError_t launch_hop_projector(cudaStream_t st, int n_nmer, const Nmer* nmers, FragTab ft, const double* xyz,
                                  const int* elem, const DevElem* el, double v_hop, const double* S, double* V);
+cudaError_t launch_loop_control(cudaStream_t st, unsigned long long handle, const void* mix_state, int* outer,
+                                int max_outer);
 cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);
 cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, const double* bounds,
                                  double cut, double* rmin);

@@ -202,3 +202,18 @@ def test_hop_needs_fp64(gpu, params):
     gpu.set_system(G.polyalanine_helix(3))
     with pytest.raises(fmo.FMOError):
         gpu.run(fmo.options(precision="mixed"))
+
+
+def test_graph_driven_and_host_driven_monomer_loops_agree(gpu, params, water64):
+    from paper_2606_28022_b300 import fmo
+    s = water64.subsystem(range(12))
+    gpu.set_system(s)
+    out = []
+    for schedule in (0, 1):
+        for prec in ("fp64", "mixed"):
+            gpu.run(fmo.options(schedule=schedule, precision=prec))
+            out.append((gpu.energies(), gpu.monomers().shell_dq.copy(), gpu.stats()["outer_iterations"]))
+    for a, b in ((0, 2), (1, 3)):
+        assert out[a][0][:2] == out[b][0][:2]          # FMO1, FMO2 (FMO3 is NaN at level 2)
+        assert np.array_equal(out[a][1], out[b][1])
+        assert out[a][2] == out[b][2]
