@@ -310,7 +310,7 @@ fmo_status fmo_get_stats(fmo_ctx *ctx, fmo_stats *st);
  * Limits: at most 256 basis functions, 128 shells and 128 atoms; larger
  * molecules return FMO_ERR_ARG with a message.  The call only enqueues work:
  * read the outputs after the stream has finished.
- * Memory: all scratch (about 4.5 MiB) is one fixed device array that every
+ * Memory: all scratch (about 5 MiB) is one fixed device array that every
  * GPU loading the library holds until the process exits.  The first call on
  * a device looks up that array's device address; make that first call before
  * any stream capture.  All calls share the array and it keeps the last

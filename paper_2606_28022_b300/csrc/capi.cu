@@ -46,7 +46,7 @@ struct Pass {
   std::vector<int> order;
   int max_n = 0, max_nsh = 0, max_nat = 0, max_pairs = 0;
   long long tot_mat = 0, tot_sh = 0, tot_gam = 0, tot_ao = 0, tot_hist = 0, tot_apad = 0;
-  DevBuf d_nm, d_order, S, H0, gam, CTd, W1d, W2d, Agd, CTf, W1f, W2f, Agf, esp, dq, eps, hist;
+  DevBuf d_nm, d_order, S, H0, S32, H32, gam, CTd, W1d, W2d, Agd, CTf, W1f, W2f, Agf, esp, dq, eps, hist;
   DevBuf energy, e_el, e_rep, dEV, iters, iters32, status;
   DevBuf V;                               // hybrid orbital projectors (n x n per n-mer)
   int max_healed_sh = 0, max_projected = 0;
@@ -303,6 +303,8 @@ cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3
   ENS(P.W1d, sizeof(double) * mat);
   ENS(P.W2d, sizeof(double) * mat);
   if (precision == FMO_PREC_MIXED) {
+    ENS(P.S32, sizeof(float) * mat);
+    ENS(P.H32, sizeof(float) * mat);
     ENS(P.CTf, sizeof(float) * mat);
     ENS(P.W1f, sizeof(float) * mat);
     ENS(P.W2f, sizeof(float) * mat);
@@ -367,6 +369,10 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
                       P.H0.as<double>(), reuse ? warm_from->d_nm.as<Nmer>() : nullptr,
                       reuse ? warm_from->S.as<double>() : nullptr,
                       reuse ? warm_from->H0.as<double>() : nullptr, ctx->d_prim.as<PrimPair>()));
+  if (precision == FMO_PREC_MIXED) {   // FP32 copies for the FP32 iterations
+    CK(launch_to_float(st, P.tot_mat, P.S.as<double>(), P.S32.as<float>()));
+    CK(launch_to_float(st, P.tot_mat, P.H0.as<double>(), P.H32.as<float>()));
+  }
   if (ctx->n_cut > 0)
     CK(launch_hop_projector(st, nn, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(),
                             ctx->d_el.as<DevElem>(), ctx->params.v_hop, P.S.as<double>(), P.V.as<double>()));
@@ -437,6 +443,7 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.CTf = P.CTf.as<float>(); L.W1f = P.W1f.as<float>(); L.W2f = P.W2f.as<float>(); L.Agf = P.Agf.as<float>();
   L.phi = with_phi ? ctx->d_phi.as<double>() : nullptr;
   L.vhop = ctx->n_cut > 0 ? P.V.as<double>() : nullptr;
+  if (o.precision == FMO_PREC_MIXED) { L.S32 = P.S32.as<float>(); L.H32 = P.H32.as<float>(); }
   L.dq_mono = ctx->d_dq_mono.as<double>();
   L.esp = P.esp.as<double>(); L.dq = P.dq.as<double>(); L.eps = P.eps.as<double>(); L.hist = P.hist.as<double>();
   L.energy = P.energy.as<double>(); L.e_el = P.e_el.as<double>(); L.e_rep = P.e_rep.as<double>();

@@ -161,7 +161,8 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // Block-level GEMM: C[m][n] = sum_k a(m,k) * b(n,k) with
 //   a(m,k) = A[m*sam + ka*sak] * (kscale ? kscale[k] : 1),  ka = kidx ? kidx[k] : k,
 //   b(n,k) = B[n*sbn + kb*sbk],                             kb = kidx_b ? kidx_b[k] : k
-// (B may be stored in a wider type TB; it is rounded to T on load).
+// (B may be stored in a wider type TB; it is rounded to T on load; kscale is
+// of type TS: double scales multiply in FP64, scales of type T in T).
 // 256 threads as a 16 x 16 grid, each computing TM x TN outputs of a
 // (16 TM) x (16 TN) tile; BK = 16.  The tile edge (64 or 80) is chosen per
 // dimension to waste the least padding (an n = 76 monomer fits one 80-row
@@ -171,12 +172,12 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 constexpr int kGemmSmemElems = 2 * 16 * (80 + 1);
 
-template <typename T, typename TB, int TM, int TN>
+template <typename T, typename TB, typename TS, int TM, int TN>
 __device__ __forceinline__ void block_gemm_tile(int M, int N, int K, const T* __restrict__ A, long long sam,
                                                 long long sak, const TB* __restrict__ B, long long sbn,
                                                 long long sbk, T* __restrict__ C, long long ldc,
                                                 const int* __restrict__ kidx, const int* __restrict__ kidx_b,
-                                                const double* __restrict__ kscale, T* smem) {
+                                                const TS* __restrict__ kscale, T* smem) {
   constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
   // rows of the staged slices padded by one element: the k-contiguous
   // stores (16 k values per warp) then fall into distinct banks
@@ -225,7 +226,10 @@ __device__ __forceinline__ void block_gemm_tile(int M, int N, int K, const T* __
           T v = T(0);
           if (oa[r] >= 0 && gk < K) {
             v = A[oa[r] + (long long)(kidx ? kidx[gk] : gk) * sak];
-            if (kscale) v = T(double(v) * kscale[gk]);
+            if (kscale) {
+              if constexpr (sizeof(TS) == sizeof(T)) v = v * T(kscale[gk]);
+              else v = T(double(v) * kscale[gk]);
+            }
           }
           ra[r] = v;
         }
@@ -279,15 +283,18 @@ __device__ __forceinline__ int gemm_micro(int d) {
   return p5 < p4 ? 5 : 4;
 }
 
-template <typename T, typename TB = T>
+template <typename X>
+struct NoDeduce { using type = X; };   // keeps kscale out of template deduction (nullptr -> TS = double)
+
+template <typename T, typename TB = T, typename TS = double>
 __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long long sam, long long sak,
                            const TB* __restrict__ B, long long sbn, long long sbk, T* __restrict__ C,
                            long long ldc, const int* __restrict__ kidx, const int* __restrict__ kidx_b,
-                           const double* __restrict__ kscale, T* smem) {
+                           const typename NoDeduce<TS>::type* __restrict__ kscale, T* smem) {
   const int tm = gemm_micro(M), tn = gemm_micro(N);
 #define FMO_GEMM_CASE(a, b)                                                                              \
   if (tm == a && tn == b) {                                                                              \
-    block_gemm_tile<T, TB, a, b>(M, N, K, A, sam, sak, B, sbn, sbk, C, ldc, kidx, kidx_b, kscale, smem); \
+    block_gemm_tile<T, TB, TS, a, b>(M, N, K, A, sam, sak, B, sbn, sbk, C, ldc, kidx, kidx_b, kscale, smem); \
     return;                                                                                              \
   }
   FMO_GEMM_CASE(4, 4) FMO_GEMM_CASE(4, 5) FMO_GEMM_CASE(5, 4) FMO_GEMM_CASE(5, 5)

@@ -478,6 +478,8 @@ struct SccArgs {
   int reortho32;     // single step: one FP32 Newton-Schulz step before the iteration
   double jac_hint;   // SCC residual before this launch (sets the first Jacobi threshold)
   const double* jac_hint_dev;   // if set: read jac_hint from the device (graph-launched steps)
+  const float* S32;  // mixed precision: S and H0 rounded to FP32 (the FP32 iterations read these)
+  const float* H32;
   int fp64_finish;   // mixed: stop after this many FP64 iterations (0: converge in FP64)
   int energy_finish; // mixed n-mers: end with the FP64 energy of the FP32-converged density
   int cold_steps;    // Newton-Schulz steps allowed for the cold start (far from orthonormal: more)
@@ -498,6 +500,7 @@ struct SccSmem {
   void* gemm;
   double* red;
   double* sig;
+  float* sig32;  // FP32 copy of sig for the FP32 Fock build
   double* dqin;
   double* dqout;
   double* esp;
@@ -563,7 +566,7 @@ __device__ SccSmem carve_scc_smem(unsigned char* base, int max_n, int max_nsh, i
   s.dqout = (double*)take(sizeof(double) * max_nsh);
   s.esp = (double*)take(sizeof(double) * max_nsh);
   s.q0 = (double*)take(sizeof(double) * max_nsh);
-  take(sizeof(double) * max_nsh);
+  s.sig32 = (float*)take(sizeof(double) * max_nsh);
   take(sizeof(double) * max_nsh);
   s.dqat = (double*)take(sizeof(double) * max_nat);
   s.g3 = (double*)take(sizeof(double) * max_nat);
@@ -934,7 +937,9 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
       v = warp_sum(v);
       if (lane == 0) {
         const int a = sm.mp.sh_at[s];
-        sm.sig[s] = v - sm.g3[a] * sm.dqat[a] * sm.dqat[a] + sm.esp[s];
+        const double sg = v - sm.g3[a] * sm.dqat[a] * sm.dqat[a] + sm.esp[s];
+        sm.sig[s] = sg;
+        if constexpr (sizeof(T) == 4) sm.sig32[s] = float(sg);
       }
     }
   }
@@ -943,7 +948,19 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double* Vm = ar.vhop ? ar.vhop + nm.mat : nullptr;   // hybrid orbital projectors, if any
-    for (int i = wid; i < n; i += nw) {
+    if constexpr (sizeof(T) == 4) {
+      // FP32 iteration: built in FP32 from the FP32 copies of H0 and S (the
+      // result is rounded to FP32 anyway; no FP64 work per element)
+      const float* H32 = ar.H32 + nm.mat;
+      const float* S32 = ar.S32 + nm.mat;
+      for (int i = wid; i < n; i += nw) {
+        const float si = sm.sig32[sm.mp.ao_sh[i]];
+        const float* hr = H32 + (long long)i * n;
+        const float* sr = S32 + (long long)i * n;
+        T* fr = pp.W1 + (long long)i * n;
+        for (int j = lane; j < n; j += 32) fr[j] = fmaf(0.5f * sr[j], si + sm.sig32[sm.mp.ao_sh[j]], hr[j]);
+      }
+    } else for (int i = wid; i < n; i += nw) {
       const double si = sm.sig[sm.mp.ao_sh[i]];
       const double* hr = Hm + (long long)i * n;
       const double* sr = Sm + (long long)i * n;
@@ -988,7 +1005,7 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     if (sm.misc[1]) {
       const int no = sm.misc[2], nv = sm.misc[0];
       T* K = pp.W2;                                 // no x nv
-      double kmax = 0.0;
+      T kmax_t = T(0);
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int r = wid; r < no; r += nw) {
         const int i = sm.occ[r];
@@ -999,10 +1016,10 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
           const int a = sm.virt[c];
           const T k = arow[a] * recip<T>(ei - sm.eps[a]);
           krow[c] = k;
-          kmax = fmax(kmax, fabs(double(k)));
+          kmax_t = fmax(kmax_t, fabs(k));
         }
       }
-      kmax = block_max(kmax, sm.red);
+      const double kmax = block_max(double(kmax_t), sm.red);
       // (1 + k + k^2/2) keeps orthonormality up to k^4/4: rotate only while
       // that stays below the working precision, otherwise diagonalise
       rotated = kmax <= (sizeof(T) == 8 ? 1e-4 : 2e-2);
@@ -1036,11 +1053,11 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   }
   mark(3);
   // compacted occupations
-  double* fc = reinterpret_cast<double*>(sm.jsc);   // js scratch is free here (npad doubles)
-  for (int k = threadIdx.x; k < nocc; k += blockDim.x) fc[k] = sm.focc[sm.occ[k]];
+  T* fc = reinterpret_cast<T*>(sm.jsc);   // js scratch is free here (npad doubles)
+  for (int k = threadIdx.x; k < nocc; k += blockDim.x) fc[k] = T(sm.focc[sm.occ[k]]);
   __syncthreads();
   // density P = sum_occ f_i c_i c_i^T  (W1)
-  block_gemm<T>(n, n, nocc, pp.CT, 1, n, pp.CT, 1, n, pp.W1, n, sm.occ, sm.occ, fc, gemm);
+  block_gemm<T, T, T>(n, n, nocc, pp.CT, 1, n, pp.CT, 1, n, pp.W1, n, sm.occ, sm.occ, fc, gemm);
   mark(4);
   // Mulliken shell populations (Eq. 3) and the band energy sum P H0, one warp per shell
   double eb_local = 0.0;
@@ -1048,11 +1065,29 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int s = wid; s < nsh; s += nw) {
       double pop = 0.0, eb = 0.0;
-      for (int k = sm.mp.sh_ao0[s]; k < sm.mp.sh_ao0[s + 1]; ++k) {
-        for (int j = lane; j < n; j += 32) {
-          const double pv = double(pp.W1[(long long)k * n + j]);
-          pop += pv * Sm[(long long)k * n + j];
-          eb += pv * Hm[(long long)k * n + j];
+      if constexpr (sizeof(T) == 4) {
+        // FP32 iteration: per-lane FP32 partial sums (a few rows of n/32
+        // terms each) of the FP32 density with the FP32 copies, lanes summed
+        // in FP64
+        const float* S32 = ar.S32 + nm.mat;
+        const float* H32 = ar.H32 + nm.mat;
+        float popf = 0.f, ebf = 0.f;
+        for (int k = sm.mp.sh_ao0[s]; k < sm.mp.sh_ao0[s + 1]; ++k) {
+          for (int j = lane; j < n; j += 32) {
+            const float pv = pp.W1[(long long)k * n + j];
+            popf = fmaf(pv, S32[(long long)k * n + j], popf);
+            ebf = fmaf(pv, H32[(long long)k * n + j], ebf);
+          }
+        }
+        pop = double(popf);
+        eb = double(ebf);
+      } else {
+        for (int k = sm.mp.sh_ao0[s]; k < sm.mp.sh_ao0[s + 1]; ++k) {
+          for (int j = lane; j < n; j += 32) {
+            const double pv = double(pp.W1[(long long)k * n + j]);
+            pop += pv * Sm[(long long)k * n + j];
+            eb += pv * Hm[(long long)k * n + j];
+          }
         }
       }
       pop = warp_sum(pop);
@@ -1083,7 +1118,10 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
   T* gemm = reinterpret_cast<T*>(sm.gemm);
   const double* Sm = ar.S + nm.mat;
   for (int step = 0; step < max_steps; ++step) {
-    block_gemm<T, double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);   // V = CT S
+    if constexpr (sizeof(T) == 4)   // S rounded to FP32 either way; the FP32 copy skips the conversions
+      block_gemm<T>(n, n, n, pp.CT, n, 1, ar.S32 + nm.mat, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
+    else
+      block_gemm<T, double>(n, n, n, pp.CT, n, 1, Sm, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);   // V = CT S
     block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.W1, n, nullptr, nullptr, nullptr, gemm);       // M = V CT^T
     const double err = max_dev_from_identity(pp.W1, n, n, sm.red);
     if (err < tol) break;
@@ -1982,7 +2020,7 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
   ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho;
-  ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.jac_hint_dev = L.jac_hint_dev; ar.trace = L.trace;
+  ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.jac_hint_dev = L.jac_hint_dev; ar.S32 = L.S32; ar.H32 = L.H32; ar.trace = L.trace;
   ar.fp64_finish = L.fp64_finish; ar.energy_finish = L.energy_finish; ar.first_jac_tol = L.first_jac_tol; ar.cold_steps = L.cold_steps; ar.first_rot = L.first_rot; ar.tol = L.tol; ar.etol = L.etol;
   ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
   ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
@@ -2122,6 +2160,21 @@ cudaError_t launch_fmo_sum(cudaStream_t st, int n_frag, const double* e_mono, lo
 }
 
 __global__ void stamp_kernel(unsigned long long* t) { *t = globaltimer_ns(); }
+
+// out[i] = in[i] rounded to FP32 (grid-stride)
+__global__ void __launch_bounds__(256) to_float_kernel(long long n, const double* __restrict__ in,
+                                                       float* __restrict__ out) {
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    out[i] = float(in[i]);
+}
+
+cudaError_t launch_to_float(cudaStream_t st, long long n, const double* in, float* out) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, 148LL * 16);
+  to_float_kernel<<<int(blocks), 256, 0, st>>>(n, in, out);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
 
 cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t) {
   stamp_kernel<<<1, 1, 0, st>>>(t);

@@ -72,6 +72,8 @@ struct SccLaunch {
   int reortho32;
   double jac_hint;
   const double* jac_hint_dev;
+  const float* S32;   // mixed precision: FP32 copies of S and H0 (launch_to_float)
+  const float* H32;
   double* trace;
   int fp64_finish;
   int energy_finish;
@@ -118,6 +120,8 @@ cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const 
 cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const long long* out_idx, FragTab ft,
                          const double* xyz, const int* sh_atom, const double* sh_inv_eta, const double* dq,
                          GParams g, double* out);
+// out[i] = (float)in[i], i < n
+cudaError_t launch_to_float(cudaStream_t st, long long n, const double* in, float* out);
 cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t);
 cudaError_t launch_global_mix(cudaStream_t st, int n, double* x, const double* xo, int nf, const double* e,
                               double* hist, void* state, double tol, double etol, int allow_converge);

@@ -28,7 +28,7 @@ namespace {
 constexpr int kNaMaxAO = 256;      // basis functions of the molecule
 constexpr int kNaMaxShell = 128;   // shells
 constexpr int kNaMaxAtom = 128;    // atoms
-constexpr size_t kNaBytes = 4608 * 1024;   // 4.5 MiB
+constexpr size_t kNaBytes = 5120 * 1024;   // 5 MiB
 
 // The scratch of every call, on every device that loads the library.  Host
 // code must not pass this symbol to a kernel (on the host it is only a
@@ -188,6 +188,8 @@ extern "C" fmo_status fmo_scc_solve_noalloc(const fmo_params* p, int32_t n_atoms
   float* W1f = L.take<float>((size_t)n * n);
   float* W2f = L.take<float>((size_t)n * n);
   float* Agf = L.take<float>((size_t)npad * npad);
+  float* S32 = L.take<float>((size_t)n * n);
+  float* H32 = L.take<float>((size_t)n * n);
   double* gam = L.take<double>((size_t)nsh * nsh);
   double* espv = L.take<double>(nsh);
   double* dqv = L.take<double>(nsh);
@@ -244,12 +246,17 @@ extern "C" fmo_status fmo_scc_solve_noalloc(const fmo_params* p, int32_t n_atoms
                          d_kab, ne, g, S, H0));
   NA_CK(launch_gamma(st, 1, nsh, d_nm, ft, xyz_dev, d_elem, d_sh_atom, d_inv_eta, g, gam));
   const bool use_f = (o.precision == FMO_PREC_MIXED);
+  if (use_f) {   // FP32 copies of S and H0 for the FP32 iterations
+    NA_CK(launch_to_float(st, (long long)n * n, S, S32));
+    NA_CK(launch_to_float(st, (long long)n * n, H0, H32));
+  }
   NA_CK(launch_lowdin(st, 1, n, d_nm, S, use_f ? (void*)CTf : (void*)CTd, use_f ? (void*)W1f : (void*)W1d,
                       use_f ? (void*)Agf : (void*)Agd, use_f ? 1 : 0, 0, d_status));
   SccLaunch sl{};
   sl.nmers = d_nm; sl.order = d_order; sl.ft = ft; sl.xyz = xyz_dev; sl.elem = d_elem; sl.atom_sh0 = d_atom_sh0;
   sl.el = d_el; sl.g = g; sl.S = S; sl.H0 = H0; sl.gam = gam;
   sl.CTd = CTd; sl.W1d = W1d; sl.W2d = W2d; sl.Agd = Agd; sl.CTf = CTf; sl.W1f = W1f; sl.W2f = W2f; sl.Agf = Agf;
+  if (use_f) { sl.S32 = S32; sl.H32 = H32; }
   sl.phi = esp_dev;          // with zero monomer charges the ESP is exactly esp_dev
   sl.dq_mono = dq0;          // neutral guess, and nothing to subtract from the ESP
   sl.esp = espv; sl.dq = dqv; sl.eps = eps; sl.hist = hist;
