@@ -302,6 +302,120 @@ __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long lo
 }
 
 // ---------------------------------------------------------------------------
+// Block-level GEMM in double-float arithmetic, for products whose left
+// operand holds exact FP32 values and whose result is needed to FP64
+// accuracy: C[m][n] = sum_k A[arow(m)][k] * B[n][k], with A float (row arow(m)
+// = arow ? arow[m] : m, leading dimension lda), B double (leading dimension
+// ldb) and C double.  Each b is split on staging into b_hi = fl32(b) and
+// b_lo = fl32(b - b_hi) (b to ~2^-48 relative); a*b_hi is formed exactly as
+// p + e (p = fl32(a b_hi), e = fma(a, b_hi, -p)), a*b_lo is added to e, and
+// the running sum is kept as an unevaluated pair (hi, lo) by Knuth's
+// TwoSum on hi with the small parts accumulated in lo (renormalised after
+// every 16 terms).  The error is ~1e-14 relative to sum |a b| per output: FP64-grade accuracy from
+// ~10 FP32 instructions per term, where B300 issues FP64 FMAs at 1/64 of the
+// FP32 rate.  Same thread/tile layout as block_gemm_tile (TM x TN per thread,
+// BK = 16); smem: 3 * 16 * (16*max(TM,TN) + 1) floats.  Ends with __syncthreads().
+
+template <int TM, int TN>
+__device__ __forceinline__ void block_gemm_df_tile(int M, int N, int K, const float* __restrict__ A,
+                                                   const int* __restrict__ arow, long long lda,
+                                                   const double* __restrict__ B, long long ldb,
+                                                   double* __restrict__ C, long long ldc, float* smem) {
+  constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
+  constexpr int LDA = BM + 1, LDB = BN + 1;
+  float* As = smem;                 // [BK][LDA]
+  float* Bh = As + BK * LDA;        // [BK][LDB]
+  float* Bl = Bh + BK * LDB;        // [BK][LDB]
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += BM) {
+    for (int n0 = 0; n0 < N; n0 += BN) {
+      float hi[TM][TN], lo[TM][TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) { hi[i][j] = 0.f; lo[i][j] = 0.f; }
+      for (int k0 = 0; k0 < K; k0 += BK) {
+        // stage: 16 consecutive k of a row per 16 threads (coalesced)
+        for (int e = tid; e < BM * BK; e += kBlock) {
+          const int kk = e % BK, mm = e / BK, gm = m0 + mm, gk = k0 + kk;
+          float v = 0.f;
+          if (gm < M && gk < K) v = A[(long long)(arow ? arow[gm] : gm) * lda + gk];
+          As[kk * LDA + mm] = v;
+        }
+        for (int e = tid; e < BN * BK; e += kBlock) {
+          const int kk = e % BK, nn = e / BK, gn = n0 + nn, gk = k0 + kk;
+          float h = 0.f, l = 0.f;
+          if (gn < N && gk < K) {
+            const double b = B[(long long)gn * ldb + gk];
+            h = float(b);
+            l = float(b - double(h));
+          }
+          Bh[kk * LDB + nn] = h;
+          Bl[kk * LDB + nn] = l;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+          float a[TM], bh[TN], bl[TN];
+#pragma unroll
+          for (int i = 0; i < TM; ++i) a[i] = As[kk * LDA + ty * TM + i];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) { bh[j] = Bh[kk * LDB + tx * TN + j]; bl[j] = Bl[kk * LDB + tx * TN + j]; }
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+              // _rn intrinsics: never contracted into FMAs, so the
+              // error-free transformations stay exact
+              const float p = __fmul_rn(a[i], bh[j]);
+              float e = fmaf(a[i], bh[j], -p);
+              e = fmaf(a[i], bl[j], e);
+              const float s = __fadd_rn(hi[i][j], p);
+              const float bb = __fsub_rn(s, hi[i][j]);
+              const float err = __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+              hi[i][j] = s;
+              lo[i][j] = __fadd_rn(lo[i][j], __fadd_rn(err, e));
+            }
+        }
+        // renormalise once per slice (Fast2Sum, |lo| << |hi|): keeps lo, and
+        // so its own rounding, small
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            const float s = __fadd_rn(hi[i][j], lo[i][j]);
+            lo[i][j] = __fsub_rn(lo[i][j], __fsub_rn(s, hi[i][j]));
+            hi[i][j] = s;
+          }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int gm = m0 + ty * TM + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          const int gn = n0 + tx * TN + j;
+          if (gn < N) C[gm * ldc + gn] = double(hi[i][j]) + double(lo[i][j]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ inline void block_gemm_df(int M, int N, int K, const float* __restrict__ A, const int* __restrict__ arow,
+                                     long long lda, const double* __restrict__ B, long long ldb, double* __restrict__ C,
+                                     long long ldc, float* smem) {
+  const int tm = gemm_micro(M), tn = gemm_micro(N);
+  if (tm == 4 && tn == 4) block_gemm_df_tile<4, 4>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+  else if (tm == 4) block_gemm_df_tile<4, 5>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+  else if (tn == 4) block_gemm_df_tile<5, 4>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+  else block_gemm_df_tile<5, 5>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+}
+
+// ---------------------------------------------------------------------------
 // Block-level cyclic Jacobi eigensolver for a symmetric n x n matrix A
 // (row-major, leading dimension lda >= npad, padding row/column zero).
 // Parallel (round-robin) ordering: each round rotates npad/2 disjoint index

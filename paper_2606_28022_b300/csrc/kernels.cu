@@ -1188,14 +1188,21 @@ __device__ double fp64_energy_of_rows(const Nmer& nm, const SccArgs& ar, SccSmem
   __syncthreads();
   double* gemm = reinterpret_cast<double*>(sm.gemm);
   float* gf = reinterpret_cast<float*>(sm.gemm);
-  block_gemm<double>(no, n, n, Co, n, 1, Sm, n, 1, W, n, nullptr, nullptr, nullptr, gemm);   // W = C_o S
-  block_gemm<double>(no, n, n, Co, n, 1, Hm, n, 1, Y, n, nullptr, nullptr, nullptr, gemm);   // Y = C_o H0
+  // the rows are exact FP32 values: the three products with them run in
+  // double-float arithmetic (FP64-grade results from FP32 instructions)
+  block_gemm_df(no, n, n, ct32, sm.occ, n, Sm, n, W, n, gf);   // W = C_o S (S symmetric)
+  block_gemm_df(no, n, n, ct32, sm.occ, n, Hm, n, Y, n, gf);   // Y = C_o H0 (H0 symmetric)
   double err0 = 0.0;
   for (int step = 0; step < 2; ++step) {
-    block_gemm<double>(no, no, n, W, n, 1, Co, n, 1, M, no, nullptr, nullptr, nullptr, gemm);   // M = C_o S C_o^T
+    if (step == 0) block_gemm_df(no, no, n, ct32, sm.occ, n, W, n, M, no, gf);   // M = C_o W^T = C_o S C_o^T
+    else block_gemm<double>(no, no, n, W, n, 1, Co, n, 1, M, no, nullptr, nullptr, nullptr, gemm);
     const double err = max_dev_from_identity(M, no, no, sm.red, wf1);
     if (step == 0) err0 = err;
-    else if (err0 <= 1e-8) break;   // one step left ~err0^2: done
+    if (step == 0 && err0 <= 1e-6) {
+      // one Newton-Schulz step leaves ~err0^2 plus the FP32 rounding of the
+      // correction (~1e-7 err0): below 1e-12, nothing for a second step
+      step = 1;
+    }
     double* X[3] = {Co, W, Y};
     for (int x = 0; x < 3; ++x) {
       block_gemm<float, double>(no, n, no, wf1, no, 1, X[x], 1, n, wf2, n, nullptr, nullptr, nullptr, gf);
