@@ -302,11 +302,11 @@ __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long lo
 }
 
 // ---------------------------------------------------------------------------
-// Block-level GEMM in double-float arithmetic, for products whose left
-// operand holds exact FP32 values and whose result is needed to FP64
-// accuracy: C[m][n] = sum_k A[arow(m)][k] * B[n][k], with A float (row arow(m)
-// = arow ? arow[m] : m, leading dimension lda), B double (leading dimension
-// ldb) and C double.  Each b is split on staging into b_hi = fl32(b) and
+// Block-level GEMM in double-float arithmetic, for products whose result is
+// needed to FP64 accuracy: C[m][n] = sum_k A[arow(m)][k] * B[n][k], with A
+// float (exact FP32 values) or double (row arow(m) = arow ? arow[m] : m,
+// leading dimension lda), B double (leading dimension ldb) and C double.
+// A double A is split like b below and a_lo*b_hi joins the small terms.  Each b is split on staging into b_hi = fl32(b) and
 // b_lo = fl32(b - b_hi) (b to ~2^-48 relative); a*b_hi is formed exactly as
 // p + e (p = fl32(a b_hi), e = fma(a, b_hi, -p)), a*b_lo is added to e, and
 // the running sum is kept as an unevaluated pair (hi, lo) by Knuth's
@@ -314,18 +314,20 @@ __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long lo
 // every 16 terms).  The error is ~1e-14 relative to sum |a b| per output: FP64-grade accuracy from
 // ~10 FP32 instructions per term, where B300 issues FP64 FMAs at 1/64 of the
 // FP32 rate.  Same thread/tile layout as block_gemm_tile (TM x TN per thread,
-// BK = 16); smem: 3 * 16 * (16*max(TM,TN) + 1) floats.  Ends with __syncthreads().
+// BK = 16); smem: 4 * 16 * (16*max(TM,TN) + 1) floats (kGemmSmemElems doubles).  Ends with __syncthreads().
 
-template <int TM, int TN>
-__device__ __forceinline__ void block_gemm_df_tile(int M, int N, int K, const float* __restrict__ A,
+template <int TM, int TN, typename TA>
+__device__ __noinline__ void block_gemm_df_tile(int M, int N, int K, const TA* __restrict__ A,
                                                    const int* __restrict__ arow, long long lda,
                                                    const double* __restrict__ B, long long ldb,
                                                    double* __restrict__ C, long long ldc, float* smem) {
   constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
   constexpr int LDA = BM + 1, LDB = BN + 1;
+  constexpr bool kSplitA = sizeof(TA) == 8;   // A in FP64: split like B
   float* As = smem;                 // [BK][LDA]
   float* Bh = As + BK * LDA;        // [BK][LDB]
   float* Bl = Bh + BK * LDB;        // [BK][LDB]
+  float* Al = Bl + BK * LDB;        // [BK][LDA] (kSplitA only)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   for (int m0 = 0; m0 < M; m0 += BM) {
@@ -339,9 +341,14 @@ __device__ __forceinline__ void block_gemm_df_tile(int M, int N, int K, const fl
         // stage: 16 consecutive k of a row per 16 threads (coalesced)
         for (int e = tid; e < BM * BK; e += kBlock) {
           const int kk = e % BK, mm = e / BK, gm = m0 + mm, gk = k0 + kk;
-          float v = 0.f;
-          if (gm < M && gk < K) v = A[(long long)(arow ? arow[gm] : gm) * lda + gk];
+          float v = 0.f, vl = 0.f;
+          if (gm < M && gk < K) {
+            const TA a = A[(long long)(arow ? arow[gm] : gm) * lda + gk];
+            v = float(a);
+            if constexpr (kSplitA) vl = float(double(a) - double(v));
+          }
           As[kk * LDA + mm] = v;
+          if constexpr (kSplitA) Al[kk * LDA + mm] = vl;
         }
         for (int e = tid; e < BN * BK; e += kBlock) {
           const int kk = e % BK, nn = e / BK, gn = n0 + nn, gk = k0 + kk;
@@ -357,9 +364,12 @@ __device__ __forceinline__ void block_gemm_df_tile(int M, int N, int K, const fl
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
-          float a[TM], bh[TN], bl[TN];
+          float a[TM], al[TM], bh[TN], bl[TN];
 #pragma unroll
-          for (int i = 0; i < TM; ++i) a[i] = As[kk * LDA + ty * TM + i];
+          for (int i = 0; i < TM; ++i) {
+            a[i] = As[kk * LDA + ty * TM + i];
+            if constexpr (kSplitA) al[i] = Al[kk * LDA + ty * TM + i];
+          }
 #pragma unroll
           for (int j = 0; j < TN; ++j) { bh[j] = Bh[kk * LDB + tx * TN + j]; bl[j] = Bl[kk * LDB + tx * TN + j]; }
 #pragma unroll
@@ -371,6 +381,7 @@ __device__ __forceinline__ void block_gemm_df_tile(int M, int N, int K, const fl
               const float p = __fmul_rn(a[i], bh[j]);
               float e = fmaf(a[i], bh[j], -p);
               e = fmaf(a[i], bl[j], e);
+              if constexpr (kSplitA) e = fmaf(al[i], bh[j], e);
               const float s = __fadd_rn(hi[i][j], p);
               const float bb = __fsub_rn(s, hi[i][j]);
               const float err = __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(s, bb)), __fsub_rn(p, bb));
@@ -405,14 +416,15 @@ __device__ __forceinline__ void block_gemm_df_tile(int M, int N, int K, const fl
   __syncthreads();
 }
 
-__device__ inline void block_gemm_df(int M, int N, int K, const float* __restrict__ A, const int* __restrict__ arow,
+template <typename TA>
+__device__ inline void block_gemm_df(int M, int N, int K, const TA* __restrict__ A, const int* __restrict__ arow,
                                      long long lda, const double* __restrict__ B, long long ldb, double* __restrict__ C,
                                      long long ldc, float* smem) {
   const int tm = gemm_micro(M), tn = gemm_micro(N);
-  if (tm == 4 && tn == 4) block_gemm_df_tile<4, 4>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
-  else if (tm == 4) block_gemm_df_tile<4, 5>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
-  else if (tn == 4) block_gemm_df_tile<5, 4>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
-  else block_gemm_df_tile<5, 5>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+  if (tm == 4 && tn == 4) block_gemm_df_tile<4, 4, TA>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+  else if (tm == 4) block_gemm_df_tile<4, 5, TA>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+  else if (tn == 4) block_gemm_df_tile<5, 4, TA>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
+  else block_gemm_df_tile<5, 5, TA>(M, N, K, A, arow, lda, B, ldb, C, ldc, smem);
 }
 
 // ---------------------------------------------------------------------------

@@ -984,8 +984,21 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   T* gemm = reinterpret_cast<T*>(sm.gemm);
   mark(0);
   // U = CT F  (W2), then A = U CT^T: the Fock matrix in the current MO basis
-  block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
-  block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, nullptr, gemm);
+  if constexpr (sizeof(T) == 8) {
+    if (f_ct) {
+      // FP64 iteration of a mixed-precision solve: double-float products
+      // (FP64-grade, on the FP32 pipe); F is symmetric, so its rows serve as B
+      float* gdf = reinterpret_cast<float*>(sm.gemm);
+      block_gemm_df<double>(n, n, n, pp.CT, nullptr, n, pp.W1, n, pp.W2, n, gdf);
+      block_gemm_df<double>(n, n, n, pp.W2, nullptr, n, pp.CT, n, pp.A, pp.lda, gdf);
+    } else {
+      block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
+      block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, nullptr, gemm);
+    }
+  } else {
+    block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
+    block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, nullptr, gemm);
+  }
   mark(1);
   int nocc = 0;
   double mts = 0.0;
@@ -1141,10 +1154,11 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
 __device__ void reortho_handover(const Nmer& nm, const SccArgs& ar, SccSmem& sm, PrecPtrs<double> pd,
                                  const float* ct32, float* wf1, float* wf2) {
   const int n = nm.n;
-  double* gemm = reinterpret_cast<double*>(sm.gemm);
   const double* Sm = ar.S + nm.mat;
-  block_gemm<double>(n, n, n, pd.CT, n, 1, Sm, n, 1, pd.W2, n, nullptr, nullptr, nullptr, gemm);   // V = CT S
-  block_gemm<double>(n, n, n, pd.W2, n, 1, pd.CT, n, 1, pd.W1, n, nullptr, nullptr, nullptr, gemm);  // M
+  float* gdf = reinterpret_cast<float*>(sm.gemm);
+  // double-float products (FP64-grade); the rows are exact FP32 values
+  block_gemm_df<float>(n, n, n, ct32, nullptr, n, Sm, n, pd.W2, n, gdf);     // V = CT S (S symmetric)
+  block_gemm_df<double>(n, n, n, pd.W2, nullptr, n, pd.CT, n, pd.W1, n, gdf);  // M = V CT^T
   const double err = max_dev_from_identity(pd.W1, n, n, sm.red, wf1);
   float* gf = reinterpret_cast<float*>(sm.gemm);
   block_gemm<float>(n, n, n, wf1, n, 1, ct32, 1, n, wf2, n, nullptr, nullptr, nullptr, gf);   // (M - I) CT
@@ -1190,11 +1204,11 @@ __device__ double fp64_energy_of_rows(const Nmer& nm, const SccArgs& ar, SccSmem
   float* gf = reinterpret_cast<float*>(sm.gemm);
   // the rows are exact FP32 values: the three products with them run in
   // double-float arithmetic (FP64-grade results from FP32 instructions)
-  block_gemm_df(no, n, n, ct32, sm.occ, n, Sm, n, W, n, gf);   // W = C_o S (S symmetric)
-  block_gemm_df(no, n, n, ct32, sm.occ, n, Hm, n, Y, n, gf);   // Y = C_o H0 (H0 symmetric)
+  block_gemm_df<float>(no, n, n, ct32, sm.occ, n, Sm, n, W, n, gf);   // W = C_o S (S symmetric)
+  block_gemm_df<float>(no, n, n, ct32, sm.occ, n, Hm, n, Y, n, gf);   // Y = C_o H0 (H0 symmetric)
   double err0 = 0.0;
   for (int step = 0; step < 2; ++step) {
-    if (step == 0) block_gemm_df(no, no, n, ct32, sm.occ, n, W, n, M, no, gf);   // M = C_o W^T = C_o S C_o^T
+    if (step == 0) block_gemm_df<float>(no, no, n, ct32, sm.occ, n, W, n, M, no, gf);   // M = C_o W^T = C_o S C_o^T
     else block_gemm<double>(no, no, n, W, n, 1, Co, n, 1, M, no, nullptr, nullptr, nullptr, gemm);
     const double err = max_dev_from_identity(M, no, no, sm.red, wf1);
     if (step == 0) err0 = err;
