@@ -428,6 +428,54 @@ __device__ inline void block_gemm_df(int M, int N, int K, const TA* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Solve (a + w0sq I) g = c for the Broyden coefficients (m x m, m <= kHist,
+// a row-major) by Gauss-Jordan elimination with partial pivoting on one
+// warp: lane r holds row r (the right-hand side in column kHist, columns
+// m..kHist-1 zero), the rows are updated in parallel.  Pivot choice (the
+// first row of largest |M[r][col]|), factors, updates and the final division
+// are those of the serial textbook loop, element by element, so the result is
+// the same; one thread doing it alone waits ~60 cycles on every dependent
+// FP64 instruction, on B300's FP64 pipe.  All 32 lanes of the warp call it.
+static __device__ __noinline__ void warp_gj_solve(int m, const double* a, const double* c, double w0sq, double* g) {
+  const int lane = threadIdx.x & 31;
+  double row[kHist + 1];
+#pragma unroll
+  for (int j = 0; j < kHist; ++j) row[j] = (lane < m && j < m) ? a[lane * m + j] + (lane == j ? w0sq : 0.0) : 0.0;
+  row[kHist] = (lane < m) ? c[lane] : 0.0;
+#pragma unroll
+  for (int col = 0; col < kHist; ++col) {
+    if (col >= m) break;
+    double v = (lane >= col && lane < m) ? fabs(row[col]) : -1.0;
+    int idx = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    const int piv = idx;
+    if (piv != col) {
+      const int src = (lane == col) ? piv : (lane == piv ? col : lane);
+#pragma unroll
+      for (int j = 0; j <= kHist; ++j) row[j] = __shfl_sync(0xffffffffu, row[j], src);
+    }
+    double prow[kHist + 1];
+#pragma unroll
+    for (int j = 0; j <= kHist; ++j) prow[j] = __shfl_sync(0xffffffffu, row[j], col);
+    if (lane < m && lane != col) {
+      const double f = row[col] / prow[col];
+#pragma unroll
+      for (int j = col; j <= kHist; ++j) row[j] -= f * prow[j];
+    }
+  }
+  double diag = 1.0;
+#pragma unroll
+  for (int j = 0; j < kHist; ++j)
+    if (j == lane) diag = row[j];
+  if (lane < m) g[lane] = row[kHist] / diag;
+}
+
+// ---------------------------------------------------------------------------
 // Block-level cyclic Jacobi eigensolver for a symmetric n x n matrix A
 // (row-major, leading dimension lda >= npad, padding row/column zero).
 // Parallel (round-robin) ordering: each round rotates npad/2 disjoint index

@@ -775,26 +775,8 @@ __device__ void broyden_step(int nsh, int it, double* hist, SccSmem& sm, int& hc
       if (lane == 0) { if (e < m * m) a[e] = s; else c[e - m * m] = s; }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      // solve (w0^2 I + a) g = c, Gaussian elimination with partial pivoting
-      double M[kHist][kHist + 1];
-      for (int i = 0; i < m; ++i) {
-        for (int j = 0; j < m; ++j) M[i][j] = a[i * m + j] + (i == j ? w0 * w0 : 0.0);
-        M[i][m] = c[i];
-      }
-      for (int col = 0; col < m; ++col) {
-        int piv = col;
-        for (int r = col + 1; r < m; ++r) if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
-        if (piv != col) for (int j = 0; j <= m; ++j) { double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
-        const double d = M[col][col];
-        for (int r = 0; r < m; ++r) {
-          if (r == col) continue;
-          const double f = M[r][col] / d;
-          for (int j = col; j <= m; ++j) M[r][j] -= f * M[col][j];
-        }
-      }
-      for (int i = 0; i < m; ++i) gv[i] = M[i][m] / M[i][i];
-    }
+    // solve (w0^2 I + a) g = c, Gaussian elimination with partial pivoting
+    if (threadIdx.x < 32) warp_gj_solve(m, a, c, w0 * w0, gv);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
@@ -1755,7 +1737,7 @@ struct MixState {
   double gram[kHist * kHist];   // dF_k . dF_l by history slot (each pair formed once)
 };
 
-__global__ void global_mix_kernel(int n, double* __restrict__ x, const double* __restrict__ xo, int nf,
+__global__ void __launch_bounds__(1024) global_mix_kernel(int n, double* __restrict__ x, const double* __restrict__ xo, int nf,
                                   const double* __restrict__ e, double* __restrict__ hist, MixState* st,
                                   double alpha, double w0, double tol, double etol, int allow_converge) {
   __shared__ double red[32];
@@ -1841,25 +1823,7 @@ __global__ void global_mix_kernel(int n, double* __restrict__ x, const double* _
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && m > 0) {
-    double M[kHist][kHist + 1];
-    for (int i = 0; i < m; ++i) {
-      for (int j = 0; j < m; ++j) M[i][j] = a[i * m + j] + (i == j ? w0 * w0 : 0.0);
-      M[i][m] = c[i];
-    }
-    for (int col = 0; col < m; ++col) {
-      int piv = col;
-      for (int r = col + 1; r < m; ++r) if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
-      if (piv != col) for (int j = 0; j <= m; ++j) { const double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
-      const double d = M[col][col];
-      for (int r = 0; r < m; ++r) {
-        if (r == col) continue;
-        const double f = M[r][col] / d;
-        for (int j = col; j <= m; ++j) M[r][j] -= f * M[col][j];
-      }
-    }
-    for (int i = 0; i < m; ++i) gv[i] = M[i][m] / M[i][i];
-  }
+  if (threadIdx.x < 32 && m > 0) warp_gj_solve(m, a, c, w0 * w0, gv);   // (w0^2 I + a) g = c
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double v = x[i] + alpha * (xo[i] - x[i]);
