@@ -395,7 +395,7 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
   } else {
     CK(launch_lowdin(st, nn, P.max_n, P.d_nm.as<Nmer>(), P.S.as<double>(),
                      use_f ? P.CTf.p : P.CTd.p, use_f ? P.W1f.p : P.W1d.p, use_f ? P.Agf.p : P.Agd.p,
-                     use_f ? 1 : 0, a_in, P.status.as<int>()));
+                     use_f ? 1 : 0, a_in, P.status.as<int>(), use_f ? P.W2f.p : nullptr));
   }
   return FMO_OK;
 }

@@ -358,14 +358,20 @@ __global__ void gamma_kernel(const Nmer* __restrict__ nmers, FragTab ft, const d
 }
 
 // ---------------------------------------------------------------------------
-// Loewdin orthogonaliser X = S^{-1/2} of each n-mer (Jacobi eigensolve of S),
-// written as the starting eigenvector rows CT = X (X is symmetric).
+// Loewdin orthogonaliser X = S^{-1/2} of each n-mer, written as the starting
+// eigenvector rows CT = X (X is symmetric): coupled Newton-Schulz steps in
+// FP32 when a spare n x n buffer W2 is given, else (FP64, or no convergence)
+// from a Jacobi eigensolve of S.
+
+template <typename T>
+__device__ double max_dev_from_identity(const T* X, int m, int n, double* red, float* out = nullptr);
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) lowdin_kernel(const Nmer* __restrict__ nmers,
                                                         const double* __restrict__ S, T* __restrict__ CT,
                                                         T* __restrict__ W, T* __restrict__ Ag,
-                                                        int a_in_smem, double tol, int* __restrict__ status) {
+                                                        int a_in_smem, double tol, int* __restrict__ status,
+                                                        T* __restrict__ W2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Nmer nm = nmers[blockIdx.x];
   const int n = nm.n, npad = nm.npad;
@@ -387,6 +393,52 @@ __global__ void __launch_bounds__(kBlock) lowdin_kernel(const Nmer* __restrict__
   const double* Sm = S + nm.mat;
   T* CTm = CT + nm.mat;
   T* Wm = W + nm.mat;
+  if (W2) {
+    // S^-1/2 by the coupled Newton-Schulz iteration (Higham, Functions of
+    // Matrices, Sec. 6.3): Y0 = S/c, Z0 = I, T = (3I - Z Y)/2, Y <- Y T,
+    // Z <- T Z; Y -> (S/c)^1/2 and Z -> (S/c)^-1/2 while ||I - S/c|| < 1,
+    // which c = max row sum of |S| (>= the largest eigenvalue) ensures.
+    // Three GEMMs per step, ~10 steps for the condition numbers of these
+    // bases, against a full Jacobi eigen-solve.  Ends at FP32 rounding (the
+    // residual max |ZY - I| stops halving); the SCC's cold start restores
+    // S-orthonormality of the rows to FP32 anyway.  Not converged: Jacobi.
+    double rs = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double t = 0.0;
+      for (int j = 0; j < n; ++j) t += fabs(Sm[(long long)i * n + j]);
+      rs = fmax(rs, t);
+    }
+    const double c = block_max(rs, red);
+    T* Y = Wm;
+    T* Z = CTm;
+    T* X = W2 + nm.mat;   // spare
+    T* P = A;             // n x n, leading dimension n
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      Y[e] = T(Sm[e] / c);
+      Z[e] = T((e / n) == (e % n) ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    double prev = 1e30, err = 1e30;
+    for (int it = 0; it < 60; ++it) {
+      block_gemm<T>(n, n, n, Z, n, 1, Y, 1, n, P, n, nullptr, nullptr, nullptr, gemm);   // Z Y
+      err = max_dev_from_identity(P, n, n, red);
+      if (err < 1e-6 || (err < 1e-3 && err > 0.5 * prev)) break;
+      prev = err;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+        P[e] = T((e / n) == (e % n) ? 1.5 : 0.0) - T(0.5) * P[e];
+      __syncthreads();
+      block_gemm<T>(n, n, n, Y, n, 1, P, 1, n, X, n, nullptr, nullptr, nullptr, gemm);   // Y T
+      T* t = Y; Y = X; X = t;
+      block_gemm<T>(n, n, n, P, n, 1, Z, 1, n, X, n, nullptr, nullptr, nullptr, gemm);   // T Z
+      t = Z; Z = X; X = t;
+    }
+    if (err < 1e-3) {
+      const T f = T(1.0 / sqrt(c));
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) CTm[e] = Z[e] * f;   // Z may be CTm itself
+      __syncthreads();
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < npad * npad; e += blockDim.x) {
     const int i = e / npad, j = e % npad;
     A[e] = (i < n && j < n) ? T(Sm[(long long)i * n + j]) : T(0);
@@ -844,7 +896,7 @@ __device__ __forceinline__ double recip<double>(double d) {
 // max |X - I| over an m x n row-major matrix (a warp per row); optionally
 // stores X - I in FP32 into out.  Block-uniform result.
 template <typename T>
-__device__ double max_dev_from_identity(const T* X, int m, int n, double* red, float* out = nullptr) {
+__device__ double max_dev_from_identity(const T* X, int m, int n, double* red, float* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double err = 0.0;
   for (int i = wid; i < m; i += nw) {
@@ -1972,18 +2024,18 @@ static size_t lowdin_smem(int max_n, int elem_bytes, int a_in_smem) {
 }
 
 cudaError_t launch_lowdin(cudaStream_t st, int n_nmer, int max_n, const Nmer* nmers, const double* S,
-                          void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status) {
+                          void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status, void* W2) {
   if (n_nmer == 0) return cudaSuccess;
   if (use_float) {
     const size_t sb = lowdin_smem(max_n, 4, a_in_smem);
     cudaFuncSetAttribute(lowdin_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     lowdin_kernel<float><<<n_nmer, kBlock, sb, st>>>(nmers, S, (float*)CT, (float*)W, (float*)Ag, a_in_smem,
-                                                     1e-7, status);
+                                                     1e-7, status, (float*)W2);
   } else {
     const size_t sb = lowdin_smem(max_n, 8, a_in_smem);
     cudaFuncSetAttribute(lowdin_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     lowdin_kernel<double><<<n_nmer, kBlock, sb, st>>>(nmers, S, (double*)CT, (double*)W, (double*)Ag,
-                                                      a_in_smem, 1e-14, status);
+                                                      a_in_smem, 1e-14, status, nullptr);
   }
   LAUNCH_CHECK();
   return cudaSuccess;

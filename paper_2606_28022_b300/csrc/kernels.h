@@ -99,7 +99,8 @@ cudaError_t launch_gamma(cudaStream_t st, int n_nmer, int max_nsh, const Nmer* n
                          const double* xyz, const int* elem, const int* sh_atom, const double* sh_inv_eta,
                          GParams g, double* gam);
 cudaError_t launch_lowdin(cudaStream_t st, int n_nmer, int max_n, const Nmer* nmers, const double* S,
-                          void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status);
+                          void* CT, void* W, void* Ag, int use_float, int a_in_smem, int* status,
+                          void* W2 = nullptr);   // W2: spare n x n per n-mer (FP32: Newton-Schulz start)
 size_t scc_smem_size(int max_n, int max_nsh, int max_nat, int a_bytes);
 cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L);
 cudaError_t launch_warm_start(cudaStream_t st, int n_nmer, const Nmer* nmers, const Nmer* mono, const float* mono_ct,
