@@ -175,11 +175,11 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
       int aoB = s_ao0[bj];
       for (int sb = 0; sb < EB.nsh; ++sb) {
         const int lb = EB.l[sb];
-        double blk[3][3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u)
-#pragma unroll
-          for (int v = 0; v < 3; ++v) blk[u][v] = 0.0;
+        // PA = (b/p) d and PB = -(a/p) d are multiples of the bond vector d,
+        // so each block is d-weighted sums of two scalars over the
+        // primitive pairs: ss: sum s00; ps: d_u sum (b/p) s00; sp: -d_v sum
+        // (a/p) s00; pp: -d_u d_v sum (a/p)(b/p) s00 + delta_uv sum 1/(2p) s00
+        double t0 = 0.0, t1 = 0.0;
         for (int pa = 0; pa < EA.nprim[sa]; ++pa) {
           for (int pb = 0; pb < EB.nprim[sb]; ++pb) {
             PrimPair q;
@@ -196,26 +196,29 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
             const double xe = q.abp * r2;
             if (xe > kPrimScreen) continue;   // exp(-xe) < 1e-20
             const double s00 = q.pref * exp(-xe);
-            const double ip = q.ip;
-            const double PA[3] = {q.bp * dx, q.bp * dy, q.bp * dz};
-            const double PB[3] = {-q.ap * dx, -q.ap * dy, -q.ap * dz};
             if (la == 0 && lb == 0) {
-              blk[0][0] += s00;
+              t0 += s00;
             } else if (la == 1 && lb == 0) {
-#pragma unroll
-              for (int u = 0; u < 3; ++u) blk[u][0] += PA[u] * s00;
+              t0 = fma(q.bp, s00, t0);
             } else if (la == 0 && lb == 1) {
-#pragma unroll
-              for (int v = 0; v < 3; ++v) blk[0][v] += PB[v] * s00;
+              t0 = fma(q.ap, s00, t0);
             } else {
-#pragma unroll
-              for (int u = 0; u < 3; ++u)
-#pragma unroll
-                for (int v = 0; v < 3; ++v)
-                  blk[u][v] += (PA[u] * PB[v] + (u == v ? 0.5 * ip : 0.0)) * s00;
+              t0 = fma(q.ap * q.bp, s00, t0);
+              t1 = fma(q.ip, s00, t1);
             }
           }
         }
+        const double d[3] = {dx, dy, dz};
+        double blk[3][3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            if (la == 0 && lb == 0) blk[u][v] = t0;
+            else if (la == 1 && lb == 0) blk[u][v] = d[u] * t0;
+            else if (la == 0 && lb == 1) blk[u][v] = -d[v] * t0;
+            else blk[u][v] = -d[u] * d[v] * t0 + (u == v ? 0.5 * t1 : 0.0);
+          }
         const int nu = 2 * la + 1, nv = 2 * lb + 1;
         double fac = 0.0;
         const double hB = EB.h[sb] * (1.0 + EB.kcn[sb] * cn[gb]);
