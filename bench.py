@@ -41,7 +41,7 @@ FP64_PEAK_TFLOPS = 1.25                                 # nominal B300 FP64 rate
 # DRAM bytes (read + write) of the dimer-pass SCC launch of this workload, from
 # one ncu capture of the current kernel (profiles/scc_kernel_anthracene128_fmo2.md);
 # None whenever the kernel has changed since that capture
-DIMER_SCC_DRAM_BYTES = 543883776 + 535409920
+DIMER_SCC_DRAM_BYTES = 531186944 + 527815168
 
 
 def workload(rank: int, n_mol: int = 128):
