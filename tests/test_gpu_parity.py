@@ -146,6 +146,9 @@ def test_anthracene32_monomer_loop_fp64_and_mixed(gpu, params):
     assert np.max(np.abs(mono.shell_dq - np.concatenate(ref.dq_mono))) < DQ
     gpu.run(fmo.options(level=1, precision="mixed"))
     assert abs(gpu.energies()[0] - ref.e_fmo1) < E_TOT_MIXED
+    # mixed-precision monomers finish in FP64-grade iterations (double-float
+    # products on the FP32 pipe): their energies meet the FP64 bar
+    assert np.max(np.abs(gpu.monomers().energy - ref.e_mono)) < E_FRAG
 
 
 def test_anthracene4_mixed_nmer_finish_iterate(gpu, params, anthracene4):
