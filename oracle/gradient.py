@@ -4,13 +4,17 @@ TEST INFRASTRUCTURE ONLY (see oracle/xtb.py): the slow, plain reference for
 the analytic-gradient rows.  It differentiates the energy that oracle/xtb.py
 computes, term by term, at the converged density (Sec. 2.4, GFN1-xTB energy
 gradient):
-  Eq. 26 (the single-system gradient): P dH0 + W dS + 1/2 dq dq dgamma
-          + dE_rep, with the energy-weighted density of Eq. 27 inside W
-  Eq. 28  dH0 = H dS + S dH: the S part joins the W term; the rest is the
+  Eq. 23  the single-system gradient: P dH0 + W dS + 1/2 dq dq dgamma
+          + dE_rep
+  Eq. 24  W with the energy-weighted density, the shell shifts and the
+          third-order term
+  Eq. 25  dH0 = H dS + S dH: the S part joins the W term; the rest is the
           derivative of the distance polynomial Pi (Eq. 9) and of the
           CN-dependent levels (Eq. 10)
-  Eqs. 29-31  coordination-number gradient: F_A dCN_A with F_A the
+  Eqs. 26-28  coordination number, its gradient F_A dCN_A, and F_A, the
           sensitivity of the energy to CN_A
+(equation numbers as in oracle/fmo.py: the halogen-bond expression is not
+counted)
 Because the Fermi-smeared SCC energy E - TS is stationary in the orbitals and
 occupations at convergence, these explicit terms are the whole gradient of a
 system in no external potential; finite differences of xtb.single_point pin
@@ -22,11 +26,22 @@ exp(-mu R^2), PA = -(b/p) R and PB = (a/p) R.
 READING C-18: the CN counting function is cut at cn_cutoff (READING C-3), so
 the gradient is that of the cut sum (no pair within the cut contributes a
 derivative at the cut itself).
+
+fmo_gradient is the FMO gradient by its definition: central differences of
+the oracle's FMO1/2/3 energy (oracle/fmo.py) in every coordinate.  It is the
+reference the analytic FMO gradient (explicit terms plus the self-consistent
+Z-vector response of Sec. 2.4) has to reach; slow (6 N_atoms FMO runs), for
+small systems.  Two exact identities pin it to the analytic single-system
+gradient: one fragment (E_FMO = E), and FMO2 of two fragments with an SCC
+dimer (E_FMO2 = E of the whole system).
 """
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 
+from . import fmo as ofmo
 from . import xtb
 
 
@@ -122,7 +137,7 @@ def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) ->
     at = b.ao_atom
     P = res.P
     S = res.S
-    Wt = (res.C * (res.occ * res.eps)) @ res.C.T                  # Eq. 27
+    Wt = (res.C * (res.occ * res.eps)) @ res.C.T                  # energy-weighted density (Eq. 24)
     gam = xtb.gamma_matrix(Z, xyz, params, b)
     g3 = xtb.atom_param(Z, params, "gamma3")
     dq = res.dq
@@ -155,7 +170,7 @@ def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) ->
     Hpref = np.where(off, kab * kll * hbar * fen * Pi, 0.0)           # H0 = Hpref S off the atom blocks
 
     grad = np.zeros((n_at, 3))
-    # (1) every S-dependence: P Hpref + 1/2 (sigma_mu + sigma_nu) P - W~ (Eqs. 26-28)
+    # (1) every S-dependence: P Hpref + 1/2 (sigma_mu + sigma_nu) P - W~ (Eqs. 23-25)
     dS = overlap_derivative(Z, xyz, params, b)
     Mw = np.where(off, P * Hpref + 0.5 * (sig_ao[:, None] + sig_ao[None, :]) * P - Wt, 0.0)
     grad += np.einsum("kcij,ij->kc", dS, Mw)
@@ -169,7 +184,7 @@ def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) ->
     for k in range(n_at):
         grad[k] += pair[at == k].sum(axis=(0, 1))
         grad[k] -= pair[:, at == k].sum(axis=(0, 1))
-    # (3) CN-dependent levels (Eqs. 10, 29-31): F_A = dE/dCN_A
+    # (3) CN-dependent levels (Eqs. 10, 26-28): F_A = dE/dCN_A
     dh = h_l * k_cn                                                    # dh_l / dCN of the shell's atom
     dh_ao = dh[sh]
     F = np.zeros(n_at)
@@ -180,7 +195,7 @@ def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) ->
     np.add.at(F, at, (Hcn * dh_ao[None, :]).sum(axis=0))
     dcn = cn_derivative(Z, xyz, params)
     grad += np.einsum("a,akc->kc", F, dcn)
-    # (4) the Coulomb kernel at fixed charges: 1/2 sum dq_s dq_t dgamma_st (Eq. 26)
+    # (4) the Coulomb kernel at fixed charges: 1/2 sum dq_s dq_t dgamma_st (Eq. 23)
     eta = xtb.shell_hardness(Z, b, params)
     sa = b.sh_atom
     for s in range(b.n_sh):
@@ -208,3 +223,25 @@ def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) ->
             grad[a] += de * rv / r
             grad[c] -= de * rv / r
     return grad
+
+
+def fmo_gradient(system, params, opts=None, h=1e-4) -> np.ndarray:
+    """dE_FMO/dxyz (n_atoms x 3) by central differences of the oracle's FMO
+    energy at the level opts.level, converged to 1e-12."""
+    opts = ofmo.FMOOptions() if opts is None else opts
+    opts = dataclasses.replace(opts, scc_tol=1e-12, e_tol=1e-13, outer_tol=1e-12)
+    key = {1: "e_fmo1", 2: "e_fmo2", 3: "e_fmo3"}[opts.level]
+
+    def energy(xyz):
+        return getattr(ofmo.fmo(dataclasses.replace(system, xyz=xyz), params, opts), key)
+
+    xyz0 = np.asarray(system.xyz, dtype=np.float64)
+    g = np.zeros_like(xyz0)
+    for k in range(len(xyz0)):
+        for c in range(3):
+            xp = xyz0.copy()
+            xp[k, c] += h
+            xm = xyz0.copy()
+            xm[k, c] -= h
+            g[k, c] = (energy(xp) - energy(xm)) / (2.0 * h)
+    return g

@@ -14,8 +14,8 @@ Every function follows one passage of the paper (Einsele & Mitric, FMO-xTB):
   Eqs. 8-10 zeroth-order Hamiltonian H0, polynomial factor Pi, CN-dependent
           levels
   Eq. 11  repulsion energy
-  Eq. 16 (CN definition, gradient section) coordination number
-  Eq. 24 (embedding potential V^I) the ESP term of the Fock matrix
+  Eq. 26 (CN definition, gradient section) coordination number
+  Eq. 21 (embedding potential V^I) the ESP term of the Fock matrix
 Readings of passages the paper leaves open are marked READING and listed in
 the design notes.  Units: bohr, Hartree; charges in electrons
 (dq = population - reference occupation, READING C-6).
@@ -364,7 +364,7 @@ def n_electrons(Z, params, charge=0.0) -> float:
 class SCCProblem:
     """The fixed matrices of one SCC solve (S, H0, gamma, X = S^-1/2, ...) and
     the map from input shell charges to the output density and energy: one
-    iteration of the SCC loop (Eqs. 2, 3, 6, 7 and the ESP of Eq. 24)."""
+    iteration of the SCC loop (Eqs. 2, 3, 6, 7 and the ESP of Eq. 21)."""
 
     def __init__(self, Z, xyz, params, cn, esp=None, charge=0.0, extra_fock=None, n_el=None, q0=None,
                  rep_mask=None):
@@ -425,7 +425,7 @@ def scc(Z, xyz, params, cn, esp=None, guess=None, charge=0.0, tol=1e-10, e_tol=1
 
     cn          coordination numbers of these atoms (taken from the whole
                 system in FMO: the CN sum runs over the supersystem)
-    esp         per-shell external potential (ESP^I_mu) of Eq. 24; enters the
+    esp         per-shell external potential (ESP^I_mu) of Eq. 21; enters the
                 Fock matrix as 1/2 S (esp_mu + esp_nu)
     extra_fock  an AO matrix added to F and kept out of the energy (the HOP
                 projector)

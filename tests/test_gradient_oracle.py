@@ -6,6 +6,7 @@ translation and rotation invariance of an isolated system's energy."""
 import numpy as np
 import pytest
 
+from oracle import fmo as ofmo
 from oracle import gradient, xtb
 from paper_2606_28022_b300.inputs import geometry as G
 
@@ -69,3 +70,23 @@ def test_gradient_is_translation_and_rotation_invariant(params):
     assert np.max(np.abs(g.sum(axis=0))) < 1e-12                 # no net force
     assert np.max(np.abs(np.cross(a.xyz, g).sum(axis=0))) < 1e-11  # no net torque
     assert np.abs(g).max() > 1e-3
+
+
+def test_fmo_gradient_one_fragment_equals_scc_gradient(params, water64):
+    s = water64.subsystem([5])
+    g_fmo = gradient.fmo_gradient(s, params, ofmo.FMOOptions(level=2))
+    assert np.max(np.abs(g_fmo - gradient.scc_gradient(s.Z, s.xyz, params))) < FD_TOL
+
+
+def test_fmo2_gradient_of_two_fragments_equals_whole_system_gradient(params, water_dimer):
+    # FMO2 of two fragments with an SCC dimer is the whole-system energy
+    g_fmo = gradient.fmo_gradient(water_dimer, params, ofmo.FMOOptions(level=2, all_dimers_scc=True))
+    g_all = gradient.scc_gradient(water_dimer.Z, water_dimer.xyz, params)
+    assert np.max(np.abs(g_fmo - g_all)) < FD_TOL
+
+
+def test_fmo2_gradient_of_three_fragments_has_no_net_force(params, water64):
+    s = water64.subsystem([0, 1, 2])
+    g = gradient.fmo_gradient(s, params, ofmo.FMOOptions(level=2, all_dimers_scc=True))
+    assert np.abs(g).max() > 1e-3
+    assert np.max(np.abs(g.sum(axis=0))) < 1e-8
