@@ -1240,7 +1240,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     CK(upload(ctx->d_esdim_idx, es_idx, st));
     CK(launch_esdim(st, int(es_pairs.size()), ctx->d_esdim_pairs.as<int2>(), ctx->d_esdim_idx.as<long long>(),
                     ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
-                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_dE_pair.as<double>()));
+                    ctx->d_dq_mono.as<double>(), ctx->g, ctx->d_dE_pair.as<double>(),
+                    ctx->gam_full_ok ? ctx->d_gam_full.as<double>() : nullptr, ctx->n_sh));
   }
   cudaEventRecord(ev[4], st);
   sr.set("fmo_trimers");

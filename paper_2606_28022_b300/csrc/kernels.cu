@@ -1691,14 +1691,20 @@ __global__ void __launch_bounds__(256) phi_gemv_kernel(int n_sh, const double* _
   const int mu = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (mu >= n_sh) return;
   const double* row = gam + (size_t)mu * n_sh;
-  double s0 = 0.0, s1 = 0.0;
+  // four independent loads in flight per lane: the row stream needs the
+  // memory-level parallelism to approach HBM bandwidth
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int l = lane;
-  for (; l + 32 < n_sh; l += 64) {
-    s0 = fma(row[l], dq[l], s0);
-    s1 = fma(row[l + 32], dq[l + 32], s1);
+  for (; l + 96 < n_sh; l += 128) {
+    const double a0 = __ldcs(row + l), a1 = __ldcs(row + l + 32), a2 = __ldcs(row + l + 64),
+                 a3 = __ldcs(row + l + 96);
+    s0 = fma(a0, dq[l], s0);
+    s1 = fma(a1, dq[l + 32], s1);
+    s2 = fma(a2, dq[l + 64], s2);
+    s3 = fma(a3, dq[l + 96], s3);
   }
-  if (l < n_sh) s0 = fma(row[l], dq[l], s0);
-  const double v = warp_sum(s0 + s1);
+  for (; l < n_sh; l += 32) s0 = fma(row[l], dq[l], s0);
+  const double v = warp_sum((s0 + s1) + (s2 + s3));
   if (lane == 0) phi[mu] = v;
 }
 
@@ -1777,7 +1783,8 @@ __global__ void pair_distance_kernel(int n_frag, FragTab ft, const double* __res
 __global__ void esdim_kernel(int n_pairs, const int2* __restrict__ pairs, const long long* __restrict__ out_idx,
                              FragTab ft, const double* __restrict__ xyz, const int* __restrict__ sh_atom,
                              const double* __restrict__ sh_inv_eta, const double* __restrict__ dq,
-                             GParams g, double* __restrict__ out) {
+                             GParams g, double* __restrict__ out, const double* __restrict__ gam_full,
+                             int n_sh) {
   __shared__ double red[32];
   for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
     const int I = pairs[p].x, J = pairs[p].y;
@@ -1785,6 +1792,10 @@ __global__ void esdim_kernel(int n_pairs, const int2* __restrict__ pairs, const 
     double acc = 0.0;
     for (int k = threadIdx.x; k < ns * nt; k += blockDim.x) {
       const int mu = s0 + k / nt, nu = t0 + k % nt;
+      if (gam_full) {   // the stored gamma of all shell pairs: the same values
+        acc += gam_full[(size_t)mu * n_sh + nu] * dq[mu] * dq[nu];
+        continue;
+      }
       const int a = sh_atom[mu], b = sh_atom[nu];
       const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
                    dz = xyz[3 * a + 2] - xyz[3 * b + 2];
@@ -2187,10 +2198,11 @@ cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const 
 
 cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const long long* out_idx, FragTab ft,
                          const double* xyz, const int* sh_atom, const double* sh_inv_eta, const double* dq,
-                         GParams g, double* out) {
+                         GParams g, double* out, const double* gam_full, int n_sh) {
   if (n_pairs == 0) return cudaSuccess;
   const int blocks = std::min(n_pairs, 148 * 16);
-  esdim_kernel<<<blocks, 256, 0, st>>>(n_pairs, pairs, out_idx, ft, xyz, sh_atom, sh_inv_eta, dq, g, out);
+  esdim_kernel<<<blocks, 256, 0, st>>>(n_pairs, pairs, out_idx, ft, xyz, sh_atom, sh_inv_eta, dq, g, out, gam_full,
+                                       n_sh);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

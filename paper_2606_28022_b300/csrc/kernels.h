@@ -120,7 +120,7 @@ cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const 
                                  double cut, double* rmin);
 cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const long long* out_idx, FragTab ft,
                          const double* xyz, const int* sh_atom, const double* sh_inv_eta, const double* dq,
-                         GParams g, double* out);
+                         GParams g, double* out, const double* gam_full = nullptr, int n_sh = 0);
 // out[i] = (float)in[i], i < n
 cudaError_t launch_to_float(cudaStream_t st, long long n, const double* in, float* out);
 cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t);
