@@ -284,6 +284,22 @@ fmo_status fmo_get_dimers(fmo_ctx *ctx, int64_t *n, int32_t *ij, double *dE, dou
  * corr[n] (dE_IJK - dE_IJ - dE_IK - dE_JK). */
 fmo_status fmo_get_trimers(fmo_ctx *ctx, int64_t *n, int32_t *ijk, double *dE3, double *corr);
 
+/*
+ * Nuclear gradient dE/dxyz (Eh/bohr) of the last fmo_run, grad[3*n_atoms] in
+ * the input atom order (host memory, caller-owned).  The analytic GFN1-xTB
+ * gradient of one SCC system (the building block of the gradient section,
+ * Eqs. 23-28: P dH0 + W dS + 1/2 dq dq dgamma + dE_rep, with the Pi and
+ * CN-dependent parts of dH0), evaluated on the GPU from the run's FP64
+ * orbitals.  This release covers systems that are one fragment without cut
+ * bonds, run in precision FP64 (there E_FMO is the GFN1-xTB energy); the FMO
+ * terms of several fragments (explicit embedding, charge-transfer and ES-DIM
+ * terms and the self-consistent Z-vector response) are not built.
+ * Errors: FMO_ERR_ARG (NULL), FMO_ERR_STATE (no run), FMO_ERR_UNSUPPORTED
+ * (several fragments, cut bonds, mixed precision, more than 2048 atoms),
+ * FMO_ERR_CUDA.
+ */
+fmo_status fmo_get_gradient(fmo_ctx *ctx, double *grad);
+
 fmo_status fmo_get_stats(fmo_ctx *ctx, fmo_stats *st);
 
 /*

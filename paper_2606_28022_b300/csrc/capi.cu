@@ -139,6 +139,8 @@ struct fmo_ctx {
   // results of the last run
   bool have_result = false;
   int last_level = 0;
+  int last_precision = 0;
+  DevBuf d_grad_work, d_grad;
   double totals[3] = {0, 0, 0};
   std::vector<double> r_e_mono, r_dq_mono, r_dE_pair, r_e_dim_pair, r_dEV_pair;
   std::vector<int> r_mono_iters, r_mono_status, r_pair_iters;
@@ -765,7 +767,7 @@ void fmo_destroy(fmo_ctx* ctx) {
                     &ctx->d_mlp_fcharge, &ctx->d_mlp_err, &ctx->d_mlp_X, &ctx->d_mlp_y, &ctx->d_mlp_q, &ctx->d_ghost_frag, &ctx->d_ghost_src, &ctx->d_bda_baa_frag, &ctx->d_hop_baa, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
-                    &ctx->d_totals})
+                    &ctx->d_totals, &ctx->d_grad_work, &ctx->d_grad})
     b->release();
   ctx->stg.release();
   ctx->mono.release();
@@ -1340,6 +1342,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   ctx->stats.d2h_bytes = ctx->d2h_bytes;
   ctx->h2d_bytes = 0;
   ctx->last_level = o.level;
+  ctx->last_precision = o.precision;
   if (o.level < 2) ctx->totals[1] = std::nan("");
   if (o.level < 3) ctx->totals[2] = std::nan("");
   ctx->have_result = true;
@@ -1399,6 +1402,33 @@ fmo_status fmo_get_dimers(fmo_ctx* ctx, int64_t* n, int32_t* ij, double* dE, dou
   if (dEV) std::memcpy(dEV, ctx->r_dEV_pair.data(), sizeof(double) * np);
   if (scc) std::memcpy(scc, ctx->r_pair_scc.data(), np);
   if (iters) std::memcpy(iters, ctx->r_pair_iters.data(), sizeof(int) * np);
+  return FMO_OK;
+}
+
+fmo_status fmo_get_gradient(fmo_ctx* ctx, double* grad) {
+  if (!ctx || !grad) return FMO_ERR_ARG;
+  if (!ctx->have_result) return fail(ctx, FMO_ERR_STATE, "no results: call fmo_run");
+  if (ctx->n_frag != 1 || ctx->n_cut > 0)
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: only a system that is one fragment without cut bonds");
+  if (ctx->last_precision != FMO_PREC_FP64)
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: needs a run in precision FP64");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->own_stream;
+  Pass& P = ctx->mono;
+  const Nmer& m = P.nm[0];
+  if (m.nat > 8 * kBlock) return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: more than 2048 atoms");
+  CK(ctx->d_grad_work.ensure(sizeof(double) * 4 * (size_t)m.n * m.n));
+  CK(ctx->d_grad.ensure(sizeof(double) * 3 * (size_t)m.nat));
+  CK(launch_xtb_gradient(st, P.d_nm.as<Nmer>(), m.n, m.nsh, m.nat, ctx->ftab(), ctx->d_xyz.as<double>(),
+                         ctx->d_elem.as<int>(), ctx->d_atom_sh0.as<int>(), ctx->d_el.as<DevElem>(),
+                         ctx->d_kab.as<double>(), ctx->ne, ctx->d_prim.as<PrimPair>(), ctx->d_cn.as<double>(), ctx->g,
+                         P.S.as<double>(), P.H0.as<double>(), P.CTd.as<double>(), P.eps.as<double>(),
+                         P.gam.as<double>(), ctx->d_grad_work.as<double>(), ctx->d_grad.as<double>()));
+  std::vector<double> g(3 * (size_t)m.nat);
+  CK(d2h(g.data(), ctx->d_grad.p, sizeof(double) * g.size(), st));
+  CK(sync_stream(st));
+  for (int i = 0; i < m.nat; ++i)   // internal atom order -> input order
+    for (int c = 0; c < 3; ++c) grad[3 * ctx->perm[i] + c] = g[3 * (size_t)i + c];
   return FMO_OK;
 }
 

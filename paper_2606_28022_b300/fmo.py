@@ -25,7 +25,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 
 SYMBOLS = ["fmo_options_default", "fmo_create", "fmo_set_system", "fmo_set_coordinates",
            "fmo_set_coordinates_device", "fmo_set_guess", "fmo_run", "fmo_get_energy",
-           "fmo_get_sizes", "fmo_get_monomers", "fmo_get_dimers", "fmo_get_trimers",
+           "fmo_get_sizes", "fmo_get_monomers", "fmo_get_dimers", "fmo_get_trimers", "fmo_get_gradient",
            "fmo_get_stats", "fmo_last_error", "fmo_destroy", "fmo_mlp_init", "fmo_mlp_set_weights",
            "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train"]
 MLP_N_WEIGHTS = 26908
@@ -108,6 +108,7 @@ def load_library(path: str | None = None):
     lib.fmo_get_monomers.argtypes = [vp, dp, dp, ip, ip]
     lib.fmo_get_dimers.argtypes = [vp, C.POINTER(i64), ip, dp, dp, dp, C.POINTER(C.c_uint8), ip]
     lib.fmo_get_trimers.argtypes = [vp, C.POINTER(i64), ip, dp, dp]
+    lib.fmo_get_gradient.argtypes = [vp, dp]
     lib.fmo_get_stats.argtypes = [vp, C.POINTER(FmoStats)]
     fp = C.POINTER(C.c_float)
     lib.fmo_mlp_init.argtypes = [vp, C.c_uint64]
@@ -312,6 +313,12 @@ class FMO:
         d3, cr = np.zeros(max(m, 1)), np.zeros(max(m, 1))
         self._check(self.lib.fmo_get_trimers(self.h, C.byref(n), _ip(ijk), _dp(d3), _dp(cr)))
         return Trimers(ijk[:3 * m].reshape(-1, 3), d3[:m], cr[:m])
+
+    def gradient(self) -> np.ndarray:
+        """dE/dxyz (n_atoms x 3, Eh/bohr) of the last run (fmo_get_gradient)."""
+        g = np.zeros(3 * self.n_atoms)
+        self._check(self.lib.fmo_get_gradient(self.h, _dp(g)))
+        return g.reshape(-1, 3)
 
     # learned initial charges (options guess=1)
     def mlp_init(self, seed: int = 0):
