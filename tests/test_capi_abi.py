@@ -58,6 +58,7 @@ def test_defaults_and_argument_errors(lib):
     assert lib.fmo_create(None, None, 0) == 1                     # FMO_ERR_ARG
     assert lib.fmo_run(None, None, None) == 1
     assert lib.fmo_get_energy(None, None, None, None) == 1
+    assert lib.fmo_get_gradient(None, None) == 1
     lib.fmo_destroy(None)                                       # allowed
 
 
