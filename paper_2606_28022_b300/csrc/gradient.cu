@@ -25,8 +25,6 @@
 //   6. after a barrier, the CN gradient (F_A + F_B) f'(R_AB) R_AB/|R_AB|.
 // Each atom's gradient is summed by its own thread in a fixed order.
 
-#include <cstdio>
-
 #include "fmo_device.cuh"
 #include "kernels.h"
 
@@ -54,7 +52,6 @@ struct GradArgs {
   double* T;
   double* W;
   double* grad;          // [nat][3], local atom order
-  int* status;
 };
 
 __global__ void __launch_bounds__(kBlock) xtb_gradient_kernel(GradArgs ar) {
@@ -318,7 +315,7 @@ cudaError_t launch_xtb_gradient(cudaStream_t st, const Nmer* nm, int n, int nsh,
   ar.ne = ne; ar.prim = prim; ar.cn = cn; ar.g = g; ar.S = S; ar.H0 = H0; ar.CT = CT; ar.eps = eps; ar.gam = gam;
   const size_t nn = (size_t)n * n;
   ar.P = work; ar.F = work + nn; ar.T = work + 2 * nn; ar.W = work + 3 * nn;
-  ar.grad = grad; ar.status = nullptr;
+  ar.grad = grad;
   const size_t sb = gradient_smem(n, nsh, nat);
   cudaError_t e = cudaFuncSetAttribute(xtb_gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
   if (e != cudaSuccess) return e;
