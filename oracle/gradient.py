@@ -123,28 +123,26 @@ def cn_derivative(Z, xyz, params) -> np.ndarray:
     return d
 
 
-def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) -> np.ndarray:
-    """Analytic gradient (n_atoms x 3, Eh/bohr) of the GFN1-xTB energy of one
-    neutral system without external potential, at its SCC solution."""
+def explicit_gradient(Z, xyz, params, basis, P, Wt, sigma, Q, cn, dcn, atoms=None, n_all=None,
+                      with_rep=True, M_extra=None) -> np.ndarray:
+    """The explicit terms of Eqs. 23-28 for one system at fixed P, W~, shell
+    shifts sigma and charge product Q (n_sh x n_sh, Q = dq dq^T for the
+    energy): sum dS (P H + 1/2 (sigma_mu + sigma_nu) P - W~ [+ M_extra])
+    + the Pi and CN parts of dH0 + 1/2 sum Q dgamma [+ dE_rep].
+    cn: the CN of the system's atoms (in FMO: supersystem values); dcn
+    [a, k, c]: their derivatives with respect to every atom k of the
+    supersystem (n_all atoms); atoms: the system's atoms in the supersystem
+    (default: all).  Returns n_all x 3."""
     Z = np.asarray(Z)
     xyz = np.asarray(xyz, dtype=np.float64)
-    cn = xtb.coordination_numbers(Z, xyz, params)
-    if res is None:
-        res = xtb.scc(Z, xyz, params, cn, tol=tol, e_tol=tol)
-    b = res.basis
+    b = basis
     n_at = len(Z)
+    atoms = np.arange(n_at) if atoms is None else np.asarray(atoms)
+    n_all = n_at if n_all is None else n_all
     sh = b.ao_shell
     at = b.ao_atom
-    P = res.P
-    S = res.S
-    Wt = (res.C * (res.occ * res.eps)) @ res.C.T                  # energy-weighted density (Eq. 24)
-    gam = xtb.gamma_matrix(Z, xyz, params, b)
-    g3 = xtb.atom_param(Z, params, "gamma3")
-    dq = res.dq
-    dq_at = np.bincount(b.sh_atom, weights=dq, minlength=n_at)
-    sigma = gam @ dq - g3[b.sh_atom] * dq_at[b.sh_atom] ** 2         # shell shifts
-    sig_ao = sigma[sh]
-
+    S = xtb.overlap_matrix(Z, xyz, params, b)
+    sig_ao = np.asarray(sigma)[sh]
     # pieces of H0 (Eq. 8) per AO pair
     h_l = xtb.shell_param(Z, b, params, "h_l")
     k_cn = xtb.shell_param(Z, b, params, "k_cn_l")
@@ -172,7 +170,10 @@ def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) ->
     grad = np.zeros((n_at, 3))
     # (1) every S-dependence: P Hpref + 1/2 (sigma_mu + sigma_nu) P - W~ (Eqs. 23-25)
     dS = overlap_derivative(Z, xyz, params, b)
-    Mw = np.where(off, P * Hpref + 0.5 * (sig_ao[:, None] + sig_ao[None, :]) * P - Wt, 0.0)
+    Mw = P * Hpref + 0.5 * (sig_ao[:, None] + sig_ao[None, :]) * P - Wt
+    if M_extra is not None:
+        Mw = Mw + M_extra
+    Mw = np.where(off, Mw, 0.0)
     grad += np.einsum("kcij,ij->kc", dS, Mw)
     # (2) the distance polynomial Pi(R_AB) (Eq. 9)
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -184,45 +185,65 @@ def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) ->
     for k in range(n_at):
         grad[k] += pair[at == k].sum(axis=(0, 1))
         grad[k] -= pair[:, at == k].sum(axis=(0, 1))
-    # (3) CN-dependent levels (Eqs. 10, 26-28): F_A = dE/dCN_A
-    dh = h_l * k_cn                                                    # dh_l / dCN of the shell's atom
-    dh_ao = dh[sh]
+    # (4) the Coulomb kernel: 1/2 sum Q_st dgamma_st (Eq. 23)
+    eta = xtb.shell_hardness(Z, b, params)
+    sa = b.sh_atom
+    for s_ in range(b.n_sh):
+        for t in range(b.n_sh):
+            if sa[s_] == sa[t] or Q[s_, t] == 0.0:
+                continue
+            rv = xyz[sa[s_]] - xyz[sa[t]]
+            r = float(np.linalg.norm(rv))
+            e = 2.0 / (1.0 / eta[s_] + 1.0 / eta[t])
+            gm = (r ** params.k_g + e ** (-params.k_g)) ** (-1.0 / params.k_g)
+            dg = -r ** (params.k_g - 1.0) * gm ** (1.0 + params.k_g)
+            v = 0.5 * Q[s_, t] * dg * rv / r
+            grad[sa[s_]] += v
+            grad[sa[t]] -= v
+    # (5) repulsion (Eq. 11)
+    if with_rep:
+        zeff = xtb.atom_param(Z, params, "z_eff")
+        arep = xtb.atom_param(Z, params, "alpha_rep")
+        for a in range(n_at):
+            for c in range(a):
+                rv = xyz[a] - xyz[c]
+                r = float(np.linalg.norm(rv))
+                al = np.sqrt(arep[a] * arep[c])
+                ex = np.exp(-al * r ** params.k_f)
+                de = zeff[a] * zeff[c] * ex * (-1.0 / r ** 2 - al * params.k_f * r ** (params.k_f - 2.0))
+                grad[a] += de * rv / r
+                grad[c] -= de * rv / r
+    out = np.zeros((n_all, 3))
+    out[atoms] += grad
+    # (3) CN-dependent levels (Eqs. 10, 26-28): F_A = dE/dCN_A, then the chain
+    # rule over every atom the CN depends on
+    dh_ao = (h_l * k_cn)[sh]                                            # dh_l / dCN of the shell's atom
     F = np.zeros(n_at)
-    onsite_diag = np.diag(P) * dh_ao
-    np.add.at(F, at, onsite_diag)
+    np.add.at(F, at, np.diag(P) * dh_ao)
     Hcn = np.where(off, P * S * kab * kll * fen * Pi * 0.5, 0.0)       # d(hbar)/dh_mu = 1/2
     np.add.at(F, at, (Hcn * dh_ao[:, None]).sum(axis=1))
     np.add.at(F, at, (Hcn * dh_ao[None, :]).sum(axis=0))
-    dcn = cn_derivative(Z, xyz, params)
-    grad += np.einsum("a,akc->kc", F, dcn)
-    # (4) the Coulomb kernel at fixed charges: 1/2 sum dq_s dq_t dgamma_st (Eq. 23)
-    eta = xtb.shell_hardness(Z, b, params)
-    sa = b.sh_atom
-    for s in range(b.n_sh):
-        for t in range(b.n_sh):
-            if sa[s] == sa[t]:
-                continue
-            rv = xyz[sa[s]] - xyz[sa[t]]
-            r = float(np.linalg.norm(rv))
-            e = 2.0 / (1.0 / eta[s] + 1.0 / eta[t])
-            gm = (r ** params.k_g + e ** (-params.k_g)) ** (-1.0 / params.k_g)
-            dg = -r ** (params.k_g - 1.0) * gm ** (1.0 + params.k_g)
-            v = 0.5 * dq[s] * dq[t] * dg * rv / r
-            grad[sa[s]] += v
-            grad[sa[t]] -= v
-    # (5) repulsion (Eq. 11)
-    zeff = xtb.atom_param(Z, params, "z_eff")
-    arep = xtb.atom_param(Z, params, "alpha_rep")
-    for a in range(n_at):
-        for c in range(a):
-            rv = xyz[a] - xyz[c]
-            r = float(np.linalg.norm(rv))
-            al = np.sqrt(arep[a] * arep[c])
-            ex = np.exp(-al * r ** params.k_f)
-            de = zeff[a] * zeff[c] * ex * (-1.0 / r ** 2 - al * params.k_f * r ** (params.k_f - 2.0))
-            grad[a] += de * rv / r
-            grad[c] -= de * rv / r
-    return grad
+    out += np.einsum("a,akc->kc", F, dcn)
+    return out
+
+
+def scc_gradient(Z, xyz, params, res: xtb.SCCResult | None = None, tol=1e-12) -> np.ndarray:
+    """Analytic gradient (n_atoms x 3, Eh/bohr) of the GFN1-xTB energy of one
+    neutral system without external potential, at its SCC solution."""
+    Z = np.asarray(Z)
+    xyz = np.asarray(xyz, dtype=np.float64)
+    cn = xtb.coordination_numbers(Z, xyz, params)
+    if res is None:
+        res = xtb.scc(Z, xyz, params, cn, tol=tol, e_tol=tol)
+    b = res.basis
+    Wt = (res.C * (res.occ * res.eps)) @ res.C.T                  # energy-weighted density (Eq. 24)
+    gam = xtb.gamma_matrix(Z, xyz, params, b)
+    g3 = xtb.atom_param(Z, params, "gamma3")
+    dq = res.dq
+    dq_at = np.bincount(b.sh_atom, weights=dq, minlength=len(Z))
+    sigma = gam @ dq - g3[b.sh_atom] * dq_at[b.sh_atom] ** 2         # shell shifts
+    return explicit_gradient(Z, xyz, params, b, res.P, Wt, sigma, np.outer(dq, dq), cn,
+                             cn_derivative(Z, xyz, params))
 
 
 def fmo_gradient(system, params, opts=None, h=1e-4) -> np.ndarray:

@@ -1,0 +1,58 @@
+"""Pins of the oracle's analytic FMO1 gradient (explicit terms plus the
+self-consistent Z-vector response, oracle/fmo_gradient.py): central
+differences of the oracle's FMO1 energy, the one-fragment identity, and a
+planted mistake (no response) that the finite differences catch."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import fmo as ofmo
+from oracle import fmo_gradient, gradient
+from paper_2606_28022_b300.inputs import geometry as G
+
+FD_TOL = 2e-8   # Eh/bohr
+
+
+@pytest.fixture(scope="module")
+def water3(water64):
+    return water64.subsystem([0, 1, 2])
+
+
+@pytest.fixture(scope="module")
+def water3_fd(params, water3):
+    return gradient.fmo_gradient(water3, params, ofmo.FMOOptions(level=1))
+
+
+def test_fmo1_gradient_equals_finite_differences(params, water3, water3_fd):
+    g = fmo_gradient.fmo1_gradient(water3, params)
+    assert np.abs(water3_fd).max() > 1e-3
+    assert np.max(np.abs(g - water3_fd)) < FD_TOL
+    assert np.max(np.abs(g.sum(axis=0))) < 1e-12
+
+
+def test_fmo1_gradient_without_response_misses(params, water3, water3_fd, monkeypatch):
+    # planted mistake: monomer susceptibilities set to zero (no SCZV response)
+    real = fmo_gradient.response.susceptibility
+    monkeypatch.setattr(fmo_gradient.response, "susceptibility", lambda prob, res: 0.0 * real(prob, res))
+    g = fmo_gradient.fmo1_gradient(water3, params)
+    assert np.max(np.abs(g - water3_fd)) > 1e-4
+
+
+def test_fmo1_gradient_one_fragment_is_scc_gradient(params, water64):
+    s = water64.subsystem([4])
+    g = fmo_gradient.fmo1_gradient(s, params)
+    assert np.max(np.abs(g - gradient.scc_gradient(s.Z, s.xyz, params))) < 1e-9
+
+
+def test_fmo1_gradient_anthracene_pair_sampled(params):
+    a, _ = G.anthracene_cluster(8, 2)
+    a = a.subsystem([0, 1])
+    g = fmo_gradient.fmo1_gradient(a, params)
+    opts = ofmo.FMOOptions(level=1, scc_tol=1e-12, e_tol=1e-13, outer_tol=1e-12)
+    energy = lambda x: ofmo.fmo(dataclasses.replace(a, xyz=x), params, opts).e_fmo1
+    for k in (0, 17, 30):
+        for c in range(3):
+            xp = a.xyz.copy(); xp[k, c] += 1e-4
+            xm = a.xyz.copy(); xm[k, c] -= 1e-4
+            assert abs((energy(xp) - energy(xm)) / 2e-4 - g[k, c]) < FD_TOL
