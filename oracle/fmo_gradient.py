@@ -1,6 +1,6 @@
-"""FP64 CPU oracle of the analytic FMO1 gradient: explicit terms plus the
-self-consistent Z-vector (SCZV) response of the monomer charges (Sec. 2.4,
-explicit gradient and response gradient).
+"""FP64 CPU oracle of the analytic FMO1 and FMO2 gradients: explicit terms
+plus the self-consistent Z-vector (SCZV) response of the monomer charges
+(Sec. 2.4, explicit gradient and response gradient).
 
 TEST INFRASTRUCTURE ONLY (see oracle/xtb.py).
 
@@ -22,8 +22,10 @@ contracted with the first-order changes of P, W~, the shifts and the charges
 that the potential z_I causes (coupled-perturbed SCC, as in
 oracle/response.py; W~ = sum f_i e_i c_i c_i^T changes by
 C [N o (C^T dF C)] C^T with N_ij = (f_i e_i - f_j e_j)/(e_i - e_j), minus
-the Fermi-level shift).  Systems without cut bonds.  Central differences of
-the oracle's FMO1 energy pin it (tests/test_fmo_gradient_oracle.py).
+the Fermi-level shift).  FMO2 (fmo2_gradient) adds the SCC dimers and the
+ES-DIM pairs in the same form.  Systems without cut bonds.  Central
+differences of the oracle's FMO1 and FMO2 energies pin both
+(tests/test_fmo_gradient_oracle.py).
 """
 from __future__ import annotations
 
@@ -150,4 +152,144 @@ def fmo1_gradient(system, params, tol=1e-12) -> np.ndarray:
                     v = yI[s] * q[K][t] * dg * rv / rr
                     grad[a] -= v
                     grad[c] += v
+    return grad
+
+
+def _gamma_pair_grad(xyz, at_a, eta_a, ca, at_b, eta_b, cb, k_g, n_all):
+    """Gradient of sum_{s in a, t in b} ca_s cb_t gamma_st over shell sets a
+    and b (different atoms)."""
+    g = np.zeros((n_all, 3))
+    rv = xyz[at_a][:, None, :] - xyz[at_b][None, :, :]
+    rr = np.linalg.norm(rv, axis=-1)
+    ee = 2.0 / (1.0 / eta_a[:, None] + 1.0 / eta_b[None, :])
+    gm = (rr ** k_g + ee ** (-k_g)) ** (-1.0 / k_g)
+    dg = -rr ** (k_g - 1.0) * gm ** (1.0 + k_g)
+    v = (ca[:, None] * cb[None, :] * dg / rr)[..., None] * rv
+    np.add.at(g, at_a, v.sum(axis=1))
+    np.add.at(g, at_b, -v.sum(axis=0))
+    return g
+
+
+def fmo2_gradient(system, params, opts=None, tol=1e-12) -> np.ndarray:
+    """dE_FMO2/dxyz (n_atoms x 3, Eh/bohr), analytic: explicit terms of the
+    monomers, SCC dimers (Eq. 12 with dE^V of Eqs. 13-14) and ES-DIM pairs
+    (Eq. 15), plus the SCZV response of the monomer charges.  With
+    L_X = E'_X + esp_X . dq_X stationary in each n-mer density,
+      E'_I + sum over its SCC dimers ... = sum_I c_I E'_I
+        + sum_IJ [L_IJ - esp_IJ . (dq_I + dq_J)] + sum_ES dq_I Gamma_IJ dq_J,
+    c_I = 1 - (SCC dimers of I); every term linear in the monomer-charge
+    derivatives collects into w, and z = (1 - Gamma chi)^-1 w gives the
+    response z . dQ/dxi|_esp + (chi z)^T dGamma dq."""
+    opts = ofmo.FMOOptions(level=2) if opts is None else opts
+    Z = np.asarray(system.Z)
+    xyz = np.asarray(system.xyz, dtype=np.float64)
+    if len(system.cut_bonds):
+        raise ValueError("cut bonds are not covered")
+    import dataclasses
+    o = dataclasses.replace(opts, level=2, scc_tol=tol, e_tol=0.1 * tol, outer_tol=tol)
+    r = ofmo.fmo(system, params, o)
+    nf = system.n_frag
+    n_all = len(Z)
+    kg = params.k_g
+    atoms = [np.nonzero(system.frag == f)[0] for f in range(nf)]
+    cn_all = xtb.coordination_numbers(Z, xyz, params)
+    dcn_all = gradient.cn_derivative(Z, xyz, params)
+    bases = [xtb.make_basis(Z[a], params) for a in atoms]
+    sh_at = [atoms[I][bases[I].sh_atom] for I in range(nf)]           # supersystem atom of each shell
+    eta = [xtb.shell_hardness(Z[a], b, params) for a, b in zip(atoms, bases)]
+    gam = [[xtb.gamma_between(xyz[sh_at[I]], eta[I], xyz[sh_at[K]], eta[K], kg) for K in range(nf)]
+           for I in range(nf)]
+    q = [np.asarray(d, dtype=np.float64) for d in r.dq_mono]
+
+    def esp_of(nmer):
+        return [sum((gam[I][K] @ q[K] for K in range(nf) if K not in nmer), np.zeros(len(q[I]))) for I in nmer]
+
+    def solve(nmer):
+        at = np.concatenate([atoms[I] for I in nmer])
+        esp = np.concatenate(esp_of(nmer))
+        prob = xtb.SCCProblem(Z[at], xyz[at], params, cn_all[at], esp=esp,
+                              charge=float(sum(system.frag_charge[I] for I in nmer)))
+        res = xtb.solve_problem(prob, guess=np.concatenate([q[I] for I in nmer]), tol=tol, e_tol=0.1 * tol)
+        return at, esp, prob, res
+
+    def explicit(at, b, prob, res, esp):
+        dq_at = np.bincount(b.sh_atom, weights=res.dq, minlength=len(at))
+        sig = prob.gam @ res.dq - prob.g3[b.sh_atom] * dq_at[b.sh_atom] ** 2 + esp
+        Wt = (res.C * (res.occ * res.eps)) @ res.C.T
+        return gradient.explicit_gradient(Z[at], xyz[at], params, b, res.P, Wt, sig, np.outer(res.dq, res.dq),
+                                          cn_all[at], dcn_all[at], atoms=at, n_all=n_all), sig
+
+    pairs = [tuple(int(x) for x in pq) for pq in r.dimers]
+    scc = [bool(x) for x in r.dimer_scc]
+    n_scc = np.zeros(nf)
+    for (I, J), ok in zip(pairs, scc):
+        if ok:
+            n_scc[I] += 1
+            n_scc[J] += 1
+    off = np.cumsum([0] + [len(x) for x in q])
+    w = np.zeros(off[-1])
+    grad = np.zeros((n_all, 3))
+
+    # monomers: c_I (dL_I/dxi|_esp - esp_I . dq_I')
+    mono = []
+    for I in range(nf):
+        at, esp, prob, res = solve((I,))
+        q[I] = res.dq
+        mono.append((prob, res))
+    for I in range(nf):
+        prob, res = mono[I]
+        esp = esp_of((I,))[0]
+        gI, sigI = explicit(atoms[I], bases[I], prob, res, esp)
+        mono[I] = (prob, res, sigI)
+        c = 1.0 - n_scc[I]
+        grad += c * gI
+        w[off[I]:off[I + 1]] -= c * esp
+    # SCC dimers: L_IJ - esp_IJ . (dq_I + dq_J); ES-DIM pairs: dq_I Gamma_IJ dq_J
+    for (I, J), ok in zip(pairs, scc):
+        if not ok:
+            grad += _gamma_pair_grad(xyz, sh_at[I], eta[I], q[I], sh_at[J], eta[J], q[J], kg, n_all)
+            w[off[I]:off[I + 1]] += gam[I][J] @ q[J]
+            w[off[J]:off[J + 1]] += gam[J][I] @ q[I]
+            continue
+        at, esp, prob, res = solve((I, J))
+        b = xtb.make_basis(Z[at], params)
+        gIJ, _ = explicit(at, b, prob, res, esp)
+        grad += gIJ
+        nI = len(q[I])
+        ddq = res.dq - np.concatenate([q[I], q[J]])
+        eI, eJ = esp[:nI], esp[nI:]
+        w[off[I]:off[I + 1]] -= eI
+        w[off[J]:off[J + 1]] -= eJ
+        for K in range(nf):
+            if K in (I, J):
+                continue
+            # ddq . dGamma_{IJ,K} dq_K (explicit) and ddq . Gamma_{IJ,K} dq_K' (into w)
+            grad += _gamma_pair_grad(xyz, sh_at[I], eta[I], ddq[:nI], sh_at[K], eta[K], q[K], kg, n_all)
+            grad += _gamma_pair_grad(xyz, sh_at[J], eta[J], ddq[nI:], sh_at[K], eta[K], q[K], kg, n_all)
+            w[off[K]:off[K + 1]] += gam[K][I] @ ddq[:nI] + gam[K][J] @ ddq[nI:]
+
+    # response: z = (1 - Gamma chi)^-1 w; z . dQ/dxi|_esp + (chi z)^T dGamma dq
+    n_sh = off[-1]
+    G = np.zeros((n_sh, n_sh))
+    chi = np.zeros((n_sh, n_sh))
+    for I in range(nf):
+        chi[off[I]:off[I + 1], off[I]:off[I + 1]] = response.susceptibility(mono[I][0], mono[I][1])
+        for K in range(nf):
+            if K != I:
+                G[off[I]:off[I + 1], off[K]:off[K + 1]] = gam[I][K]
+    z = np.linalg.solve(np.eye(n_sh) - G @ chi, w)
+    y = chi @ z
+    for I in range(nf):
+        prob, res, sigI = mono[I]
+        dq1, dsig, dP, dWt = _first_order(prob, res, z[off[I]:off[I + 1]])
+        sh = bases[I].ao_shell
+        M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
+        Q = np.outer(res.dq, dq1) + np.outer(dq1, res.dq)
+        grad += gradient.explicit_gradient(Z[atoms[I]], xyz[atoms[I]], params, bases[I], dP, dWt, sigI, Q,
+                                           cn_all[atoms[I]], dcn_all[atoms[I]], atoms=atoms[I], n_all=n_all,
+                                           with_rep=False, M_extra=M_extra)
+        for K in range(nf):
+            if K != I:
+                grad += _gamma_pair_grad(xyz, sh_at[I], eta[I], y[off[I]:off[I + 1]], sh_at[K], eta[K], q[K],
+                                         kg, n_all)
     return grad

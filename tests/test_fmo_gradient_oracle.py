@@ -56,3 +56,15 @@ def test_fmo1_gradient_anthracene_pair_sampled(params):
             xp = a.xyz.copy(); xp[k, c] += 1e-4
             xm = a.xyz.copy(); xm[k, c] -= 1e-4
             assert abs((energy(xp) - energy(xm)) / 2e-4 - g[k, c]) < FD_TOL
+
+
+@pytest.mark.parametrize("frags,all_scc", [([0, 1, 2], True), ([0, 1, 2, 3], False)])
+def test_fmo2_gradient_equals_finite_differences(params, water64, frags, all_scc):
+    # all SCC dimers, and a mix of SCC dimers and ES-DIM pairs (4.0 A rule)
+    s = water64.subsystem(frags)
+    opts = ofmo.FMOOptions(level=2, all_dimers_scc=all_scc)
+    r = ofmo.fmo(s, params, opts)
+    assert r.dimer_scc.all() if all_scc else (r.dimer_scc.any() and not r.dimer_scc.all())
+    g = fmo_gradient.fmo2_gradient(s, params, opts)
+    fd = gradient.fmo_gradient(s, params, opts)
+    assert np.max(np.abs(g - fd)) < FD_TOL
