@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the analytic FMO1 and FMO2 gradients: explicit terms
+"""FP64 CPU oracle of the analytic FMO1, FMO2 and FMO3 gradients: explicit terms
 plus the self-consistent Z-vector (SCZV) response of the monomer charges
 (Sec. 2.4, explicit gradient and response gradient).
 
@@ -23,9 +23,10 @@ that the potential z_I causes (coupled-perturbed SCC, as in
 oracle/response.py; W~ = sum f_i e_i c_i c_i^T changes by
 C [N o (C^T dF C)] C^T with N_ij = (f_i e_i - f_j e_j)/(e_i - e_j), minus
 the Fermi-level shift).  FMO2 (fmo2_gradient) adds the SCC dimers and the
-ES-DIM pairs in the same form.  Systems without cut bonds.  Central
-differences of the oracle's FMO1 and FMO2 energies pin both
-(tests/test_fmo_gradient_oracle.py).
+ES-DIM pairs in the same form, FMO3 (fmo3_gradient) the trimer corrections.
+Systems without cut bonds.  Central differences of the oracle's FMO1, FMO2
+and FMO3 energies pin them, and so does the exact identity of FMO3 of three
+fragments with the whole system (tests/test_fmo_gradient_oracle.py).
 """
 from __future__ import annotations
 
@@ -175,18 +176,32 @@ def fmo2_gradient(system, params, opts=None, tol=1e-12) -> np.ndarray:
     monomers, SCC dimers (Eq. 12 with dE^V of Eqs. 13-14) and ES-DIM pairs
     (Eq. 15), plus the SCZV response of the monomer charges.  With
     L_X = E'_X + esp_X . dq_X stationary in each n-mer density,
-      E'_I + sum over its SCC dimers ... = sum_I c_I E'_I
-        + sum_IJ [L_IJ - esp_IJ . (dq_I + dq_J)] + sum_ES dq_I Gamma_IJ dq_J,
+      E_FMO2 = sum_I c_I E'_I + sum_SCC [L_IJ - esp_IJ . (dq_I + dq_J)]
+               + sum_ES dq_I Gamma_IJ dq_J,
     c_I = 1 - (SCC dimers of I); every term linear in the monomer-charge
     derivatives collects into w, and z = (1 - Gamma chi)^-1 w gives the
     response z . dQ/dxi|_esp + (chi z)^T dGamma dq."""
     opts = ofmo.FMOOptions(level=2) if opts is None else opts
+    return _nmer_gradient(system, params, opts, 2, tol)
+
+
+def fmo3_gradient(system, params, opts=None, tol=1e-12) -> np.ndarray:
+    """dE_FMO3/dxyz: as fmo2_gradient with the trimer corrections of
+    Eqs. 16-19, corr_IJK = dE_IJK - dE_IJ - dE_IK - dE_JK.  Each trimer adds
+    L_IJK - esp_IJK . (dq_I + dq_J + dq_K) with coefficient 1, takes one from
+    the coefficient of each of its pair terms, and changes c_I by
+    -1 + (its SCC pairs holding I)."""
+    opts = ofmo.FMOOptions(level=3) if opts is None else opts
+    return _nmer_gradient(system, params, opts, 3, tol)
+
+
+def _nmer_gradient(system, params, opts, level, tol):
+    import dataclasses
     Z = np.asarray(system.Z)
     xyz = np.asarray(system.xyz, dtype=np.float64)
     if len(system.cut_bonds):
         raise ValueError("cut bonds are not covered")
-    import dataclasses
-    o = dataclasses.replace(opts, level=2, scc_tol=tol, e_tol=0.1 * tol, outer_tol=tol)
+    o = dataclasses.replace(opts, level=level, scc_tol=tol, e_tol=0.1 * tol, outer_tol=tol)
     r = ofmo.fmo(system, params, o)
     nf = system.n_frag
     n_all = len(Z)
@@ -221,11 +236,23 @@ def fmo2_gradient(system, params, opts=None, tol=1e-12) -> np.ndarray:
 
     pairs = [tuple(int(x) for x in pq) for pq in r.dimers]
     scc = [bool(x) for x in r.dimer_scc]
-    n_scc = np.zeros(nf)
+    tris = [tuple(int(x) for x in t) for t in r.trimers] if level >= 3 else []
+    pair_k = {pq: k for k, pq in enumerate(pairs)}
+    m_pair = np.ones(len(pairs))                  # coefficient of each pair term
+    c_mono = np.ones(nf)                          # coefficient of each E'_I
     for (I, J), ok in zip(pairs, scc):
         if ok:
-            n_scc[I] += 1
-            n_scc[J] += 1
+            c_mono[I] -= 1.0
+            c_mono[J] -= 1.0
+    for t in tris:
+        for pq in ((t[0], t[1]), (t[0], t[2]), (t[1], t[2])):
+            k = pair_k[pq]
+            m_pair[k] -= 1.0
+            if scc[k]:                            # -dE_IJ gives +E'_I, +E'_J back
+                c_mono[pq[0]] += 1.0
+                c_mono[pq[1]] += 1.0
+        for I in t:
+            c_mono[I] -= 1.0
     off = np.cumsum([0] + [len(x) for x in q])
     w = np.zeros(off[-1])
     grad = np.zeros((n_all, 3))
@@ -241,32 +268,38 @@ def fmo2_gradient(system, params, opts=None, tol=1e-12) -> np.ndarray:
         esp = esp_of((I,))[0]
         gI, sigI = explicit(atoms[I], bases[I], prob, res, esp)
         mono[I] = (prob, res, sigI)
-        c = 1.0 - n_scc[I]
+        c = c_mono[I]
         grad += c * gI
         w[off[I]:off[I + 1]] -= c * esp
-    # SCC dimers: L_IJ - esp_IJ . (dq_I + dq_J); ES-DIM pairs: dq_I Gamma_IJ dq_J
-    for (I, J), ok in zip(pairs, scc):
-        if not ok:
-            grad += _gamma_pair_grad(xyz, sh_at[I], eta[I], q[I], sh_at[J], eta[J], q[J], kg, n_all)
-            w[off[I]:off[I + 1]] += gam[I][J] @ q[J]
-            w[off[J]:off[J + 1]] += gam[J][I] @ q[I]
+    # n-mer terms m_X [L_X - esp_X . (sum of its monomer charges)] for SCC
+    # dimers and trimers; ES-DIM pairs m_IJ dq_I Gamma_IJ dq_J
+    nmers = [(pq, m_pair[k]) for k, (pq, ok) in enumerate(zip(pairs, scc)) if ok] + [(t, 1.0) for t in tris]
+    for k, ((I, J), ok) in enumerate(zip(pairs, scc)):
+        m = m_pair[k]
+        if ok or m == 0.0:
             continue
-        at, esp, prob, res = solve((I, J))
+        grad += m * _gamma_pair_grad(xyz, sh_at[I], eta[I], q[I], sh_at[J], eta[J], q[J], kg, n_all)
+        w[off[I]:off[I + 1]] += m * (gam[I][J] @ q[J])
+        w[off[J]:off[J + 1]] += m * (gam[J][I] @ q[I])
+    for X, m in nmers:
+        if m == 0.0:
+            continue
+        at, esp, prob, res = solve(X)
         b = xtb.make_basis(Z[at], params)
-        gIJ, _ = explicit(at, b, prob, res, esp)
-        grad += gIJ
-        nI = len(q[I])
-        ddq = res.dq - np.concatenate([q[I], q[J]])
-        eI, eJ = esp[:nI], esp[nI:]
-        w[off[I]:off[I + 1]] -= eI
-        w[off[J]:off[J + 1]] -= eJ
+        gX, _ = explicit(at, b, prob, res, esp)
+        grad += m * gX
+        ddq = res.dq - np.concatenate([q[I] for I in X])
+        o0 = np.cumsum([0] + [len(q[I]) for I in X])
+        for a, I in enumerate(X):
+            w[off[I]:off[I + 1]] -= m * esp[o0[a]:o0[a + 1]]
         for K in range(nf):
-            if K in (I, J):
+            if K in X:
                 continue
-            # ddq . dGamma_{IJ,K} dq_K (explicit) and ddq . Gamma_{IJ,K} dq_K' (into w)
-            grad += _gamma_pair_grad(xyz, sh_at[I], eta[I], ddq[:nI], sh_at[K], eta[K], q[K], kg, n_all)
-            grad += _gamma_pair_grad(xyz, sh_at[J], eta[J], ddq[nI:], sh_at[K], eta[K], q[K], kg, n_all)
-            w[off[K]:off[K + 1]] += gam[K][I] @ ddq[:nI] + gam[K][J] @ ddq[nI:]
+            # ddq . dGamma_{X,K} dq_K (explicit) and ddq . Gamma_{X,K} dq_K' (into w)
+            for a, I in enumerate(X):
+                dd = ddq[o0[a]:o0[a + 1]]
+                grad += m * _gamma_pair_grad(xyz, sh_at[I], eta[I], dd, sh_at[K], eta[K], q[K], kg, n_all)
+                w[off[K]:off[K + 1]] += m * (gam[K][I] @ dd)
 
     # response: z = (1 - Gamma chi)^-1 w; z . dQ/dxi|_esp + (chi z)^T dGamma dq
     n_sh = off[-1]

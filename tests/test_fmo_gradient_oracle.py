@@ -68,3 +68,18 @@ def test_fmo2_gradient_equals_finite_differences(params, water64, frags, all_scc
     g = fmo_gradient.fmo2_gradient(s, params, opts)
     fd = gradient.fmo_gradient(s, params, opts)
     assert np.max(np.abs(g - fd)) < FD_TOL
+
+
+def test_fmo3_gradient_of_three_fragments_is_the_whole_system_gradient(params, water3):
+    # FMO3 with all dimers and the trimer SCC reproduces the whole system
+    opts = ofmo.FMOOptions(level=3, all_dimers_scc=True, trimer_cut=1e9)
+    g = fmo_gradient.fmo3_gradient(water3, params, opts)
+    assert np.max(np.abs(g - gradient.scc_gradient(water3.Z, water3.xyz, params))) < 1e-10
+
+
+def test_fmo3_gradient_equals_finite_differences(params, water64):
+    s = water64.subsystem([0, 1, 2, 3])
+    opts = ofmo.FMOOptions(level=3, all_dimers_scc=True, trimer_cut=1e9)
+    assert len(ofmo.fmo(s, params, opts).trimers) == 4
+    g = fmo_gradient.fmo3_gradient(s, params, opts)
+    assert np.max(np.abs(g - gradient.fmo_gradient(s, params, opts))) < FD_TOL
