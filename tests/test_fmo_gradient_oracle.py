@@ -83,3 +83,13 @@ def test_fmo3_gradient_equals_finite_differences(params, water64):
     assert len(ofmo.fmo(s, params, opts).trimers) == 4
     g = fmo_gradient.fmo3_gradient(s, params, opts)
     assert np.max(np.abs(g - gradient.fmo_gradient(s, params, opts))) < FD_TOL
+
+
+def test_fmo2_gradient_of_six_waters_rmsd(params, water64):
+    # the accuracy bar for the analytic gradient: RMSD against central
+    # differences well below 1e-7 Eh/bohr on a (H2O)_6 cluster (4.0 A rule)
+    s = water64.subsystem(range(6))
+    opts = ofmo.FMOOptions(level=2)
+    g = fmo_gradient.fmo2_gradient(s, params, opts)
+    fd = gradient.fmo_gradient(s, params, opts)
+    assert np.sqrt(np.mean((g - fd) ** 2)) < 1e-8
