@@ -23,7 +23,7 @@ contracted s/p Gaussians is the derivative of the closed form that
 xtb.overlap_matrix evaluates: with R = A - B, mu = ab/p, s00 = (pi/p)^1.5
 exp(-mu R^2), PA = -(b/p) R and PB = (a/p) R.
 
-READING C-18: the CN counting function is cut at cn_cutoff (READING C-3), so
+READING C-19: the CN counting function is cut at cn_cutoff (READING C-3), so
 the gradient is that of the cut sum (no pair within the cut contributes a
 derivative at the cut itself).
 
