@@ -295,8 +295,8 @@ fmo_status fmo_get_trimers(fmo_ctx *ctx, int64_t *n, int32_t *ijk, double *dE3, 
  * terms of several fragments (explicit embedding, charge-transfer and ES-DIM
  * terms and the self-consistent Z-vector response) are not built.
  * Errors: FMO_ERR_ARG (NULL), FMO_ERR_STATE (no run), FMO_ERR_UNSUPPORTED
- * (several fragments, cut bonds, mixed precision, more than 2048 atoms),
- * FMO_ERR_CUDA.
+ * (several fragments, cut bonds, mixed precision, more than 2048 atoms,
+ * fractional occupations: a HOMO-LUMO gap of fewer than ~25 kT), FMO_ERR_CUDA.
  */
 fmo_status fmo_get_gradient(fmo_ctx *ctx, double *grad);
 

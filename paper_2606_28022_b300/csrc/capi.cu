@@ -1412,21 +1412,30 @@ fmo_status fmo_get_gradient(fmo_ctx* ctx, double* grad) {
     return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: only a system that is one fragment without cut bonds");
   if (ctx->last_precision != FMO_PREC_FP64)
     return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: needs a run in precision FP64");
+  g_ctx = ctx;
   cudaSetDevice(ctx->device);
   cudaStream_t st = ctx->own_stream;
   Pass& P = ctx->mono;
   const Nmer& m = P.nm[0];
   if (m.nat > 8 * kBlock) return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: more than 2048 atoms");
   CK(ctx->d_grad_work.ensure(sizeof(double) * 4 * (size_t)m.n * m.n));
-  CK(ctx->d_grad.ensure(sizeof(double) * 3 * (size_t)m.nat));
+  CK(ctx->d_grad.ensure(sizeof(double) * 3 * (size_t)m.nat + sizeof(int)));
+  int* d_frac = reinterpret_cast<int*>(ctx->d_grad.as<double>() + 3 * (size_t)m.nat);
+  CK(cudaMemsetAsync(d_frac, 0, sizeof(int), st));
   CK(launch_xtb_gradient(st, P.d_nm.as<Nmer>(), m.n, m.nsh, m.nat, ctx->ftab(), ctx->d_xyz.as<double>(),
                          ctx->d_elem.as<int>(), ctx->d_atom_sh0.as<int>(), ctx->d_el.as<DevElem>(),
                          ctx->d_kab.as<double>(), ctx->ne, ctx->d_prim.as<PrimPair>(), ctx->d_cn.as<double>(), ctx->g,
                          P.S.as<double>(), P.H0.as<double>(), P.CTd.as<double>(), P.eps.as<double>(),
-                         P.gam.as<double>(), ctx->d_grad_work.as<double>(), ctx->d_grad.as<double>()));
+                         P.gam.as<double>(), ctx->d_grad_work.as<double>(), ctx->d_grad.as<double>(), d_frac));
   std::vector<double> g(3 * (size_t)m.nat);
+  int frac = 0;
   CK(d2h(g.data(), ctx->d_grad.p, sizeof(double) * g.size(), st));
+  CK(d2h(&frac, d_frac, sizeof(int), st));
   CK(sync_stream(st));
+  if (frac)
+    return fail(ctx, FMO_ERR_UNSUPPORTED,
+                "gradient: fractional occupations (a gap of fewer than ~25 kT); the energy-weighted density "
+                "is formed for occupations of 2 or 0");
   for (int i = 0; i < m.nat; ++i)   // internal atom order -> input order
     for (int c = 0; c < 3; ++c) grad[3 * ctx->perm[i] + c] = g[3 * (size_t)i + c];
   return FMO_OK;

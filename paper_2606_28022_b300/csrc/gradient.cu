@@ -52,6 +52,7 @@ struct GradArgs {
   double* T;
   double* W;
   double* grad;          // [nat][3], local atom order
+  int* frac;             // set to 1 if an occupation is not 2 or 0 to 1e-10
 };
 
 __global__ void __launch_bounds__(kBlock) xtb_gradient_kernel(GradArgs ar) {
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kBlock) xtb_gradient_kernel(GradArgs ar) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double x = fmin(fmax((ar.eps[nm.aov + i] - s_ef) / ar.g.kT, -700.0), 700.0);
     focc[i] = 2.0 / (exp(x) + 1.0);
+    if (focc[i] > 1e-10 && focc[i] < 2.0 - 1e-10) *ar.frac = 1;   // W~ = 1/2 PFP needs 2 or 0
   }
   __syncthreads();
   // 2. density (rows of CT are the orbitals)
@@ -308,14 +310,14 @@ cudaError_t launch_xtb_gradient(cudaStream_t st, const Nmer* nm, int n, int nsh,
                                 const double* xyz, const int* elem, const int* atom_sh0, const DevElem* el,
                                 const double* kab, int ne, const PrimPair* prim, const double* cn, GParams g,
                                 const double* S, const double* H0, const double* CT, const double* eps,
-                                const double* gam, double* work, double* grad) {
+                                const double* gam, double* work, double* grad, int* frac) {
   if (nat > 8 * kBlock) return cudaErrorInvalidValue;
   GradArgs ar;
   ar.nm = nm; ar.ft = ft; ar.xyz = xyz; ar.elem = elem; ar.atom_sh0 = atom_sh0; ar.el = el; ar.kab = kab;
   ar.ne = ne; ar.prim = prim; ar.cn = cn; ar.g = g; ar.S = S; ar.H0 = H0; ar.CT = CT; ar.eps = eps; ar.gam = gam;
   const size_t nn = (size_t)n * n;
   ar.P = work; ar.F = work + nn; ar.T = work + 2 * nn; ar.W = work + 3 * nn;
-  ar.grad = grad;
+  ar.grad = grad; ar.frac = frac;
   const size_t sb = gradient_smem(n, nsh, nat);
   cudaError_t e = cudaFuncSetAttribute(xtb_gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
   if (e != cudaSuccess) return e;

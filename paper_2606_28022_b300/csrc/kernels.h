@@ -123,12 +123,13 @@ cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const 
                          GParams g, double* out, const double* gam_full = nullptr, int n_sh = 0);
 // Analytic gradient of the GFN1-xTB energy of one n-mer that is one fragment
 // without hybrid-orbital projection (gradient.cu): grad[nat][3] in the
-// fragment's atom order; work holds 4 n^2 doubles.
+// fragment's atom order; work holds 4 n^2 doubles; *frac (zeroed by the
+// caller) is set to 1 if an occupation is fractional.
 cudaError_t launch_xtb_gradient(cudaStream_t st, const Nmer* nm, int n, int nsh, int nat, FragTab ft,
                                 const double* xyz, const int* elem, const int* atom_sh0, const DevElem* el,
                                 const double* kab, int ne, const PrimPair* prim, const double* cn, GParams g,
                                 const double* S, const double* H0, const double* CT, const double* eps,
-                                const double* gam, double* work, double* grad);
+                                const double* gam, double* work, double* grad, int* frac);
 // out[i] = (float)in[i], i < n
 cudaError_t launch_to_float(cudaStream_t st, long long n, const double* in, float* out);
 cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t);

@@ -54,3 +54,16 @@ def test_gradient_refuses_what_it_does_not_cover(gpu, params, water64):
     gpu.run(fmo.options(precision="mixed"))
     with pytest.raises(fmo.FMOError):
         gpu.gradient()                                   # mixed precision
+
+
+def test_gradient_refuses_fractional_occupations(params):
+    # a high electronic temperature smears the occupations: the energy-weighted
+    # density of the kernel (1/2 P F P) needs occupations of 2 or 0
+    from paper_2606_28022_b300 import fmo
+    hot = dataclasses.replace(params, t_el=20000.0)
+    g = fmo.FMO(hot, 0)
+    g.set_system(G.polyalanine_helix(1))
+    g.run(fmo.options(level=1))
+    with pytest.raises(fmo.FMOError):
+        g.gradient()
+    g.close()
