@@ -54,6 +54,20 @@ def workload(rank: int, n_mol: int = 128):
     return system, info
 
 
+def job_rate(t_total: float, solves: float, dev=None):
+    """Whole-job throughput over all ranks: the solves of every rank divided by
+    the slowest rank's timed seconds.  Returns (rate, t_max, solves_all)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(solves) / t_total, t_total, float(solves)
+    t = torch.tensor([t_total, float(solves)], dtype=torch.float64, device=dev)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t[1]) / float(tmax[0]), float(tmax[0]), float(t[1])
+
+
 def clocks_sampler(dev_index: int):
     """Sample nvidia-smi clocks / throttle reasons in the background."""
     cmd = ["nvidia-smi", "-i", str(dev_index),
@@ -231,16 +245,7 @@ def main():
     t_total = sum(step_ms) / 1e3
     solves = sum(s["n_monomer_solves"] + s["n_dimer_scc"] + s["n_trimer_scc"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
-    if world > 1:
-        t = torch.tensor([t_total, float(solves)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        t_total_max = float(tmax[0])
-        solves_all = float(t[1])
-    else:
-        t_total_max, solves_all = t_total, float(solves)
-    value = solves_all / t_total_max
+    value, t_total_max, solves_all = job_rate(t_total, solves, dev)
 
     e1, e2, _ = g.energies()
     s0 = stats[-1]
