@@ -23,10 +23,13 @@ that the potential z_I causes (coupled-perturbed SCC, as in
 oracle/response.py; W~ = sum f_i e_i c_i c_i^T changes by
 C [N o (C^T dF C)] C^T with N_ij = (f_i e_i - f_j e_j)/(e_i - e_j), minus
 the Fermi-level shift).  FMO2 (fmo2_gradient) adds the SCC dimers and the
-ES-DIM pairs in the same form, FMO3 (fmo3_gradient) the trimer corrections.
-Systems without cut bonds.  Central differences of the oracle's FMO1, FMO2
-and FMO3 energies pin them, and so does the exact identity of FMO3 of three
-fragments with the whole system (tests/test_fmo_gradient_oracle.py).
+ES-DIM pairs in the same form, FMO3 (fmo3_gradient) the trimer corrections;
+these take systems without cut bonds.  fmo1_gradient_hop covers FMO1 with cut
+bonds (hybrid orbital projection, HOP section): ghost records, the projector
+term Tr(P dV/dxi), and the derivative of the Tr(P V^HOP) that E'_I leaves
+out.  Central differences of the oracle's FMO1, FMO2 and FMO3 energies pin
+them, and so does the exact identity of FMO3 of three fragments with the
+whole system (tests/test_fmo_gradient_oracle.py).
 """
 from __future__ import annotations
 
@@ -165,7 +168,10 @@ def _gamma_pair_grad(xyz, at_a, eta_a, ca, at_b, eta_b, cb, k_g, n_all):
     ee = 2.0 / (1.0 / eta_a[:, None] + 1.0 / eta_b[None, :])
     gm = (rr ** k_g + ee ** (-k_g)) ** (-1.0 / k_g)
     dg = -rr ** (k_g - 1.0) * gm ** (1.0 + k_g)
-    v = (ca[:, None] * cb[None, :] * dg / rr)[..., None] * rv
+    with np.errstate(divide="ignore", invalid="ignore"):
+        # a ghost and its own bond-detachment atom share one position and
+        # move together: their distance has no gradient
+        v = np.where((rr > 0.0)[..., None], (ca[:, None] * cb[None, :] * dg / rr)[..., None] * rv, 0.0)
     np.add.at(g, at_a, v.sum(axis=1))
     np.add.at(g, at_b, -v.sum(axis=0))
     return g
@@ -325,4 +331,158 @@ def _nmer_gradient(system, params, opts, level, tol):
             if K != I:
                 grad += _gamma_pair_grad(xyz, sh_at[I], eta[I], y[off[I]:off[I + 1]], sh_at[K], eta[K], q[K],
                                          kg, n_all)
+    return grad
+
+
+def _first_order_general(prob, res, dv=None, dF_ext=None):
+    """_first_order for a shell potential dv and/or an AO-matrix perturbation
+    dF_ext of the Fock matrix (kept out of the shifts)."""
+    b = prob.basis
+    sh = b.ao_shell
+    C, eps, f = res.C, res.eps, res.occ
+    fp = -2.0 * (f / 2.0) * (1.0 - f / 2.0) / prob.kT
+    de = eps[:, None] - eps[None, :]
+    fe = f * eps
+    with np.errstate(divide="ignore", invalid="ignore"):
+        M = np.where(np.abs(de) > 1e-12, (f[:, None] - f[None, :]) / de, 0.5 * (fp[:, None] + fp[None, :]))
+        dfe = fp * eps + f
+        N = np.where(np.abs(de) > 1e-12, (fe[:, None] - fe[None, :]) / de, 0.5 * (dfe[:, None] + dfe[None, :]))
+    sfp = fp.sum()
+
+    def orbital(dF):
+        dFm = C.T @ dF @ C
+        X = M * dFm
+        Y = N * dFm
+        if abs(sfp) > 0.0:
+            def_ = float(fp @ np.diag(dFm)) / sfp
+            X = X - np.diag(fp * def_)
+            Y = Y - np.diag(fp * eps * def_)
+        return C @ X @ C.T, C @ Y @ C.T
+
+    chi0 = response.bare_response(prob, res)
+    K = response.charge_kernel(prob, res)
+    n_sh = b.n_sh
+    src = np.zeros(n_sh)
+    if dv is not None:
+        src = src + chi0 @ dv
+    if dF_ext is not None:
+        dP0, _ = orbital(dF_ext)
+        src = src + np.bincount(sh, weights=(dP0 * prob.S).sum(axis=1), minlength=n_sh)
+    dq = np.linalg.solve(np.eye(n_sh) - chi0 @ K, src)
+    dsig = K @ dq + (dv if dv is not None else 0.0)
+    dF = 0.5 * prob.S * (dsig[sh][:, None] + dsig[sh][None, :])
+    if dF_ext is not None:
+        dF = dF + dF_ext
+    dP, dWt = orbital(dF)
+    return dq, dsig, dP, dWt
+
+
+def _records(fr, nmer):
+    """Records of an n-mer (supersystem atom, cut bond or -1), its repulsion
+    mask and its projected records for explicit_gradient (as ofmo._Frags.problem)."""
+    s = fr.system
+    recs = [r for k, f in enumerate(nmer) for r, keep in zip(fr.recs[f], fr.present(nmer)[k]) if keep]
+    at = np.array([a for a, _ in recs], dtype=np.int64)
+    rep_mask = np.array([bond < 0 for _, bond in recs])
+    hop = []
+    for i, (a, bond) in enumerate(recs):
+        ks = [(bond, "ghost")] if bond >= 0 else \
+             [(k, "bda") for k in range(len(fr.cut)) if fr.cut[k, 0] == a and fr.bond_frag[k][1] not in nmer]
+        for k, kind in ks:
+            bda, baa = int(fr.cut[k, 0]), int(fr.cut[k, 1])
+            v = s.xyz[baa] - s.xyz[bda]
+            n = float(np.linalg.norm(v))
+            hop.append((i, kind, bda, baa, v / n, n))
+    return at, rep_mask, hop
+
+
+def fmo1_gradient_hop(system, params, tol=1e-12) -> np.ndarray:
+    """dE_FMO1/dxyz with cut bonds (hybrid orbital projection): as
+    fmo1_gradient, with E'_I = L_I - esp_I . dq_I - Tr(P_I V_I^HOP).  The last
+    term is not stationary in the monomer density: its derivative is that of
+    the explicit gradient along the Fock perturbation V^HOP (the projector
+    scaled by 1 + lambda), plus its charge response times d esp_I/dxi."""
+    Z = np.asarray(system.Z)
+    xyz = np.asarray(system.xyz, dtype=np.float64)
+    nf = system.n_frag
+    n_all = len(Z)
+    fr = ofmo._Frags(system, params)
+    dcn_all = gradient.cn_derivative(Z, xyz, params)
+    r = ofmo.fmo(system, params, ofmo.FMOOptions(level=1, scc_tol=tol, e_tol=0.1 * tol, outer_tol=tol))
+    q = [np.asarray(d, dtype=np.float64) for d in r.dq_mono]
+    kg = params.k_g
+    sh_at = []
+    mono = []
+    for I in range(nf):
+        at, rep_mask, hop = _records(fr, (I,))
+        sh_at.append(at[fr.sh_rec[I]])
+        mono.append((at, rep_mask, hop))
+    esp = [fr.esp((I,), q) for I in range(nf)]
+    probs, ress = [], []
+    for I in range(nf):
+        prob = fr.problem((I,), esp[I])
+        res = xtb.solve_problem(prob, guess=q[I], tol=tol, e_tol=0.1 * tol)
+        probs.append(prob)
+        ress.append(res)
+        q[I] = res.dq
+    esp = [fr.esp((I,), q) for I in range(nf)]
+    off = np.cumsum([0] + [len(x) for x in q])
+    w = np.zeros(off[-1])
+    grad = np.zeros((n_all, 3))
+    sigs = []
+
+    def explicit(I, P, Wt, sig, Q, with_rep=True, M_extra=None):
+        at, rep_mask, hop = mono[I]
+        return gradient.explicit_gradient(Z[at], xyz[at], params, probs[I].basis, P, Wt, sig, Q, fr.cn[at],
+                                          dcn_all[at], atoms=at, n_all=n_all, with_rep=with_rep,
+                                          M_extra=M_extra, rep_mask=rep_mask, hop=hop)
+
+    for I in range(nf):
+        prob, res = probs[I], ress[I]
+        at, rep_mask, hop = mono[I]
+        b = prob.basis
+        dq_at = np.bincount(b.sh_atom, weights=res.dq, minlength=len(at))
+        sig = prob.gam @ res.dq - prob.g3[b.sh_atom] * dq_at[b.sh_atom] ** 2 + esp[I]
+        sigs.append(sig)
+        Wt = (res.C * (res.occ * res.eps)) @ res.C.T
+        grad += explicit(I, res.P, Wt, sig, np.outer(res.dq, res.dq))      # dL_I/dxi|_esp
+        w[off[I]:off[I + 1]] -= esp[I]
+        if hop and prob.extra_fock is not None:
+            # - d Tr(P V)/dxi = - [d/dlambda of the explicit gradient] - dq^V . d esp_I/dxi
+            dqv, dsig, dP, dWt = _first_order_general(prob, res, dF_ext=prob.extra_fock)
+            sh = b.ao_shell
+            M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
+            Q = np.outer(res.dq, dqv) + np.outer(dqv, res.dq)
+            grad -= explicit(I, dP, dWt, sig, Q, with_rep=False, M_extra=M_extra)
+            grad -= gradient._hop_gradient(Z[at], xyz[at], params, b, prob.S,
+                                           gradient.overlap_derivative(Z[at], xyz[at], params, b), res.P, hop,
+                                           at, n_all)
+            for K in range(nf):
+                if K == I:
+                    continue
+                grad -= _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], dqv, sh_at[K], fr.sh_eta[K], q[K], kg, n_all)
+                w[off[K]:off[K + 1]] -= fr.gamma(K, I) @ dqv
+    if nf == 1:
+        return grad
+    n_sh = off[-1]
+    G = np.zeros((n_sh, n_sh))
+    chi = np.zeros((n_sh, n_sh))
+    for I in range(nf):
+        chi[off[I]:off[I + 1], off[I]:off[I + 1]] = response.susceptibility(probs[I], ress[I])
+        for K in range(nf):
+            if K != I:
+                G[off[I]:off[I + 1], off[K]:off[K + 1]] = fr.gamma(I, K)
+    z = np.linalg.solve(np.eye(n_sh) - G @ chi, w)
+    y = chi @ z
+    for I in range(nf):
+        prob, res = probs[I], ress[I]
+        dq1, dsig, dP, dWt = _first_order_general(prob, res, dv=z[off[I]:off[I + 1]])
+        sh = prob.basis.ao_shell
+        M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
+        Q = np.outer(res.dq, dq1) + np.outer(dq1, res.dq)
+        grad += explicit(I, dP, dWt, sigs[I], Q, with_rep=False, M_extra=M_extra)
+        for K in range(nf):
+            if K != I:
+                grad += _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], y[off[I]:off[I + 1]], sh_at[K],
+                                         fr.sh_eta[K], q[K], kg, n_all)
     return grad

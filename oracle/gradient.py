@@ -124,7 +124,7 @@ def cn_derivative(Z, xyz, params) -> np.ndarray:
 
 
 def explicit_gradient(Z, xyz, params, basis, P, Wt, sigma, Q, cn, dcn, atoms=None, n_all=None,
-                      with_rep=True, M_extra=None) -> np.ndarray:
+                      with_rep=True, M_extra=None, rep_mask=None, hop=None) -> np.ndarray:
     """The explicit terms of Eqs. 23-28 for one system at fixed P, W~, shell
     shifts sigma and charge product Q (n_sh x n_sh, Q = dq dq^T for the
     energy): sum dS (P H + 1/2 (sigma_mu + sigma_nu) P - W~ [+ M_extra])
@@ -132,7 +132,11 @@ def explicit_gradient(Z, xyz, params, basis, P, Wt, sigma, Q, cn, dcn, atoms=Non
     cn: the CN of the system's atoms (in FMO: supersystem values); dcn
     [a, k, c]: their derivatives with respect to every atom k of the
     supersystem (n_all atoms); atoms: the system's atoms in the supersystem
-    (default: all).  Returns n_all x 3."""
+    (default: all; a ghost record of the hybrid orbital projection maps to
+    its bond-detachment atom).  rep_mask: records in the repulsion (default
+    all); hop: the projected records, [(record, kind "bda"|"ghost", BDA atom,
+    BAA atom, unit vector BDA -> BAA, bond length)], whose projector V = sum S[:,A] D_A S[A,:] is in the Fock
+    matrix: adds Tr(P dV/dxi).  Returns n_all x 3."""
     Z = np.asarray(Z)
     xyz = np.asarray(xyz, dtype=np.float64)
     b = basis
@@ -204,8 +208,11 @@ def explicit_gradient(Z, xyz, params, basis, P, Wt, sigma, Q, cn, dcn, atoms=Non
     if with_rep:
         zeff = xtb.atom_param(Z, params, "z_eff")
         arep = xtb.atom_param(Z, params, "alpha_rep")
+        rm = np.ones(n_at, dtype=bool) if rep_mask is None else np.asarray(rep_mask, dtype=bool)
         for a in range(n_at):
             for c in range(a):
+                if not (rm[a] and rm[c]):
+                    continue
                 rv = xyz[a] - xyz[c]
                 r = float(np.linalg.norm(rv))
                 al = np.sqrt(arep[a] * arep[c])
@@ -214,7 +221,9 @@ def explicit_gradient(Z, xyz, params, basis, P, Wt, sigma, Q, cn, dcn, atoms=Non
                 grad[a] += de * rv / r
                 grad[c] -= de * rv / r
     out = np.zeros((n_all, 3))
-    out[atoms] += grad
+    np.add.at(out, atoms, grad)
+    if hop:
+        out += _hop_gradient(Z, xyz, params, b, S, dS, P, hop, atoms, n_all)
     # (3) CN-dependent levels (Eqs. 10, 26-28): F_A = dE/dCN_A, then the chain
     # rule over every atom the CN depends on
     dh_ao = (h_l * k_cn)[sh]                                            # dh_l / dCN of the shell's atom
@@ -224,6 +233,37 @@ def explicit_gradient(Z, xyz, params, basis, P, Wt, sigma, Q, cn, dcn, atoms=Non
     np.add.at(F, at, (Hcn * dh_ao[:, None]).sum(axis=1))
     np.add.at(F, at, (Hcn * dh_ao[None, :]).sum(axis=0))
     out += np.einsum("a,akc->kc", F, dcn)
+    return out
+
+
+def _hop_gradient(Z, xyz, params, b, S, dS, P, hop, atoms, n_all):
+    """Tr(P dV/dxi) of the hybrid-orbital projector V = sum_A S[:,A] D_A S[A,:]
+    with D = V_hop h h^T (detached BDA) or V_hop (1 - h h^T) (ghost), h =
+    (c_s, c_p b) on the record's s and p functions, b the unit vector from
+    the BDA to the BAA (HOP section)."""
+    from .fmo import C_P, C_S
+    out = np.zeros((n_all, 3))
+    X = np.zeros_like(P)
+    for rec, kind, bda, baa, bvec, blen in hop:
+        sh = np.nonzero(b.sh_atom == rec)[0]
+        s_sh = sh[b.sh_l[sh] == 0][0]
+        p_sh = sh[b.sh_l[sh] == 1][0]
+        idx = np.concatenate([[b.sh_ao0[s_sh]], b.sh_ao0[p_sh] + np.arange(3)])
+        h = np.concatenate([[C_S], C_P * bvec])
+        sign = 1.0 if kind == "bda" else -1.0
+        D = params.v_hop * (np.outer(h, h) if kind == "bda" else np.eye(4) - np.outer(h, h))
+        # dS part: 2 sum_{mu, a in A} dS_mu,a (P S[:,A] D)_mu,a
+        X[:, idx] += 2.0 * (P @ S[:, idx] @ D)
+        # dD part: <S[A,:] P S[:,A], dD>, dD = sign V_hop (dh h^T + h dh^T),
+        # dh = c_p (0, db), db = J dx_BAA - J dx_BDA, J = (1 - b b^T) / |b|
+        G = S[idx, :] @ P @ S[:, idx]
+        gh = (G @ h)[1:]
+        J = (np.eye(3) - np.outer(bvec, bvec)) / blen
+        v = sign * params.v_hop * 2.0 * C_P * (J @ gh)
+        out[baa] += v
+        out[bda] -= v
+    g = np.einsum("kcij,ij->kc", dS, X)
+    np.add.at(out, atoms, g)
     return out
 
 

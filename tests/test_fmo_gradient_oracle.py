@@ -93,3 +93,24 @@ def test_fmo2_gradient_of_six_waters_rmsd(params, water64):
     g = fmo_gradient.fmo2_gradient(s, params, opts)
     fd = gradient.fmo_gradient(s, params, opts)
     assert np.sqrt(np.mean((g - fd) ** 2)) < 1e-8
+
+
+def test_fmo1_gradient_with_cut_bonds_equals_finite_differences(params, water3):
+    # hybrid orbital projection: E'_I leaves Tr(P V^HOP) out, which the
+    # monomer density does not make stationary (its own response enters)
+    s = G.polyalanine_helix(2)
+    assert len(s.cut_bonds) == 1
+    g = fmo_gradient.fmo1_gradient_hop(s, params)
+    opts = ofmo.FMOOptions(level=1, scc_tol=1e-12, e_tol=1e-13, outer_tol=1e-12)
+    energy = lambda x: ofmo.fmo(dataclasses.replace(s, xyz=x), params, opts).e_fmo1
+    bda, baa = (int(a) for a in s.cut_bonds[0])
+    for k in (bda, baa, 7):
+        for c in range(3):
+            xp = s.xyz.copy(); xp[k, c] += 1e-4
+            xm = s.xyz.copy(); xm[k, c] -= 1e-4
+            # the 1e6 Eh projector leaves ~1e-8 of noise in these differences
+            assert abs((energy(xp) - energy(xm)) / 2e-4 - g[k, c]) < 2e-7
+    assert np.max(np.abs(g.sum(axis=0))) < 1e-12
+    # without cut bonds the general form reduces to fmo1_gradient
+    assert np.max(np.abs(fmo_gradient.fmo1_gradient_hop(water3, params)
+                         - fmo_gradient.fmo1_gradient(water3, params))) < 1e-12
