@@ -27,7 +27,8 @@ ES-DIM pairs in the same form, FMO3 (fmo3_gradient) the trimer corrections;
 these take systems without cut bonds.  fmo1_gradient_hop covers FMO1 with cut
 bonds (hybrid orbital projection, HOP section): ghost records, the projector
 term Tr(P dV/dxi), and the derivative of the Tr(P V^HOP) that E'_I leaves
-out.  Central differences of the oracle's FMO1, FMO2 and FMO3 energies pin
+out.  fmo_gradient_records is the general form (FMO1/2/3, cut bonds healed
+in the n-mers that hold both of their fragments).  Central differences of the oracle's FMO1, FMO2 and FMO3 energies pin
 them, and so does the exact identity of FMO3 of three fragments with the
 whole system (tests/test_fmo_gradient_oracle.py).
 """
@@ -481,6 +482,147 @@ def fmo1_gradient_hop(system, params, tol=1e-12) -> np.ndarray:
         M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
         Q = np.outer(res.dq, dq1) + np.outer(dq1, res.dq)
         grad += explicit(I, dP, dWt, sigs[I], Q, with_rep=False, M_extra=M_extra)
+        for K in range(nf):
+            if K != I:
+                grad += _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], y[off[I]:off[I + 1]], sh_at[K],
+                                         fr.sh_eta[K], q[K], kg, n_all)
+    return grad
+
+
+def fmo_gradient_records(system, params, opts=None, tol=1e-12) -> np.ndarray:
+    """dE_FMO/dxyz at opts.level (1, 2 or 3) for systems with or without cut
+    bonds, in one form: every monomer I (coefficient c_I) and every SCC dimer
+    and trimer X (coefficient m_X) contributes
+        L_X - Tr(P_X V_X^HOP) - esp_X . (monomer charges of X's fragments),
+    with L_X = E'_X + esp_X . dq_X + Tr(P_X V_X) stationary in the n-mer
+    density, esp_X on every monomer shell of X's fragments (a healed ghost
+    keeps its monomer charge there, its n-mer charge is zero: the -dq_mono
+    charge transfer of dE^V), and ES-DIM pairs m_IJ dq_I Gamma_IJ dq_J.  The
+    coefficients count the FMO2/FMO3 subtractions (fmo3_gradient)."""
+    import dataclasses
+    opts = ofmo.FMOOptions() if opts is None else opts
+    level = opts.level
+    Z = np.asarray(system.Z)
+    xyz = np.asarray(system.xyz, dtype=np.float64)
+    nf = system.n_frag
+    n_all = len(Z)
+    kg = params.k_g
+    fr = ofmo._Frags(system, params)
+    dcn_all = gradient.cn_derivative(Z, xyz, params)
+    r = ofmo.fmo(system, params, dataclasses.replace(opts, scc_tol=tol, e_tol=0.1 * tol, outer_tol=tol))
+    q = [np.asarray(d, dtype=np.float64) for d in r.dq_mono]
+    at_f = [np.array([a for a, _ in fr.recs[f]], dtype=np.int64) for f in range(nf)]
+    sh_at = [at_f[f][fr.sh_rec[f]] for f in range(nf)]               # global atom of each monomer shell
+    off = np.cumsum([0] + [fr.n_sh[f] for f in range(nf)])
+    w = np.zeros(off[-1])
+    grad = np.zeros((n_all, 3))
+
+    # coefficients (as fmo2/fmo3_gradient)
+    pairs = [tuple(int(x) for x in pq) for pq in r.dimers] if level >= 2 else []
+    scc = [bool(x) for x in r.dimer_scc] if level >= 2 else []
+    tris = [tuple(int(x) for x in t) for t in r.trimers] if level >= 3 else []
+    pair_k = {pq: k for k, pq in enumerate(pairs)}
+    m_pair = np.ones(len(pairs))
+    c_mono = np.ones(nf)
+    for (I, J), ok in zip(pairs, scc):
+        if ok:
+            c_mono[I] -= 1.0
+            c_mono[J] -= 1.0
+    for t in tris:
+        for pq in ((t[0], t[1]), (t[0], t[2]), (t[1], t[2])):
+            k = pair_k[pq]
+            m_pair[k] -= 1.0
+            if scc[k]:
+                c_mono[pq[0]] += 1.0
+                c_mono[pq[1]] += 1.0
+        for I in t:
+            c_mono[I] -= 1.0
+    terms = [((I,), c_mono[I]) for I in range(nf)]
+    terms += [(pq, m_pair[k]) for k, (pq, ok) in enumerate(zip(pairs, scc)) if ok]
+    terms += [(t, 1.0) for t in tris]
+
+    mono = {}
+    for X, m in terms:
+        at, rep_mask, hop = _records(fr, X)
+        esp = fr.esp(X, q)                                    # on the n-mer's shells
+        esp_full = fr.esp_full(X, q)                          # on every monomer shell of X
+        mask = fr.shell_mask(X)
+        qmono = np.concatenate([q[f] for f in X])
+        prob = fr.problem(X, esp)
+        res = xtb.solve_problem(prob, guess=qmono[mask], tol=tol, e_tol=0.1 * tol)
+        b = prob.basis
+        dq_at = np.bincount(b.sh_atom, weights=res.dq, minlength=len(at))
+        sig = prob.gam @ res.dq - prob.g3[b.sh_atom] * dq_at[b.sh_atom] ** 2 + esp
+        if len(X) == 1:
+            mono[X[0]] = (prob, res, at, rep_mask, hop, sig)
+        if m == 0.0:
+            continue
+
+        def explicit(P, Wt, Q, with_rep=True, M_extra=None):
+            return gradient.explicit_gradient(Z[at], xyz[at], params, b, P, Wt, sig, Q, fr.cn[at], dcn_all[at],
+                                              atoms=at, n_all=n_all, with_rep=with_rep, M_extra=M_extra,
+                                              rep_mask=rep_mask, hop=hop)
+
+        Wt = (res.C * (res.occ * res.eps)) @ res.C.T
+        grad += m * explicit(res.P, Wt, np.outer(res.dq, res.dq))
+        coef = -qmono.copy()                                   # - esp_full . q_mono
+        qx = np.zeros_like(qmono)
+        qx[mask] = res.dq
+        coef += qx                                             # + esp . dq_X (from dL/d esp)
+        if prob.extra_fock is not None:
+            dqv, dsig, dP, dWt = _first_order_general(prob, res, dF_ext=prob.extra_fock)
+            sh = b.ao_shell
+            M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
+            Q = np.outer(res.dq, dqv) + np.outer(dqv, res.dq)
+            grad -= m * explicit(dP, dWt, Q, with_rep=False, M_extra=M_extra)
+            grad -= m * gradient._hop_gradient(Z[at], xyz[at], params, b, prob.S,
+                                               gradient.overlap_derivative(Z[at], xyz[at], params, b), res.P,
+                                               hop, at, n_all)
+            dv_full = np.zeros_like(qmono)
+            dv_full[mask] = dqv
+            coef -= dv_full                                    # - dq^V . d esp/dxi
+        o0 = np.cumsum([0] + [fr.n_sh[f] for f in X])
+        for a, I in enumerate(X):
+            w[off[I]:off[I + 1]] -= m * esp_full[o0[a]:o0[a + 1]]
+        for K in range(nf):
+            if K in X:
+                continue
+            for a, I in enumerate(X):
+                cI = coef[o0[a]:o0[a + 1]]
+                grad += m * _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], cI, sh_at[K], fr.sh_eta[K], q[K], kg,
+                                             n_all)
+                w[off[K]:off[K + 1]] += m * (fr.gamma(K, I) @ cI)
+    for k, ((I, J), ok) in enumerate(zip(pairs, scc)):
+        mm = m_pair[k]
+        if ok or mm == 0.0:
+            continue
+        grad += mm * _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], q[I], sh_at[J], fr.sh_eta[J], q[J], kg, n_all)
+        w[off[I]:off[I + 1]] += mm * (fr.gamma(I, J) @ q[J])
+        w[off[J]:off[J + 1]] += mm * (fr.gamma(J, I) @ q[I])
+    if nf == 1:
+        return grad
+
+    # response: z = (1 - Gamma chi)^-1 w
+    n_sh = off[-1]
+    G = np.zeros((n_sh, n_sh))
+    chi = np.zeros((n_sh, n_sh))
+    for I in range(nf):
+        chi[off[I]:off[I + 1], off[I]:off[I + 1]] = response.susceptibility(mono[I][0], mono[I][1])
+        for K in range(nf):
+            if K != I:
+                G[off[I]:off[I + 1], off[K]:off[K + 1]] = fr.gamma(I, K)
+    z = np.linalg.solve(np.eye(n_sh) - G @ chi, w)
+    y = chi @ z
+    for I in range(nf):
+        prob, res, at, rep_mask, hop, sig = mono[I]
+        b = prob.basis
+        dq1, dsig, dP, dWt = _first_order_general(prob, res, dv=z[off[I]:off[I + 1]])
+        sh = b.ao_shell
+        M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
+        Q = np.outer(res.dq, dq1) + np.outer(dq1, res.dq)
+        grad += gradient.explicit_gradient(Z[at], xyz[at], params, b, dP, dWt, sig, Q, fr.cn[at], dcn_all[at],
+                                           atoms=at, n_all=n_all, with_rep=False, M_extra=M_extra,
+                                           rep_mask=rep_mask, hop=hop)
         for K in range(nf):
             if K != I:
                 grad += _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], y[off[I]:off[I + 1]], sh_at[K],

@@ -114,3 +114,35 @@ def test_fmo1_gradient_with_cut_bonds_equals_finite_differences(params, water3):
     # without cut bonds the general form reduces to fmo1_gradient
     assert np.max(np.abs(fmo_gradient.fmo1_gradient_hop(water3, params)
                          - fmo_gradient.fmo1_gradient(water3, params))) < 1e-12
+
+
+def test_gradient_with_healed_bonds_equals_whole_molecule(params):
+    # FMO2 of two and FMO3 of three bonded fragments heal every cut bond and
+    # reproduce the whole molecule exactly, so their gradients must too
+    a2 = G.polyalanine_helix(2)
+    g2 = fmo_gradient.fmo_gradient_records(a2, params, ofmo.FMOOptions(level=2, all_dimers_scc=True))
+    assert np.max(np.abs(g2 - gradient.scc_gradient(a2.Z, a2.xyz, params))) < 1e-10
+    a3 = G.polyalanine_helix(3)
+    g3 = fmo_gradient.fmo_gradient_records(a3, params,
+                                           ofmo.FMOOptions(level=3, all_dimers_scc=True, trimer_cut=1e9))
+    assert np.max(np.abs(g3 - gradient.scc_gradient(a3.Z, a3.xyz, params))) < 1e-10
+
+
+def test_fmo2_gradient_with_cut_bonds_equals_finite_differences(params, water64):
+    # Ala3: each bonded dimer heals one bond and keeps the other detached
+    s = G.polyalanine_helix(3)
+    opts = ofmo.FMOOptions(level=2, all_dimers_scc=True)
+    g = fmo_gradient.fmo_gradient_records(s, params, opts)
+    assert np.abs(g - gradient.scc_gradient(s.Z, s.xyz, params)).max() > 1e-4      # not the whole molecule
+    o = dataclasses.replace(opts, scc_tol=1e-12, e_tol=1e-13, outer_tol=1e-12)
+    energy = lambda x: ofmo.fmo(dataclasses.replace(s, xyz=x), params, o).e_fmo2
+    k = int(s.cut_bonds[0][0])
+    for c in range(3):
+        xp = s.xyz.copy(); xp[k, c] += 1e-4
+        xm = s.xyz.copy(); xm[k, c] -= 1e-4
+        assert abs((energy(xp) - energy(xm)) / 2e-4 - g[k, c]) < 2e-7
+    # without cut bonds the record form is the plain FMO2 gradient
+    w4 = water64.subsystem([0, 1, 2, 3])
+    o2 = ofmo.FMOOptions(level=2)
+    assert np.max(np.abs(fmo_gradient.fmo_gradient_records(w4, params, o2)
+                         - fmo_gradient.fmo2_gradient(w4, params, o2))) < 1e-12
