@@ -68,6 +68,21 @@ def job_rate(t_total: float, solves: float, dev=None):
     return float(t[1]) / float(tmax[0]), float(tmax[0]), float(t[1])
 
 
+def pass_rates(stats: list) -> dict:
+    """Fragment-SCC solves per second of each pass (size class) over the timed
+    steps: monomer solves over the monomer stage (setup excluded), SCC dimers
+    over the dimer stage, SCC trimers over the trimer stage."""
+    out = {}
+    for name, n_key, ms_key in (("monomer", "n_monomer_solves", "ms_monomer"),
+                                ("dimer", "n_dimer_scc", "ms_dimer"),
+                                ("trimer", "n_trimer_scc", "ms_trimer")):
+        n = sum(s[n_key] for s in stats)
+        ms = sum(s[ms_key] for s in stats)
+        if n > 0 and ms > 0:
+            out[name] = {"solves": int(n), "stage_ms": float(ms), "per_s": float(n / (ms / 1e3))}
+    return out
+
+
 def clocks_sampler(dev_index: int):
     """Sample nvidia-smi clocks / throttle reasons in the background."""
     cmd = ["nvidia-smi", "-i", str(dev_index),
@@ -328,6 +343,7 @@ def main():
                            "parallelism": f"replicas x{world} (independent frames)", "geometry": geo},
                 "e_fmo1": e1, "e_fmo2": e2, "fp64_form": fp64,
                 "stage_ms": {k: s0[k] for k in ("ms_setup", "ms_monomer", "ms_select", "ms_dimer", "ms_reduce")},
+                "per_pass": pass_rates(stats),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": summarize_clocks(rows)}
         print(json.dumps(line), flush=True)

@@ -49,3 +49,14 @@ def test_single_process_rate_and_rank_workloads():
     assert np.array_equal(s0.Z, s1.Z) and np.array_equal(s0.frag, s1.frag)
     assert not np.allclose(s0.xyz, s1.xyz) and not np.allclose(s1.xyz, s2.xyz)
     assert np.max(np.abs(s1.xyz - s0.xyz)) < 0.5            # a jitter, not a new geometry
+
+
+def test_pass_rates_from_run_stats():
+    sys.path.insert(0, ROOT)
+    import bench
+    st = {"n_monomer_solves": 128, "ms_monomer": 16.0, "n_dimer_scc": 511, "ms_dimer": 28.0,
+          "n_trimer_scc": 0, "ms_trimer": 0.001}
+    r = bench.pass_rates([st, st])
+    assert set(r) == {"monomer", "dimer"}                      # no trimers ran
+    assert r["monomer"]["solves"] == 256 and abs(r["monomer"]["per_s"] - 256 / 0.032) < 1e-6
+    assert abs(r["dimer"]["per_s"] - 1022 / 0.056) < 1e-6
