@@ -402,91 +402,9 @@ def fmo1_gradient_hop(system, params, tol=1e-12) -> np.ndarray:
     fmo1_gradient, with E'_I = L_I - esp_I . dq_I - Tr(P_I V_I^HOP).  The last
     term is not stationary in the monomer density: its derivative is that of
     the explicit gradient along the Fock perturbation V^HOP (the projector
-    scaled by 1 + lambda), plus its charge response times d esp_I/dxi."""
-    Z = np.asarray(system.Z)
-    xyz = np.asarray(system.xyz, dtype=np.float64)
-    nf = system.n_frag
-    n_all = len(Z)
-    fr = ofmo._Frags(system, params)
-    dcn_all = gradient.cn_derivative(Z, xyz, params)
-    r = ofmo.fmo(system, params, ofmo.FMOOptions(level=1, scc_tol=tol, e_tol=0.1 * tol, outer_tol=tol))
-    q = [np.asarray(d, dtype=np.float64) for d in r.dq_mono]
-    kg = params.k_g
-    sh_at = []
-    mono = []
-    for I in range(nf):
-        at, rep_mask, hop = _records(fr, (I,))
-        sh_at.append(at[fr.sh_rec[I]])
-        mono.append((at, rep_mask, hop))
-    esp = [fr.esp((I,), q) for I in range(nf)]
-    probs, ress = [], []
-    for I in range(nf):
-        prob = fr.problem((I,), esp[I])
-        res = xtb.solve_problem(prob, guess=q[I], tol=tol, e_tol=0.1 * tol)
-        probs.append(prob)
-        ress.append(res)
-        q[I] = res.dq
-    esp = [fr.esp((I,), q) for I in range(nf)]
-    off = np.cumsum([0] + [len(x) for x in q])
-    w = np.zeros(off[-1])
-    grad = np.zeros((n_all, 3))
-    sigs = []
-
-    def explicit(I, P, Wt, sig, Q, with_rep=True, M_extra=None):
-        at, rep_mask, hop = mono[I]
-        return gradient.explicit_gradient(Z[at], xyz[at], params, probs[I].basis, P, Wt, sig, Q, fr.cn[at],
-                                          dcn_all[at], atoms=at, n_all=n_all, with_rep=with_rep,
-                                          M_extra=M_extra, rep_mask=rep_mask, hop=hop)
-
-    for I in range(nf):
-        prob, res = probs[I], ress[I]
-        at, rep_mask, hop = mono[I]
-        b = prob.basis
-        dq_at = np.bincount(b.sh_atom, weights=res.dq, minlength=len(at))
-        sig = prob.gam @ res.dq - prob.g3[b.sh_atom] * dq_at[b.sh_atom] ** 2 + esp[I]
-        sigs.append(sig)
-        Wt = (res.C * (res.occ * res.eps)) @ res.C.T
-        grad += explicit(I, res.P, Wt, sig, np.outer(res.dq, res.dq))      # dL_I/dxi|_esp
-        w[off[I]:off[I + 1]] -= esp[I]
-        if hop and prob.extra_fock is not None:
-            # - d Tr(P V)/dxi = - [d/dlambda of the explicit gradient] - dq^V . d esp_I/dxi
-            dqv, dsig, dP, dWt = _first_order_general(prob, res, dF_ext=prob.extra_fock)
-            sh = b.ao_shell
-            M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
-            Q = np.outer(res.dq, dqv) + np.outer(dqv, res.dq)
-            grad -= explicit(I, dP, dWt, sig, Q, with_rep=False, M_extra=M_extra)
-            grad -= gradient._hop_gradient(Z[at], xyz[at], params, b, prob.S,
-                                           gradient.overlap_derivative(Z[at], xyz[at], params, b), res.P, hop,
-                                           at, n_all)
-            for K in range(nf):
-                if K == I:
-                    continue
-                grad -= _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], dqv, sh_at[K], fr.sh_eta[K], q[K], kg, n_all)
-                w[off[K]:off[K + 1]] -= fr.gamma(K, I) @ dqv
-    if nf == 1:
-        return grad
-    n_sh = off[-1]
-    G = np.zeros((n_sh, n_sh))
-    chi = np.zeros((n_sh, n_sh))
-    for I in range(nf):
-        chi[off[I]:off[I + 1], off[I]:off[I + 1]] = response.susceptibility(probs[I], ress[I])
-        for K in range(nf):
-            if K != I:
-                G[off[I]:off[I + 1], off[K]:off[K + 1]] = fr.gamma(I, K)
-    z = np.linalg.solve(np.eye(n_sh) - G @ chi, w)
-    y = chi @ z
-    for I in range(nf):
-        prob, res = probs[I], ress[I]
-        dq1, dsig, dP, dWt = _first_order_general(prob, res, dv=z[off[I]:off[I + 1]])
-        sh = prob.basis.ao_shell
-        M_extra = 0.5 * (dsig[sh][:, None] + dsig[sh][None, :]) * res.P
-        Q = np.outer(res.dq, dq1) + np.outer(dq1, res.dq)
-        grad += explicit(I, dP, dWt, sigs[I], Q, with_rep=False, M_extra=M_extra)
-        for K in range(nf):
-            if K != I:
-                grad += _gamma_pair_grad(xyz, sh_at[I], fr.sh_eta[I], y[off[I]:off[I + 1]], sh_at[K],
-                                         fr.sh_eta[K], q[K], kg, n_all)
-    return grad
+    scaled by 1 + lambda), plus its charge response times d esp_I/dxi.  The
+    FMO1 case of fmo_gradient_records."""
+    return fmo_gradient_records(system, params, ofmo.FMOOptions(level=1), tol)
 
 
 def fmo_gradient_records(system, params, opts=None, tol=1e-12) -> np.ndarray:
