@@ -42,30 +42,8 @@ from . import gradient, response, xtb
 
 def _first_order(prob, res, dv):
     """Changes of dq, shifts, P and W~ of a converged SCC system under the
-    shell potential dv (coupled-perturbed SCC)."""
-    b = prob.basis
-    sh = b.ao_shell
-    chi = response.susceptibility(prob, res)
-    dq = chi @ dv
-    dsig = dv + response.charge_kernel(prob, res) @ dq
-    dF = 0.5 * prob.S * (dsig[sh][:, None] + dsig[sh][None, :])
-    C, eps, f = res.C, res.eps, res.occ
-    fp = -2.0 * (f / 2.0) * (1.0 - f / 2.0) / prob.kT
-    de = eps[:, None] - eps[None, :]
-    fe = f * eps
-    with np.errstate(divide="ignore", invalid="ignore"):
-        M = np.where(np.abs(de) > 1e-12, (f[:, None] - f[None, :]) / de, 0.5 * (fp[:, None] + fp[None, :]))
-        dfe = fp * eps + f
-        N = np.where(np.abs(de) > 1e-12, (fe[:, None] - fe[None, :]) / de, 0.5 * (dfe[:, None] + dfe[None, :]))
-    dFm = C.T @ dF @ C
-    X = M * dFm
-    Y = N * dFm
-    sfp = fp.sum()
-    if abs(sfp) > 0.0:
-        def_ = float(fp @ np.diag(dFm)) / sfp
-        X = X - np.diag(fp * def_)
-        Y = Y - np.diag(fp * eps * def_)
-    return dq, dsig, C @ X @ C.T, C @ Y @ C.T
+    shell potential dv (coupled-perturbed SCC; _first_order_general)."""
+    return _first_order_general(prob, res, dv=dv)
 
 
 def fmo1_gradient(system, params, tol=1e-12) -> np.ndarray:
