@@ -314,8 +314,12 @@ def _nmer_gradient(system, params, opts, level, tol):
 
 
 def _first_order_general(prob, res, dv=None, dF_ext=None):
-    """_first_order for a shell potential dv and/or an AO-matrix perturbation
-    dF_ext of the Fock matrix (kept out of the shifts)."""
+    """First-order changes of dq, the shell shifts, P and W~ of a converged
+    SCC system (coupled-perturbed SCC) under a shell potential dv and/or an
+    AO-matrix perturbation dF_ext of the Fock matrix (kept out of the
+    shifts): dP = C [M o dF'] C^T and dW~ = C [N o dF'] C^T in the MO basis
+    (M, N as in the module notes, minus the Fermi-level shift), with the
+    charges self-consistent through dq = (1 - chi0 K)^-1 (bare source)."""
     b = prob.basis
     sh = b.ao_shell
     C, eps, f = res.C, res.eps, res.occ
