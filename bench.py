@@ -39,8 +39,8 @@ UNIT = "fragment-SCC/s"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # FP32 FMA lanes x 2 flops x max SM clock
 FP64_PEAK_TFLOPS = 1.25                                 # nominal B300 FP64 rate
 # DRAM bytes (read + write) of the dimer-pass SCC launch of this workload, from
-# one ncu capture of the current kernel (profiles/scc_kernel_anthracene128_fmo2.md);
-# None whenever the kernel has changed since that capture
+# one ncu capture of the current kernel; None whenever the kernel has changed
+# since that capture
 DIMER_SCC_DRAM_BYTES = 531186944 + 527815168
 
 

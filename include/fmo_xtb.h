@@ -185,10 +185,17 @@ fmo_status fmo_create(fmo_ctx **out, const fmo_params *p, int device);
  *   xyz[3*n_atoms]         coordinates (bohr), atom-major (x0,y0,z0,x1,...)
  *   frag_of_atom[n_atoms]  fragment index 0..n_frag-1; every fragment non-empty
  *   frag_charge[n_frag]    net charge of each fragment (e)
- *   n_cut, bda_baa[2*n_cut] covalent bonds cut between fragments (BDA, BAA);
- *                          must be 0 / NULL in this version
+ *   n_cut, bda_baa[2*n_cut] covalent bonds cut between fragments: bond
+ *                          detachment atom (BDA) and bond attachment atom
+ *                          (BAA), input atom indices; the bonds are treated
+ *                          by hybrid orbital projection (HOP section of the
+ *                          paper): each BDA needs exactly one s and one p
+ *                          shell and is detached at most once.  0 / NULL: no
+ *                          cut bonds.
  * Each n-mer must hold an even number of electrons (closed shell).
- * Errors: FMO_ERR_ARG on any violation, FMO_ERR_UNSUPPORTED for n_cut > 0.
+ * Errors: FMO_ERR_ARG on any violation (indices out of range, BDA and BAA in
+ * one fragment, open shell), FMO_ERR_UNSUPPORTED (a BDA without one s and one
+ * p shell, or detached twice; a fragment of more than 510 basis functions).
  */
 fmo_status fmo_set_system(fmo_ctx *ctx, int32_t n_atoms, const int32_t *Z, const double *xyz,
                           int32_t n_frag, const int32_t *frag_of_atom, const int32_t *frag_charge,
@@ -305,10 +312,12 @@ fmo_status fmo_get_stats(fmo_ctx *ctx, fmo_stats *st);
 /*
  * SCC solve of one molecule that allocates no device memory.
  *
- * For callers that cannot allocate device memory while they run: work being
- * captured into a CUDA graph, real-time loops that forbid allocation after
- * start-up, or hosts whose memory manager owns all device memory.  The paper
- * has no counterpart; it is a packaging of the library's own kernels.
+ * For callers that cannot allocate device memory while they run: real-time
+ * loops that forbid allocation after start-up (an allocation may block or
+ * fail at any moment), or hosts whose memory manager owns all device memory
+ * (a framework's caching allocator would not see a cudaMalloc made behind
+ * its back).  The paper has no counterpart; it is a packaging of the
+ * library's own kernels.
  *
  * Solves the GFN1-xTB SCC of one closed-shell molecule (one fragment) from a
  * neutral guess, optionally in an external shell potential, with the table
@@ -317,23 +326,28 @@ fmo_status fmo_get_stats(fmo_ctx *ctx, fmo_stats *st);
  *   Z[n_atoms]           host atomic numbers (1 <= n_atoms <= 128)
  *   xyz_dev[3*n_atoms]   device coordinates (bohr), atom-major
  *   charge               net charge of the molecule (e)
- *   esp_dev[n_shell]     device external potential per shell (Eh/e), or NULL
- *   energy_dev[1]        device output: E = E_el + E_rep (Eh)
+ *   esp_dev[n_shell]     device external potential per shell (Eh/e), or NULL;
+ *                        it enters the Fock matrix as 1/2 S (v_mu + v_nu)
+ *   energy_dev[1]        device output: the internal energy E = E_el + E_rep
+ *                        (Eh) of the converged density; the interaction
+ *                        sum_s v_s dq_s with the potential is not included
  *   shell_dq_dev[n_shell] device output: shell charges, table order per atom
  *   status_dev[1]        device output (or NULL): FMO_SCC_* word
  *   cuda_stream          stream for all work (NULL: the legacy default stream)
  *   err[err_len]         host buffer for a message (or NULL)
  * Limits: at most 256 basis functions, 128 shells and 128 atoms; larger
- * molecules return FMO_ERR_ARG with a message.  The call only enqueues work:
- * read the outputs after the stream has finished.
+ * molecules return FMO_ERR_ARG with a message.  The call enqueues the work
+ * and returns; read the outputs after the stream has finished.
  * Memory: all scratch (about 5 MiB) is one fixed device array that every
  * GPU loading the library holds until the process exits.  The first call on
- * a device looks up that array's device address; make that first call before
- * any stream capture.  All calls share the array and it keeps the last
- * call's contents, so calls that overlap on the GPU (other streams, other
- * host threads) race: serialise them.
- * Errors: FMO_ERR_ARG (NULL pointers, sizes, open shell, unknown element),
- * FMO_ERR_UNSUPPORTED, FMO_ERR_CUDA (launch or copy failure).
+ * a device looks up that array's device address (once per device, guarded
+ * against concurrent first calls); a cudaDeviceReset() invalidates it, and
+ * calls after a reset are not supported.  All calls share the array and it
+ * keeps the last call's contents, so calls that overlap on the GPU (other
+ * streams, other host threads) race: serialise them.
+ * Errors: FMO_ERR_ARG (NULL pointers, sizes, open shell, more electrons than
+ * the basis holds, unknown element), FMO_ERR_UNSUPPORTED, FMO_ERR_CUDA
+ * (launch or copy failure).
  */
 fmo_status fmo_scc_solve_noalloc(const fmo_params *p, int32_t n_atoms, const int32_t *Z,
                                  const double *xyz_dev, int32_t charge, const double *esp_dev,

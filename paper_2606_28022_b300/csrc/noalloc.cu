@@ -1,14 +1,15 @@
 // fmo_scc_solve_noalloc: the SCC solve of one molecule with no device
 // allocation at all.
 //
-// Some callers cannot allocate device memory while they run: code that is
-// being captured into a CUDA graph (cudaMalloc is not a capturable
-// operation), real-time or embedded loops that forbid allocation after
-// start-up, and hosts whose memory manager hands out every byte ahead of time
-// (for example a framework's caching allocator).  For them this file keeps all
-// the scratch that the SCC kernels need (the n x n matrices, gamma block,
-// charge vectors, Broyden history and index tables) in one fixed device array
-// that exists from library load until process exit.
+// Some callers cannot allocate device memory while they run: real-time or
+// embedded loops that forbid allocation after start-up (an allocation can
+// block or fail at any time), and hosts whose memory manager hands out every
+// byte ahead of time (for example a framework's caching allocator, which
+// would see a cudaMalloc behind its back as memory it cannot account for).
+// For them this file keeps all the scratch that the SCC kernels need (the
+// n x n matrices, gamma block, charge vectors, Broyden history and index
+// tables) in one fixed device array that exists from library load until
+// process exit.
 //
 // The kernels are the library's own (kernels.cu); only where their scratch
 // lives differs from fmo_run.
@@ -16,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/fmo_xtb.h"
@@ -35,8 +37,13 @@ constexpr size_t kNaBytes = 5120 * 1024;   // 5 MiB
 // stand-in); it uses the device address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
+// Device address of the array, looked up once per device (with that device
+// current) by the first call on it.  The lookup is guarded: host threads may
+// make their first calls at the same time.  A cudaDeviceReset() destroys the
+// context the address belongs to; calls after a reset are not supported.
 constexpr int kNaMaxDevices = 64;
 void* g_noalloc_addr[kNaMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
 
 void set_error(char* buf, int len, const char* msg) {
   if (buf && len > 0) {
@@ -124,6 +131,10 @@ extern "C" fmo_status fmo_scc_solve_noalloc(const fmo_params* p, int32_t n_atoms
     set_error(err, err_len, "not a closed-shell molecule");
     return FMO_ERR_ARG;
   }
+  if (nel > 2.0 * nao) {
+    set_error(err, err_len, "more electrons than the basis holds (charge too negative)");
+    return FMO_ERR_ARG;
+  }
   std::vector<DevElem> h_el(ne);
   for (int k = 0; k < ne; ++k) {
     const fmo_element& src = p->el[ez[k]];
@@ -164,19 +175,24 @@ extern "C" fmo_status fmo_scc_solve_noalloc(const fmo_params* p, int32_t n_atoms
     set_error(err, err_len, "no usable CUDA device");
     return FMO_ERR_CUDA;
   }
-  if (!g_noalloc_addr[dev]) {
-    void* addr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-    if (e != cudaSuccess || !addr) {
-      set_error(err, err_len, cudaGetErrorString(e));
-      return FMO_ERR_CUDA;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* addr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess || !addr) {
+        set_error(err, err_len, cudaGetErrorString(e));
+        return FMO_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = addr;
     }
-    g_noalloc_addr[dev] = addr;
+    base = g_noalloc_addr[dev];
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
   // ---- scratch layout
-  Layout L{reinterpret_cast<unsigned char*>(g_noalloc_addr[dev])};
+  Layout L{reinterpret_cast<unsigned char*>(base)};
   const int n = nao, npad = n + (n & 1);
   double* S = L.take<double>((size_t)n * n);
   double* H0 = L.take<double>((size_t)n * n);
@@ -225,7 +241,8 @@ extern "C" fmo_status fmo_scc_solve_noalloc(const fmo_params* p, int32_t n_atoms
     const cudaError_t e_ = (x);                                         \
     if (e_ != cudaSuccess) { set_error(err, err_len, cudaGetErrorString(e_)); return FMO_ERR_CUDA; } \
   } while (0)
-  // small tables (pageable host -> device copies; nothing is allocated)
+  // small tables: copies from pageable host memory, which the runtime stages
+  // before each call returns (nothing is allocated)
   NA_CK(cudaMemcpyAsync(d_el, h_el.data(), sizeof(DevElem) * ne, cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(d_kab, kab.data(), sizeof(double) * ne * ne, cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(d_elem, elem.data(), sizeof(int) * n_atoms, cudaMemcpyHostToDevice, st));

@@ -395,12 +395,56 @@ def test_esdim_matches_scc_dimer_for_a_far_pair(params, water64):
 
 
 def test_ddq_of_neutral_dimers_sums_to_zero(params, water64):
+    # Eq. 14: the charge moved between I and J on dimer formation is
+    # conserved: the dimer and its two monomers carry the same total charge,
+    # so sum_mu ddq_mu = 0 for every neutral dimer
     s = water64.subsystem([0, 1, 2, 3])
-    r = fmo.fmo(s, params, fmo.FMOOptions(all_dimers_scc=True))
+    opts = fmo.FMOOptions(all_dimers_scc=True)
+    r = fmo.fmo(s, params, opts)
     assert r.dimer_scc.all()
-    # the charge moved between I and J on dimer formation is conserved: the
-    # dimer and the two monomers carry the same total charge
-    assert np.all(np.isfinite(r.dE_dimer))
+    fr = fmo._Frags(s, params)
+    moved = 0.0
+    for I, J in r.dimers:
+        X = (int(I), int(J))
+        res = fr.solve(X, fr.esp(X, r.dq_mono), np.concatenate([r.dq_mono[I], r.dq_mono[J]]), opts)
+        ddq = res.dq - np.concatenate([r.dq_mono[I], r.dq_mono[J]])
+        assert abs(np.sum(ddq)) < 1e-10
+        moved = max(moved, float(np.max(np.abs(ddq))))
+    assert moved > 1e-4          # charge does move between the close pairs
+
+
+def test_embedding_correction_is_needed_with_its_sign_and_environment(params, water64):
+    # Eq. 13: dE^V_IJ = sum_mu ddq_mu ESP^{not IJ}_mu.  Planted mistakes in
+    # it (dropped, sign flipped, the partner's charges left in the ESP) must
+    # move FMO2 far from the whole-system SCC energy, which the correct form
+    # matches closely (an independent number: full xTB, not the oracle's
+    # FMO code)
+    s = water64.subsystem([0, 1, 2, 3, 4])
+    opts = fmo.FMOOptions(all_dimers_scc=True)
+    full = xtb.single_point(s, params).energy
+    r = fmo.fmo(s, params, opts)
+    err = abs(r.e_fmo2 - full)
+    dev = float(np.sum(r.dEV_dimer))
+    assert err < 0.05 * abs(r.e_fmo2 - dev - full)          # dE^V dropped
+    assert err < 0.05 * abs(r.e_fmo2 - 2.0 * dev - full)    # sign flipped
+    fr = fmo._Frags(s, params)
+    wrong = 0.0
+    for k, (I, J) in enumerate(r.dimers):
+        X = (int(I), int(J))
+        qm = np.concatenate([r.dq_mono[I], r.dq_mono[J]])
+        res = fr.solve(X, fr.esp(X, r.dq_mono), qm, opts)
+        # ESP^{not I} on I's shells and ESP^{not J} on J's: the partner included
+        esp_bad = np.concatenate([fr.esp((X[0],), r.dq_mono), fr.esp((X[1],), r.dq_mono)])
+        wrong += float((res.dq - qm) @ esp_bad) - r.dEV_dimer[k]
+    assert err < 0.05 * abs(r.e_fmo2 + wrong - full)
+    # a six-water cluster: the correct form still beats every mistake
+    s6 = water64.subsystem([0, 1, 2, 3, 4, 5])
+    full6 = xtb.single_point(s6, params).energy
+    r6 = fmo.fmo(s6, params, opts)
+    dev6 = float(np.sum(r6.dEV_dimer))
+    err6 = abs(r6.e_fmo2 - full6)
+    assert err6 < 0.3 * abs(r6.e_fmo2 - dev6 - full6)
+    assert err6 < 0.1 * abs(r6.e_fmo2 - 2.0 * dev6 - full6)
 
 
 # ---------------------------------------------------------------------------

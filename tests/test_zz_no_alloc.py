@@ -1,8 +1,10 @@
 """fmo_scc_solve_noalloc, the entry point for callers that cannot allocate
-device memory while they run (graph capture, allocation-free loops,
-frameworks that own all device memory): its results must equal those of
-fmo_run on the same one-fragment system, call after call, although every call
-reuses the same fixed scratch array left behind by the previous one.
+device memory while they run (loops that forbid allocation after start-up,
+frameworks whose allocator owns all device memory): its results must equal
+those of fmo_run on the same one-fragment system, call after call, although
+every call reuses the same fixed scratch array left behind by the previous
+one.  With an external shell potential there is no fmo_run counterpart; the
+FP64 oracle's SCC in the same potential is the reference there.
 
 Collected last on purpose: if it fails, every other test has already run."""
 import ctypes as C
@@ -68,6 +70,44 @@ def test_noalloc_matches_fmo_run_call_after_call(params):
             assert abs(float(energy.item()) - float(ref.energy[0])) < tol, (name, prec)
             assert np.max(np.abs(dq.cpu().numpy() - ref.shell_dq)) < DQ_TOL * (1 if prec == "fp64" else 10)
     ref_ctx.close()
+
+
+def test_noalloc_in_an_external_potential_matches_the_oracle(params):
+    # a nonzero potential on every shell (the form of the embedding ESP): the
+    # returned energy is the internal one, E_el + E_rep without sum v dq
+    torch = pytest.importorskip("torch")
+    from oracle import xtb
+    from paper_2606_28022_b300 import build, fmo
+    build.build()
+    lib = fmo.load_library()
+    solve = _bind(lib)
+    cparams = fmo.params_to_c(params)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    anth, _ = G.anthracene_cluster(128, 2)
+    mol = anth.subsystem([9])
+    cn = xtb.coordination_numbers(mol.Z, mol.xyz, params)
+    n_sh = xtb.make_basis(mol.Z, params).n_sh
+    rng = np.random.default_rng(5)
+    v = 0.02 * rng.standard_normal(n_sh)
+    ref = xtb.scc(mol.Z, mol.xyz, params, cn, esp=v)
+    Z = np.ascontiguousarray(mol.Z, dtype=np.int32)
+    xyz = torch.tensor(mol.xyz, dtype=torch.float64, device=dev).contiguous()
+    esp = torch.tensor(v, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):                       # two calls in a row on the shared scratch
+        energy = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+        dq = torch.full((n_sh,), float("nan"), dtype=torch.float64, device=dev)
+        status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+        err = C.create_string_buffer(256)
+        st = solve(C.byref(cparams), len(Z), Z.ctypes.data_as(C.POINTER(C.c_int32)), xyz.data_ptr(), 0,
+                   esp.data_ptr(), C.byref(fmo.options()), energy.data_ptr(), dq.data_ptr(), status.data_ptr(),
+                   stream.cuda_stream, err, 256)
+        assert st == 0, err.value
+        torch.cuda.synchronize(dev)
+        assert int(status.item()) == 0
+        assert abs(float(energy.item()) - ref.energy) < E_TOL
+        assert np.max(np.abs(dq.cpu().numpy() - ref.dq)) < DQ_TOL
 
 
 def test_noalloc_rejects_a_molecule_beyond_its_limit(params):
