@@ -142,6 +142,11 @@ typedef struct fmo_options {
                                energy is variational in the n-mer density (its
                                ESP is fixed), so it is off only to second order
                                in the FP32 charge error. */
+  int32_t want_gradient;    /* 1: keep what fmo_get_gradient needs; in mixed
+                               precision the dimers and trimers then converge
+                               in FP64 after the FP32 phase (nmer_finish and
+                               mixed_finish are ignored).  Precision FP64 runs
+                               always allow the gradient. */
 } fmo_options;
 
 /* Counters of the last fmo_run. */
@@ -165,6 +170,10 @@ typedef struct fmo_stats {
   double flops_fp64[3];       /* n-AO n-mer (transform 4n^3, density 2n^3, eigen 9n^3) */
   int64_t h2d_bytes;          /* host -> device bytes copied by the run */
   int64_t d2h_bytes;          /* device -> host bytes copied by the run */
+  double ms_gradient;         /* last fmo_get_gradient (CUDA events) */
+  int32_t zvector_iterations; /* GMRES iterations of its Z-vector solve */
+  int32_t pad_;
+  double zvector_residual;    /* final ||w - (1 - Gamma chi) z|| / ||w|| */
 } fmo_stats;
 
 typedef struct fmo_ctx fmo_ctx;
@@ -292,18 +301,24 @@ fmo_status fmo_get_dimers(fmo_ctx *ctx, int64_t *n, int32_t *ij, double *dE, dou
 fmo_status fmo_get_trimers(fmo_ctx *ctx, int64_t *n, int32_t *ijk, double *dE3, double *corr);
 
 /*
- * Nuclear gradient dE/dxyz (Eh/bohr) of the last fmo_run, grad[3*n_atoms] in
- * the input atom order (host memory, caller-owned).  The analytic GFN1-xTB
- * gradient of one SCC system (the building block of the gradient section,
- * Eqs. 23-28: P dH0 + W dS + 1/2 dq dq dgamma + dE_rep, with the Pi and
- * CN-dependent parts of dH0), evaluated on the GPU from the run's FP64
- * orbitals.  This release covers systems that are one fragment without cut
- * bonds, run in precision FP64 (there E_FMO is the GFN1-xTB energy); the FMO
- * terms of several fragments (explicit embedding, charge-transfer and ES-DIM
- * terms and the self-consistent Z-vector response) are not built.
+ * Nuclear gradient dE/dxyz (Eh/bohr) of the FMO energy of the last fmo_run at
+ * its level (FMO1, FMO2 or FMO3), grad[3*n_atoms] in the input atom order
+ * (host memory, caller-owned).  Analytic (Sec. 2.4 of the paper): for every
+ * monomer and SCC dimer and trimer, the GFN1-xTB gradient of its converged
+ * density in its embedding potential (Eqs. 23-28: P dH0 + W dS + the Coulomb
+ * and repulsion terms, the Pi and CN parts of dH0) times its FMO2/FMO3
+ * coefficient; the charge-transfer part of dE^V (Eq. 13) and the ES-DIM pairs
+ * (Eq. 15); the coordination numbers of the whole system; and the response of
+ * the monomer charges through the self-consistent Z-vector, solved in charge
+ * space: (1 - Gamma chi) z = w with the monomers' coupled-perturbed
+ * susceptibilities chi, by GMRES on the GPU.  All in FP64.
+ * Needs a run whose dimer and trimer densities are converged in FP64
+ * (precision FP64, or mixed with want_gradient = 1).
+ * Fermi occupations (Eq. 6) are taken as they are, fractional ones included.
  * Errors: FMO_ERR_ARG (NULL), FMO_ERR_STATE (no run), FMO_ERR_UNSUPPORTED
- * (several fragments, cut bonds, mixed precision, more than 2048 atoms,
- * fractional occupations: a HOMO-LUMO gap of fewer than ~25 kT), FMO_ERR_CUDA.
+ * (cut bonds, a run without FP64 n-mer densities, a trimer holding an
+ * ES-DIM pair), FMO_ERR_NOT_CONVERGED (Z-vector or eigen-solve),
+ * FMO_ERR_CUDA.
  */
 fmo_status fmo_get_gradient(fmo_ctx *ctx, double *grad);
 

@@ -140,7 +140,13 @@ struct fmo_ctx {
   bool have_result = false;
   int last_level = 0;
   int last_precision = 0;
+  bool grad_ready = false;                // the last run's n-mer densities are converged in FP64
+  bool last_cuts_ok = false;              // trimers hold only SCC pairs (gradient bookkeeping)
+  std::vector<int> r_pair_k;              // SCC-dimer index of every pair, -1 for ES-DIM
   DevBuf d_grad_work, d_grad;
+  DevBuf d_gt, d_gslots_a, d_gslots_s, d_gpair, d_gfrag_ptr, d_gent_a, d_gent_s, d_gatom_frag, d_gsh_frag,
+      d_gatom, d_gw, d_gd, d_gmono_terms, d_gmr, d_gmr_mem, d_gresp_terms, d_gresp_mem, d_gflag, d_gsh0,
+      d_gkrylov, d_gz, d_gy, d_ga, d_gout;
   double totals[3] = {0, 0, 0};
   std::vector<double> r_e_mono, r_dq_mono, r_dE_pair, r_e_dim_pair, r_dEV_pair;
   std::vector<int> r_mono_iters, r_mono_status, r_pair_iters;
@@ -461,8 +467,12 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.cold_refine = cold;
   L.reortho32 = reortho32;
   L.jac_hint = jac_hint;
-  L.fp64_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED) ? std::max(0, o.mixed_finish) : 0;
-  L.energy_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED && o.nmer_finish == FMO_NMER_FINISH_ENERGY);
+  // a gradient needs FP64-converged n-mer densities: then the FP32 phase of a
+  // mixed-precision n-mer hands over to FP64 iterations run to convergence
+  const bool grad_nmer = o.want_gradient && pass_id >= 1;
+  L.fp64_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED && !grad_nmer) ? std::max(0, o.mixed_finish) : 0;
+  L.energy_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED && o.nmer_finish == FMO_NMER_FINISH_ENERGY &&
+                     !grad_nmer);
   const bool warm_nmer = (pass_id >= 1 && o.precision == FMO_PREC_MIXED);
   L.cold_steps = warm_nmer ? 12 : 2;
   L.first_rot = warm_nmer ? 1 : 0;
@@ -704,6 +714,398 @@ fmo_status mlp_predict_device(fmo_ctx* ctx, cudaStream_t st, double* out) {
   return FMO_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Analytic FMO gradient (Sec. 2.4; kernels in fmo_gradient.cu).
+
+// y = Op(v) = v - Gamma_inter chi v (the Z-vector operator; Gamma_inter: gamma
+// between shells of different fragments).
+cudaError_t zvector_op(fmo_ctx* ctx, cudaStream_t st, int nf, const GradTerm* mt, const MonoResp* mr,
+                       const int* sh0, const double* v, double* out, double* t1, double* t2, double* t3) {
+  cudaError_t e;
+  if ((e = launch_chi_apply(st, nf, mt, mr, sh0, v, t1)) != cudaSuccess) return e;
+  if (ctx->gam_full_ok) e = launch_phi_gemv(st, ctx->n_sh, ctx->d_gam_full.as<double>(), t1, t2);
+  else e = launch_phi(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
+                      t1, ctx->g, t2, ctx->d_phi_part.as<double>(), 0);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_intra_gamma(st, nf, mt, sh0, t1, t3)) != cudaSuccess) return e;
+  return launch_vec_lincomb3(st, ctx->n_sh, 1.0, v, -1.0, t2, 1.0, t3, out);
+}
+
+// GMRES(m) with classical Gram-Schmidt applied twice for (1 - Gamma chi) z = w.
+// Stops at ||w - Op z|| <= rtol ||w||.  Returns iterations (-1: not converged).
+fmo_status zvector_gmres(fmo_ctx* ctx, cudaStream_t st, int nf, const GradTerm* mt, const MonoResp* mr,
+                         const int* sh0, const double* w, double* z, double rtol, int* iters, double* relres) {
+  const int n = ctx->n_sh;
+  const int m = 40, max_restart = 12;
+  const long long ldv = (n + 31) / 32 * 32;
+  CK(ctx->d_gkrylov.ensure(sizeof(double) * (size_t)ldv * (m + 1 + 5) + sizeof(double) * (m + 1) * 2));
+  double* V = ctx->d_gkrylov.as<double>();
+  double* u = V + (size_t)ldv * (m + 1);
+  double* t1 = u + ldv;
+  double* t2 = t1 + ldv;
+  double* t3 = t2 + ldv;
+  double* r = t3 + ldv;
+  double* dh = r + ldv;
+  double* dh2 = dh + (m + 1);
+  std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), hh(m + 1), hh2(m + 1);
+  auto norm = [&](const double* x, double* out) -> cudaError_t {
+    cudaError_t e = launch_vec_dots(st, n, 1, x, ldv, x, dh);
+    if (e != cudaSuccess) return e;
+    e = d2h(out, dh, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    e = sync_stream(st);
+    *out = std::sqrt(*out);
+    return e;
+  };
+  CK(cudaMemsetAsync(z, 0, sizeof(double) * n, st));
+  CK(cudaMemcpyAsync(r, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  double beta0 = 0.0;
+  CK(norm(r, &beta0));
+  *iters = 0;
+  *relres = 0.0;
+  if (!(beta0 > 0.0)) return FMO_OK;
+  double beta = beta0;
+  int total = 0;
+  for (int rs = 0; rs < max_restart; ++rs) {
+    CK(launch_vec_lincomb3(st, n, 1.0 / beta, r, 0.0, nullptr, 0.0, nullptr, V));
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;
+    double res = beta;
+    for (int j = 0; j < m; ++j) {
+      double* vj1 = V + (size_t)ldv * (j + 1);
+      CK(zvector_op(ctx, st, nf, mt, mr, sh0, V + (size_t)ldv * j, vj1, t1, t2, t3));
+      // h = V^T u, u -= V h, twice
+      CK(launch_vec_dots(st, n, j + 1, V, ldv, vj1, dh));
+      CK(launch_vec_update(st, n, j + 1, V, ldv, dh, vj1));
+      CK(launch_vec_dots(st, n, j + 1, V, ldv, vj1, dh2));
+      CK(launch_vec_update(st, n, j + 1, V, ldv, dh2, vj1));
+      CK(launch_vec_dots(st, n, 1, vj1, ldv, vj1, dh2 + j + 1));
+      CK(d2h(hh.data(), dh, sizeof(double) * (j + 1), st));
+      CK(d2h(hh2.data(), dh2, sizeof(double) * (j + 2), st));
+      CK(sync_stream(st));
+      const double hn = std::sqrt(std::max(hh2[j + 1], 0.0));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh2[i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) CK(launch_vec_lincomb3(st, n, 1.0 / hn, vj1, 0.0, nullptr, 0.0, nullptr, vj1));
+      // Givens rotations on column j
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+      const double den = std::hypot(a, b);
+      cs[j] = den > 0.0 ? a / den : 1.0;
+      sn[j] = den > 0.0 ? b / den : 0.0;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      res = std::fabs(gv[j + 1]);
+      k = j + 1;
+      ++total;
+      if (res <= rtol * beta0 || hn == 0.0) break;
+    }
+    // y = H^-1 g (upper triangular), z += V y
+    std::vector<double> yv(k);
+    for (int i = k - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int c = i + 1; c < k; ++c) t -= H[(size_t)i * m + c] * yv[c];
+      yv[i] = t / H[(size_t)i * m + i];
+    }
+    for (double& x : yv) x = -x;   // vec_update subtracts
+    CK(h2d(dh, yv.data(), sizeof(double) * k, st));
+    CK(launch_vec_update(st, n, k, V, ldv, dh, z));
+    // true residual
+    CK(zvector_op(ctx, st, nf, mt, mr, sh0, z, t1 + 0, u, t2, t3));   // Op z into t1 (u, t2, t3 scratch)
+    CK(launch_vec_lincomb3(st, n, 1.0, w, -1.0, t1, 0.0, nullptr, r));
+    CK(norm(r, &beta));
+    *relres = beta / beta0;
+    if (beta <= rtol * beta0 * 10.0 || beta <= rtol * beta0) { *iters = total; return FMO_OK; }
+  }
+  *iters = -total;
+  return FMO_OK;
+}
+
+fmo_status compute_gradient(fmo_ctx* ctx, std::vector<double>& gout) {
+  cudaStream_t st = ctx->own_stream;
+  const int nf = ctx->n_frag, level = ctx->last_level;
+  const Pass& M = ctx->mono;
+  const Pass& D = ctx->dim;
+  const Pass& T = ctx->tri;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  // coefficients of the FMO2/FMO3 sums (Eqs. 12, 16): monomers c_I, SCC dimers m
+  std::vector<double> c_mono(nf, 1.0), m_dim(D.nm.size(), 1.0);
+  for (const Nmer& x : D.nm) { c_mono[x.frag[0]] -= 1.0; c_mono[x.frag[1]] -= 1.0; }
+  auto pidx = [&](long long a, long long b) { return a * (2LL * nf - a - 1) / 2 + (b - a - 1); };
+  for (const Nmer& x : T.nm) {
+    const int f[3] = {x.frag[0], x.frag[1], x.frag[2]};
+    const int pr[3][2] = {{f[0], f[1]}, {f[0], f[2]}, {f[1], f[2]}};
+    for (auto& q : pr) {
+      const int k = ctx->r_pair_k[pidx(q[0], q[1])];
+      if (k < 0) return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: a trimer holds an ES-DIM pair");
+      m_dim[k] -= 1.0;
+      c_mono[q[0]] += 1.0;
+      c_mono[q[1]] += 1.0;
+    }
+    for (int I : f) c_mono[I] -= 1.0;
+  }
+  GradLaunch L{};
+  L.ft = ctx->ftab(); L.xyz = ctx->d_xyz.as<double>(); L.elem = ctx->d_elem.as<int>();
+  L.atom_sh0 = ctx->d_atom_sh0.as<int>(); L.el = ctx->d_el.as<DevElem>(); L.kab = ctx->d_kab.as<double>();
+  L.ne = ctx->ne; L.prim = ctx->d_prim.as<PrimPair>(); L.cn = ctx->d_cn.as<double>(); L.g = ctx->g;
+  L.dq_mono = ctx->d_dq_mono.as<double>();
+  for (const Pass* P : {&M, &D, &T}) {
+    L.max_n = std::max(L.max_n, P->max_n);
+    L.max_nsh = std::max(L.max_nsh, P->max_nsh);
+    L.max_nat = std::max(L.max_nat, P->max_nat);
+  }
+  if (grad_smem_max(L) > (size_t)ctx->smem_optin) return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: n-mer too large");
+  // energy terms: monomers (c_I != 0), SCC dimers, SCC trimers
+  struct TermRef { const Pass* P; int k; int kind; double m, es; };
+  std::vector<TermRef> refs;
+  for (int I = 0; I < nf; ++I) if (c_mono[I] != 0.0) refs.push_back({&M, I, kGradMonomer, c_mono[I], 0.0});
+  for (size_t k = 0; k < D.nm.size(); ++k) refs.push_back({&D, int(k), kGradNmer, m_dim[k], level >= 2 ? 1.0 : 0.0});
+  for (size_t k = 0; k < T.nm.size(); ++k) refs.push_back({&T, int(k), kGradNmer, 1.0, 0.0});
+  const int nt = int(refs.size());
+  std::vector<GradTerm> terms(nt);
+  long long aoff = 0, soff = 0;
+  std::vector<std::vector<std::pair<long long, long long>>> ent(nf);   // per fragment: (atom slot, shell slot)
+  for (int i = 0; i < nt; ++i) {
+    const TermRef& r = refs[i];
+    GradTerm& t = terms[i];
+    std::memset(&t, 0, sizeof(t));
+    t.nm = r.P->nm[r.k];
+    t.S = r.P->S.as<double>() + t.nm.mat;
+    t.H0 = r.P->H0.as<double>() + t.nm.mat;
+    t.gam = r.P->gam.as<double>() + t.nm.gam;
+    t.CT = r.P->CTd.as<double>() + t.nm.mat;
+    t.eps = r.P->eps.as<double>() + t.nm.aov;
+    t.dq = r.P->dq.as<double>() + t.nm.shv;
+    t.esp = r.P->esp.as<double>() + t.nm.shv;
+    t.m = r.m;
+    t.es = r.es;
+    t.kind = r.kind;
+    t.with_rep = 1;
+    t.aslot = aoff;
+    t.sslot = soff;
+    long long la = 0, ls = 0;
+    for (int q = 0; q < t.nm.nfrag; ++q) {
+      const int f = t.nm.frag[q];
+      ent[f].push_back({aoff + 4 * la, soff + 2 * ls});
+      la += ctx->f_nat[f];
+      ls += ctx->f_nsh[f];
+    }
+    aoff += 4LL * t.nm.nat;
+    soff += 2LL * t.nm.nsh;
+  }
+  // per-fragment entry lists (CSR, term order)
+  std::vector<int> fptr(nf + 1, 0);
+  std::vector<long long> ea, es;
+  for (int f = 0; f < nf; ++f) {
+    fptr[f] = int(ea.size());
+    for (auto& x : ent[f]) { ea.push_back(x.first); es.push_back(x.second); }
+  }
+  fptr[nf] = int(ea.size());
+  std::vector<int> atom_frag(ctx->n_int), sh_frag(ctx->n_sh), sh0(nf);
+  for (int f = 0; f < nf; ++f) {
+    sh0[f] = ctx->f_sh0[f];
+    for (int i = 0; i < ctx->f_nat[f]; ++i) atom_frag[ctx->f_atom0[f] + i] = f;
+    for (int i = 0; i < ctx->f_nsh[f]; ++i) sh_frag[ctx->f_sh0[f] + i] = f;
+  }
+  const int nat = ctx->n_int, nsh_all = ctx->n_sh;
+  CK(ctx->d_gslots_a.ensure(sizeof(double) * std::max<long long>(aoff, 1)));
+  CK(ctx->d_gslots_s.ensure(sizeof(double) * std::max<long long>(soff, 1)));
+  CK(upload(ctx->d_gfrag_ptr, fptr, st));
+  CK(upload(ctx->d_gent_a, ea, st));
+  CK(upload(ctx->d_gent_s, es, st));
+  CK(upload(ctx->d_gatom_frag, atom_frag, st));
+  CK(upload(ctx->d_gsh_frag, sh_frag, st));
+  CK(upload(ctx->d_gsh0, sh0, st));
+  CK(ctx->d_gatom.ensure(sizeof(double) * 4 * (size_t)nat));
+  CK(ctx->d_gw.ensure(sizeof(double) * (size_t)nsh_all));
+  CK(ctx->d_gd.ensure(sizeof(double) * (size_t)nsh_all));
+  CK(ctx->d_gflag.ensure(sizeof(int)));
+  CK(cudaMemsetAsync(ctx->d_gflag.p, 0, sizeof(int), st));
+  // per-term scratch, in chunks: Pa, W (n^2 each), work (4 n^2), shifts (nsh)
+  auto term_bytes = [](const Nmer& x) { return sizeof(double) * (6 * (size_t)x.n * x.n + x.nsh + 16); };
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t budget = std::max<size_t>(size_t(256) << 20, std::min<size_t>(size_t(8) << 30, free_b / 4));
+  CK(ctx->d_gt.ensure(sizeof(GradTerm) * std::max(nt, 1)));
+  for (int c0 = 0; c0 < nt;) {
+    size_t used = 0;
+    int c1 = c0;
+    while (c1 < nt && (c1 == c0 || used + term_bytes(terms[c1].nm) <= budget)) used += term_bytes(terms[c1++].nm);
+    CK(ctx->d_grad_work.ensure(used));
+    char* base = reinterpret_cast<char*>(ctx->d_grad_work.p);
+    size_t off = 0;
+    for (int i = c0; i < c1; ++i) {
+      GradTerm& t = terms[i];
+      const size_t nn = (size_t)t.nm.n * t.nm.n;
+      double* b = reinterpret_cast<double*>(base + off);
+      t.Pa = b;
+      t.W = b + nn;
+      t.work = b + 2 * nn;
+      t.sa = b + 6 * nn;
+      off += term_bytes(t.nm);
+    }
+    CK(h2d(ctx->d_gt.as<GradTerm>() + c0, terms.data() + c0, sizeof(GradTerm) * (c1 - c0), st));
+    CK(launch_grad_prep(st, c1 - c0, ctx->d_gt.as<GradTerm>() + c0, L, ctx->d_gflag.as<int>()));
+    CK(launch_grad_explicit(st, c1 - c0, ctx->d_gt.as<GradTerm>() + c0, L, ctx->d_gslots_a.as<double>(),
+                            ctx->d_gslots_s.as<double>()));
+    CK(sync_stream(st));   // the scratch is reused by the next chunk
+    c0 = c1;
+  }
+  CK(launch_grad_gather(st, nat, nsh_all, L, ctx->d_gatom_frag.as<int>(), ctx->d_gsh_frag.as<int>(),
+                        ctx->d_gfrag_ptr.as<int>(), ctx->d_gent_a.as<long long>(), ctx->d_gent_s.as<long long>(),
+                        ctx->d_gslots_a.as<double>(), ctx->d_gslots_s.as<double>(), ctx->d_gatom.as<double>(),
+                        ctx->d_gw.as<double>(), ctx->d_gd.as<double>(), 0));
+  CK(ctx->d_ga.ensure(sizeof(double) * (size_t)nsh_all));
+  CK(ctx->d_gout.ensure(sizeof(double) * 3 * (size_t)nat));
+  double* a_vec = ctx->d_ga.as<double>();
+  int zit = 0;
+  double zres = 0.0;
+  if (nf > 1) {
+    // ---- response: monomer susceptibilities, Z-vector, first-order gradients
+    std::vector<GradTerm> mt(nf);
+    std::vector<MonoResp> mr(nf);
+    size_t mem = 0;
+    std::vector<size_t> moff(nf);
+    for (int I = 0; I < nf; ++I) {
+      const Nmer& x = M.nm[I];
+      moff[I] = mem;
+      const size_t nn = (size_t)x.n * x.n, ss = (size_t)x.nsh * x.nsh;
+      mem += sizeof(double) * (nn + 2 * (size_t)x.n + ss + x.nsh + 7 * nn + (size_t)x.npad * x.npad + 3 * ss + 64);
+    }
+    CK(ctx->d_gmr_mem.ensure(mem));
+    for (int I = 0; I < nf; ++I) {
+      const Nmer& x = M.nm[I];
+      GradTerm& t = mt[I];
+      std::memset(&t, 0, sizeof(t));
+      t.nm = x;
+      t.S = M.S.as<double>() + x.mat;
+      t.H0 = M.H0.as<double>() + x.mat;
+      t.gam = M.gam.as<double>() + x.gam;
+      t.CT = M.CTd.as<double>() + x.mat;
+      t.eps = M.eps.as<double>() + x.aov;
+      t.dq = M.dq.as<double>() + x.shv;
+      t.esp = M.esp.as<double>() + x.shv;
+      t.kind = kGradMonomer;
+      const size_t nn = (size_t)x.n * x.n, ss = (size_t)x.nsh * x.nsh;
+      double* b = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->d_gmr_mem.p) + moff[I]);
+      mr[I].C = b;
+      mr[I].eps = b + nn;
+      mr[I].focc = mr[I].eps + x.n;
+      mr[I].chi = mr[I].focc + x.n;
+      mr[I].sig = mr[I].chi + ss;
+      mr[I].work = mr[I].sig + x.nsh;
+    }
+    CK(upload(ctx->d_gmono_terms, mt, st));
+    CK(upload(ctx->d_gmr, mr, st));
+    const GradTerm* dmt = ctx->d_gmono_terms.as<GradTerm>();
+    MonoResp* dmr = ctx->d_gmr.as<MonoResp>();
+    CK(launch_grad_mono_response(st, nf, dmt, dmr, L, ctx->d_gflag.as<int>()));
+    // w += gamma d (charge transfer of the SCC n-mers into every other
+    // fragment) and, with pairs, the ESP of the all-pairs ES-DIM form
+    CK(ctx->d_gz.ensure(sizeof(double) * (size_t)nsh_all));
+    CK(ctx->d_gy.ensure(sizeof(double) * (size_t)nsh_all));
+    double* z = ctx->d_gz.as<double>();
+    double* y = ctx->d_gy.as<double>();
+    if (ctx->gam_full_ok) CK(launch_phi_gemv(st, nsh_all, ctx->d_gam_full.as<double>(), ctx->d_gd.as<double>(), y));
+    else CK(launch_phi(st, nsh_all, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(),
+                       ctx->d_gd.as<double>(), ctx->g, y, ctx->d_phi_part.as<double>(), 0));
+    CK(launch_vec_lincomb3(st, nsh_all, 1.0, ctx->d_gw.as<double>(), 1.0, y, level >= 2 ? 1.0 : 0.0,
+                           M.esp.as<double>(), ctx->d_gw.as<double>()));
+    int fl = 0;
+    CK(d2h(&fl, ctx->d_gflag.p, sizeof(int), st));
+    CK(sync_stream(st));
+    if (fl & 2) return fail(ctx, FMO_ERR_NOT_CONVERGED, "gradient: monomer eigen-solve did not converge");
+    const std::vector<MonoResp>& mr_h = mr;
+    fmo_status fs = zvector_gmres(ctx, st, nf, dmt, dmr, ctx->d_gsh0.as<int>(), ctx->d_gw.as<double>(), z, 1e-12,
+                                  &zit, &zres);
+    if (fs != FMO_OK) return fs;
+    if (zit < 0) return fail(ctx, FMO_ERR_NOT_CONVERGED, "gradient: Z-vector GMRES did not converge");
+    CK(launch_chi_apply(st, nf, dmt, dmr, ctx->d_gsh0.as<int>(), z, y));
+    // response terms: one per monomer, Pa = dP, W = dW~, Pb = P, sb = dsigma
+    std::vector<GradTerm> rt(nf);
+    size_t rmem = 0;
+    std::vector<size_t> roff(nf);
+    long long raoff = 0;
+    std::vector<int> rptr(nf + 1);
+    std::vector<long long> rea(nf), res_(nf, -1);
+    for (int I = 0; I < nf; ++I) {
+      roff[I] = rmem;
+      rmem += sizeof(double) * (3 * (size_t)M.nm[I].n * M.nm[I].n + M.nm[I].nsh + 8);
+    }
+    CK(ctx->d_gresp_mem.ensure(rmem));
+    CK(ctx->d_gslots_a.ensure(sizeof(double) * std::max<long long>(aoff, 1)));
+    for (int I = 0; I < nf; ++I) {
+      GradTerm t = mt[I];
+      const size_t nn = (size_t)t.nm.n * t.nm.n;
+      double* b = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->d_gresp_mem.p) + roff[I]);
+      t.kind = kGradResponse;
+      t.Pa = b;
+      t.W = b + nn;
+      t.Pb = b + 2 * nn;
+      t.sb = b + 3 * nn;
+      t.sa = mr_h[I].sig;
+      t.qb = y + ctx->f_sh0[I];
+      t.esp = nullptr;
+      t.m = 1.0;
+      t.es = 0.0;
+      t.with_rep = 0;
+      t.aslot = raoff;
+      t.sslot = 0;
+      rptr[I] = I;
+      rea[I] = raoff;
+      raoff += 4LL * t.nm.nat;
+      rt[I] = t;
+    }
+    rptr[nf] = nf;
+    DevBuf rslots;
+    CK(rslots.ensure(sizeof(double) * std::max<long long>(raoff, 1)));
+    CK(upload(ctx->d_gresp_terms, rt, st));
+    CK(launch_grad_first_order(st, nf, ctx->d_gresp_terms.as<GradTerm>(), dmr, L, z, y));
+    CK(launch_grad_explicit(st, nf, ctx->d_gresp_terms.as<GradTerm>(), L, rslots.as<double>(), nullptr));
+    DevBuf rp, ra;
+    CK(upload(rp, rptr, st));
+    CK(upload(ra, rea, st));
+    CK(launch_grad_gather(st, nat, 0, L, ctx->d_gatom_frag.as<int>(), nullptr, rp.as<int>(), ra.as<long long>(),
+                          nullptr, rslots.as<double>(), nullptr, ctx->d_gatom.as<double>(), nullptr, nullptr, 1));
+    // a = d + chi z (+ 1/2 q with ES-DIM pairs)
+    CK(launch_vec_lincomb3(st, nsh_all, 1.0, ctx->d_gd.as<double>(), 1.0, y, level >= 2 ? 0.5 : 0.0,
+                           ctx->d_dq_mono.as<double>(), a_vec));
+    CK(sync_stream(st));
+    rslots.release();
+    rp.release();
+    ra.release();
+  } else {
+    CK(cudaMemsetAsync(a_vec, 0, sizeof(double) * (size_t)nsh_all, st));
+  }
+  CK(launch_grad_cn_coulomb(st, nat, nsh_all, L, ctx->d_gatom_frag.as<int>(), ctx->d_sh_atom.as<int>(),
+                            ctx->d_sh_inv_eta.as<double>(), a_vec, ctx->d_gatom.as<double>(),
+                            ctx->d_gout.as<double>()));
+  gout.assign(3 * (size_t)nat, 0.0);
+  int fl = 0;
+  CK(d2h(gout.data(), ctx->d_gout.p, sizeof(double) * gout.size(), st));
+  CK(d2h(&fl, ctx->d_gflag.p, sizeof(int), st));
+  cudaEventRecord(e1, st);
+  CK(sync_stream(st));
+  ctx->stats.ms_gradient = now_ms(e0, e1);
+  ctx->stats.zvector_iterations = zit;
+  ctx->stats.zvector_residual = zres;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (fl) return fail(ctx, FMO_ERR_NOT_CONVERGED, "gradient: monomer eigen-solve did not converge");
+  return FMO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -767,7 +1169,11 @@ void fmo_destroy(fmo_ctx* ctx) {
                     &ctx->d_mlp_fcharge, &ctx->d_mlp_err, &ctx->d_mlp_X, &ctx->d_mlp_y, &ctx->d_mlp_q, &ctx->d_ghost_frag, &ctx->d_ghost_src, &ctx->d_bda_baa_frag, &ctx->d_hop_baa, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
                     &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
-                    &ctx->d_totals, &ctx->d_grad_work, &ctx->d_grad})
+                    &ctx->d_totals, &ctx->d_grad_work, &ctx->d_grad, &ctx->d_gt, &ctx->d_gslots_a,
+                    &ctx->d_gslots_s, &ctx->d_gpair, &ctx->d_gfrag_ptr, &ctx->d_gent_a, &ctx->d_gent_s,
+                    &ctx->d_gatom_frag, &ctx->d_gsh_frag, &ctx->d_gatom, &ctx->d_gw, &ctx->d_gd,
+                    &ctx->d_gmono_terms, &ctx->d_gmr, &ctx->d_gmr_mem, &ctx->d_gresp_terms, &ctx->d_gresp_mem,
+                    &ctx->d_gflag, &ctx->d_gsh0, &ctx->d_gkrylov, &ctx->d_gz, &ctx->d_gy, &ctx->d_ga, &ctx->d_gout})
     b->release();
   ctx->stg.release();
   ctx->mono.release();
@@ -1031,6 +1437,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     return fail(ctx, FMO_ERR_ARG, "unknown monomer loop");
   if (o.nmer_finish != FMO_NMER_FINISH_ENERGY && o.nmer_finish != FMO_NMER_FINISH_ITERATE)
     return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
+  if (o.want_gradient != 0 && o.want_gradient != 1) return fail(ctx, FMO_ERR_ARG, "want_gradient must be 0 or 1");
   if (ctx->n_cut > 0 && o.precision != FMO_PREC_FP64)
     return fail(ctx, FMO_ERR_UNSUPPORTED, "cut bonds (hybrid orbital projection) need precision FP64");
   cudaSetDevice(ctx->device);
@@ -1334,6 +1741,15 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   for (int f = 0; f < nf; ++f) if (ctx->r_mono_status[f] != FMO_SCC_CONVERGED) ++failed;
   for (size_t t = 0; t < ntri; ++t) if (st_tri[t] != FMO_SCC_CONVERGED) ++failed;
   ctx->r_tri = tri_flat;
+  ctx->r_pair_k.assign(pair_scc.begin(), pair_scc.begin() + std::max<long long>(npair, 0));
+  ctx->grad_ready = (o.precision == FMO_PREC_FP64) || o.want_gradient;
+  ctx->last_cuts_ok = true;
+  for (auto& t : tri_tu) {
+    const long long nf_ = nf;
+    auto pix = [&](long long a, long long b) { return a * (2 * nf_ - a - 1) / 2 + (b - a - 1); };
+    if (pair_scc[pix(t[0], t[1])] < 0 || pair_scc[pix(t[0], t[2])] < 0 || pair_scc[pix(t[1], t[2])] < 0)
+      ctx->last_cuts_ok = false;
+  }
   long long iters = 0;
   for (int p = 0; p < 3; ++p) iters += ctx->stats.iters_fp32[p] + ctx->stats.iters_fp64[p];
   ctx->stats.scc_iterations = iters;
@@ -1408,35 +1824,20 @@ fmo_status fmo_get_dimers(fmo_ctx* ctx, int64_t* n, int32_t* ij, double* dE, dou
 fmo_status fmo_get_gradient(fmo_ctx* ctx, double* grad) {
   if (!ctx || !grad) return FMO_ERR_ARG;
   if (!ctx->have_result) return fail(ctx, FMO_ERR_STATE, "no results: call fmo_run");
-  if (ctx->n_frag != 1 || ctx->n_cut > 0)
-    return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: only a system that is one fragment without cut bonds");
-  if (ctx->last_precision != FMO_PREC_FP64)
-    return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: needs a run in precision FP64");
+  if (ctx->n_cut > 0)
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: cut bonds (hybrid orbital projection) are not covered");
+  if (!ctx->grad_ready)
+    return fail(ctx, FMO_ERR_UNSUPPORTED,
+                "gradient: the run's n-mer densities are not converged in FP64 (precision FP64, or mixed with "
+                "want_gradient = 1)");
+  if (!ctx->last_cuts_ok)
+    return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: a trimer holds an ES-DIM pair (trimer_cut > dimer_cut)");
   g_ctx = ctx;
   cudaSetDevice(ctx->device);
-  cudaStream_t st = ctx->own_stream;
-  Pass& P = ctx->mono;
-  const Nmer& m = P.nm[0];
-  if (m.nat > 8 * kBlock) return fail(ctx, FMO_ERR_UNSUPPORTED, "gradient: more than 2048 atoms");
-  CK(ctx->d_grad_work.ensure(sizeof(double) * 4 * (size_t)m.n * m.n));
-  CK(ctx->d_grad.ensure(sizeof(double) * 3 * (size_t)m.nat + sizeof(int)));
-  int* d_frac = reinterpret_cast<int*>(ctx->d_grad.as<double>() + 3 * (size_t)m.nat);
-  CK(cudaMemsetAsync(d_frac, 0, sizeof(int), st));
-  CK(launch_xtb_gradient(st, P.d_nm.as<Nmer>(), m.n, m.nsh, m.nat, ctx->ftab(), ctx->d_xyz.as<double>(),
-                         ctx->d_elem.as<int>(), ctx->d_atom_sh0.as<int>(), ctx->d_el.as<DevElem>(),
-                         ctx->d_kab.as<double>(), ctx->ne, ctx->d_prim.as<PrimPair>(), ctx->d_cn.as<double>(), ctx->g,
-                         P.S.as<double>(), P.H0.as<double>(), P.CTd.as<double>(), P.eps.as<double>(),
-                         P.gam.as<double>(), ctx->d_grad_work.as<double>(), ctx->d_grad.as<double>(), d_frac));
-  std::vector<double> g(3 * (size_t)m.nat);
-  int frac = 0;
-  CK(d2h(g.data(), ctx->d_grad.p, sizeof(double) * g.size(), st));
-  CK(d2h(&frac, d_frac, sizeof(int), st));
-  CK(sync_stream(st));
-  if (frac)
-    return fail(ctx, FMO_ERR_UNSUPPORTED,
-                "gradient: fractional occupations (a gap of fewer than ~25 kT); the energy-weighted density "
-                "is formed for occupations of 2 or 0");
-  for (int i = 0; i < m.nat; ++i)   // internal atom order -> input order
+  std::vector<double> g;
+  const fmo_status fs = compute_gradient(ctx, g);
+  if (fs != FMO_OK) return fs;
+  for (int i = 0; i < ctx->n_atoms; ++i)   // internal atom order -> input order
     for (int c = 0; c < 3; ++c) grad[3 * ctx->perm[i] + c] = g[3 * (size_t)i + c];
   return FMO_OK;
 }

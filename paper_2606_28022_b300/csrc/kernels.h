@@ -121,15 +121,107 @@ cudaError_t launch_pair_distance(cudaStream_t st, int n_frag, FragTab ft, const 
 cudaError_t launch_esdim(cudaStream_t st, int n_pairs, const int2* pairs, const long long* out_idx, FragTab ft,
                          const double* xyz, const int* sh_atom, const double* sh_inv_eta, const double* dq,
                          GParams g, double* out, const double* gam_full = nullptr, int n_sh = 0);
-// Analytic gradient of the GFN1-xTB energy of one n-mer that is one fragment
-// without hybrid-orbital projection (gradient.cu): grad[nat][3] in the
-// fragment's atom order; work holds 4 n^2 doubles; *frac (zeroed by the
-// caller) is set to 1 if an occupation is fractional.
-cudaError_t launch_xtb_gradient(cudaStream_t st, const Nmer* nm, int n, int nsh, int nat, FragTab ft,
-                                const double* xyz, const int* elem, const int* atom_sh0, const DevElem* el,
-                                const double* kab, int ne, const PrimPair* prim, const double* cn, GParams g,
-                                const double* S, const double* H0, const double* CT, const double* eps,
-                                const double* gam, double* work, double* grad, int* frac);
+// ---------------------------------------------------------------------------
+// Analytic FMO gradient (fmo_gradient.cu).  Every monomer and SCC n-mer X of
+// the FMO energy enters as a term with coefficient m (the FMO2/FMO3
+// inclusion-exclusion counts); the charge-space Z-vector z of the monomer
+// charges carries the response.
+
+enum { kGradMonomer = 0, kGradNmer = 1, kGradResponse = 2 };
+
+struct GradTerm {
+  Nmer nm;              // layout of the n-mer in its pass
+  const double* S;      // its overlap, H0 (n x n) and gamma block (nsh x nsh)
+  const double* H0;
+  const double* gam;
+  const double* CT;     // energy terms: FP64 orbital rows of the converged solve
+  const double* eps;    //               and their orbital energies
+  const double* dq;     // its converged shell charges (nsh)
+  const double* esp;    // its embedding potential ESP^{not X} (nsh); null for response terms
+  double* Pa;           // n x n: density (energy) or first-order density (response)
+  double* W;            // n x n: energy-weighted density, or its first-order change
+  const double* Pb;     // response terms: the monomer density (n x n), else null
+  double* sa;           // nsh: shell shifts of the converged solve (ESP included)
+  const double* sb;     // response terms: first-order shell shifts, else null
+  const double* qb;     // response terms: first-order charges, else null (1/2 dq)
+  double* work;         // energy terms: 3 n^2 doubles of scratch
+  double m;             // coefficient of the term
+  double es;            // SCC dimers at level >= 2: 1 (its pair leaves the all-pairs ES-DIM form)
+  int kind;             // kGradMonomer, kGradNmer, kGradResponse
+  int with_rep;
+  long long aslot;      // offset of its per-atom slots (nat x 4: g, F)
+  long long sslot;      // offset of its per-shell slots (nsh x 2: w, d)
+};
+
+// One monomer's response data (kernels fmo_gradient.cu): canonical orbitals
+// and energies at its converged charges, and its susceptibility chi.
+struct MonoResp {
+  double* C;            // n x n canonical orbital rows
+  double* eps;          // n: their orbital energies
+  double* focc;         // n: their Fermi occupations (Eq. 6)
+  double* chi;          // nsh x nsh
+  double* sig;          // nsh: shell shifts (ESP included)
+  double* work;         // scratch: 7 n^2 + npad^2 + 3 nsh^2 doubles
+};
+
+struct GradLaunch {
+  FragTab ft;
+  const double* xyz;
+  const int* elem;
+  const int* atom_sh0;
+  const DevElem* el;
+  const double* kab;
+  int ne;
+  const PrimPair* prim;
+  const double* cn;
+  GParams g;
+  const double* dq_mono;  // converged monomer charges, global shell order
+  int max_n, max_nsh, max_nat;
+};
+
+// energy terms: occupations, density P, shifts, energy-weighted density W~
+cudaError_t launch_grad_prep(cudaStream_t st, int n_terms, const GradTerm* terms, const GradLaunch& L, int* flag);
+// explicit gradient of every term into its slots (sslots may be null for response terms)
+cudaError_t launch_grad_explicit(cudaStream_t st, int n_terms, const GradTerm* terms, const GradLaunch& L,
+                                 double* aslots, double* sslots);
+// per atom (and shell), fixed order: sum of the slots of the entries of its
+// fragment (frag_ptr CSR; ent_aoff / ent_soff slot offsets of the fragment's
+// first atom / shell, ent_soff < 0: no shell slots); g_atom[n_atoms][4],
+// w[n_sh], d[n_sh]; accumulate: add to the outputs instead of overwriting
+cudaError_t launch_grad_gather(cudaStream_t st, int n_atoms, int n_sh, const GradLaunch& L, const int* atom_frag,
+                               const int* sh_frag, const int* frag_ptr, const long long* ent_aoff,
+                               const long long* ent_soff, const double* aslots, const double* sslots,
+                               double* g_atom, double* w, double* d, int accumulate);
+// monomers: canonical orbitals, susceptibility chi (flag |= 2: eigen-solve
+// not converged)
+cudaError_t launch_grad_mono_response(cudaStream_t st, int n_mono, const GradTerm* mono_terms, MonoResp* mr,
+                                      const GradLaunch& L, int* flag);
+// Z-vector operator pieces: y = chi z (block diagonal); out = the monomers'
+// own gamma blocks times v (sh0: first global shell of each monomer)
+cudaError_t launch_chi_apply(cudaStream_t st, int n_mono, const GradTerm* mono_terms, const MonoResp* mr,
+                             const int* sh0, const double* z, double* y);
+cudaError_t launch_intra_gamma(cudaStream_t st, int n_mono, const GradTerm* mono_terms, const int* sh0,
+                               const double* v, double* out);
+// out[j] = V_j . u (j < k, rows of V ldv apart); u -= sum_j h_j V_j;
+// out = a x + b y + c z (y, z may be null)
+cudaError_t launch_vec_dots(cudaStream_t st, int n, int k, const double* V, long long ldv, const double* u,
+                            double* out);
+cudaError_t launch_vec_update(cudaStream_t st, int n, int k, const double* V, long long ldv, const double* h,
+                              double* u);
+cudaError_t launch_vec_lincomb3(cudaStream_t st, int n, double a, const double* x, double b, const double* y,
+                                double c, const double* z, double* out);
+// monomers: first-order P, W~ and shifts along the Z-vector potential z
+// (y = chi z), into the response terms
+cudaError_t launch_grad_first_order(cudaStream_t st, int n_mono, const GradTerm* resp_terms, const MonoResp* mr,
+                                    const GradLaunch& L, const double* z, const double* y);
+// per atom: gathered term gradient + CN chain rule sum_A F_A dCN_A + the
+// inter-fragment Coulomb sum over (a_s q_t + q_s a_t) dgamma_st
+cudaError_t launch_grad_cn_coulomb(cudaStream_t st, int n_atoms, int n_sh, const GradLaunch& L,
+                                   const int* atom_frag, const int* sh_atom, const double* sh_inv_eta,
+                                   const double* a, const double* g_atom, double* grad);
+// largest dynamic shared memory of the gradient kernels for these maxima
+size_t grad_smem_max(const GradLaunch& L);
+
 // out[i] = (float)in[i], i < n
 cudaError_t launch_to_float(cudaStream_t st, long long n, const double* in, float* out);
 cudaError_t launch_stamp(cudaStream_t st, unsigned long long* t);

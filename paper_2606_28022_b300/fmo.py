@@ -57,7 +57,8 @@ class FmoOptions(C.Structure):
                 ("schedule", C.c_int32), ("monomer_loop", C.c_int32), ("dimer_cut", C.c_double),
                 ("trimer_cut", C.c_double), ("scc_tol", C.c_double), ("e_tol", C.c_double),
                 ("outer_tol", C.c_double), ("mixed_switch_tol", C.c_double),
-                ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("nmer_finish", C.c_int32)]
+                ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("nmer_finish", C.c_int32),
+                ("want_gradient", C.c_int32)]
 
 
 class FmoStats(C.Structure):
@@ -70,7 +71,8 @@ class FmoStats(C.Structure):
                 ("ms_scc", C.c_double * 3), ("scc_launches", C.c_int64 * 3),
                 ("iters_fp32", C.c_int64 * 3), ("iters_fp64", C.c_int64 * 3),
                 ("flops_fp32", C.c_double * 3), ("flops_fp64", C.c_double * 3),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("ms_gradient", C.c_double),
+                ("zvector_iterations", C.c_int32), ("pad_", C.c_int32), ("zvector_residual", C.c_double)]
 
     def as_dict(self):
         out = {}

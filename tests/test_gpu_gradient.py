@@ -1,6 +1,7 @@
-"""GPU analytic gradient (fmo_get_gradient, through the C ABI) against the
-oracle's analytic single-system gradient, itself pinned to finite
-differences (tests/test_gradient_oracle.py)."""
+"""GPU analytic gradient (fmo_get_gradient, through the C ABI) of systems that
+are one fragment against the oracle's analytic single-system gradient, itself
+pinned to finite differences (tests/test_gradient_oracle.py).  Several
+fragments: tests/test_gpu_fmo_gradient.py."""
 import dataclasses
 
 import numpy as np
@@ -46,24 +47,26 @@ def test_gradient_of_one_fragment_system_matches_oracle(gpu, params, water64, na
 
 def test_gradient_refuses_what_it_does_not_cover(gpu, params, water64):
     from paper_2606_28022_b300 import fmo
-    gpu.set_system(water64.subsystem([0, 1]))
-    gpu.run(fmo.options())
-    with pytest.raises(fmo.FMOError):
-        gpu.gradient()                                   # two fragments
     gpu.set_system(water64.subsystem([0]))
     gpu.run(fmo.options(precision="mixed"))
     with pytest.raises(fmo.FMOError):
-        gpu.gradient()                                   # mixed precision
+        gpu.gradient()                 # n-mer densities not converged in FP64
+    gpu.set_system(G.polyalanine_helix(3))
+    gpu.run(fmo.options())
+    with pytest.raises(fmo.FMOError):
+        gpu.gradient()                 # cut bonds (hybrid orbital projection)
 
 
-def test_gradient_refuses_fractional_occupations(params):
-    # a high electronic temperature smears the occupations: the energy-weighted
-    # density of the kernel (1/2 P F P) needs occupations of 2 or 0
+def test_gradient_with_fractional_occupations(params):
+    # a high electronic temperature smears the occupations over the frontier
+    # orbitals: P and W~ are the Fermi-weighted sums over canonical orbitals
     from paper_2606_28022_b300 import fmo
     hot = dataclasses.replace(params, t_el=20000.0)
+    s = G.polyalanine_helix(1)
     g = fmo.FMO(hot, 0)
-    g.set_system(G.polyalanine_helix(1))
+    g.set_system(s)
     g.run(fmo.options(level=1))
-    with pytest.raises(fmo.FMOError):
-        g.gradient()
+    grad = g.gradient()
     g.close()
+    ref = ograd.scc_gradient(s.Z, s.xyz, hot)
+    assert np.max(np.abs(grad - ref)) < G_TOL
