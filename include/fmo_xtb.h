@@ -369,6 +369,17 @@ fmo_status fmo_scc_solve_noalloc(const fmo_params *p, int32_t n_atoms, const int
                                  const fmo_options *opt, double *energy_dev, double *shell_dq_dev,
                                  int32_t *status_dev, void *cuda_stream, char *err, int32_t err_len);
 
+/*
+ * Measured FMA throughput of CUDA device `device` in TFLOP/s (2 flops per
+ * FMA): precision FMO_PREC_MIXED measures FP32, FMO_PREC_FP64 FP64.  A
+ * diagnostic for the roofline of the SCC kernel; the paper has no
+ * counterpart.  Runs an FMA-loop kernel (8 blocks of 256 threads per SM,
+ * eight independent FMA chains per thread) on a private stream and returns
+ * the best of five timed launches.  Allocates and frees 8 bytes of device
+ * memory.  Errors: FMO_ERR_ARG (NULL, unknown precision), FMO_ERR_CUDA.
+ */
+fmo_status fmo_fma_peak(int32_t precision, int32_t device, double *tflops);
+
 /* Message of the last error on this context ("" if none). */
 const char *fmo_last_error(const fmo_ctx *ctx);
 

@@ -27,7 +27,7 @@ SYMBOLS = ["fmo_options_default", "fmo_create", "fmo_set_system", "fmo_set_coord
            "fmo_set_coordinates_device", "fmo_set_guess", "fmo_run", "fmo_get_energy",
            "fmo_get_sizes", "fmo_get_monomers", "fmo_get_dimers", "fmo_get_trimers", "fmo_get_gradient",
            "fmo_get_stats", "fmo_last_error", "fmo_destroy", "fmo_mlp_init", "fmo_mlp_set_weights",
-           "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train"]
+           "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train", "fmo_scc_solve_noalloc", "fmo_fma_peak"]
 MLP_N_WEIGHTS = 26908
 
 
@@ -118,6 +118,8 @@ def load_library(path: str | None = None):
     lib.fmo_mlp_get_weights.argtypes = [vp, fp, C.POINTER(i64)]
     lib.fmo_mlp_predict.argtypes = [vp, dp]
     lib.fmo_mlp_train.argtypes = [vp, i32, dp, dp, i32, i32, C.c_double, C.c_uint64, dp]
+    lib.fmo_fma_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
+    lib.fmo_scc_solve_noalloc.argtypes = [vp, i32, ip, vp, i32, vp, vp, vp, vp, vp, vp, C.c_char_p, i32]
     lib.fmo_last_error.argtypes = [vp]
     lib.fmo_last_error.restype = C.c_char_p
     lib.fmo_destroy.argtypes = [vp]
@@ -128,6 +130,15 @@ def load_library(path: str | None = None):
     if path is None:
         _lib_handle = lib
     return lib
+
+
+def fma_peak(precision: str = "fp32", device: int = 0) -> float:
+    """Measured FMA throughput of the device in TFLOP/s (fmo_fma_peak)."""
+    t = C.c_double(0.0)
+    st = load_library().fmo_fma_peak(PREC_FP64 if precision == "fp64" else PREC_MIXED, device, C.byref(t))
+    if st != FMO_OK:
+        raise FMOError(st, "fmo_fma_peak failed")
+    return t.value
 
 
 def params_to_c(params: Params) -> FmoParams:
