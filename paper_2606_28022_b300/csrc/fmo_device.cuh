@@ -276,6 +276,162 @@ __device__ __forceinline__ void block_gemm_tile(int M, int N, int K, const T* __
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Block-level FP32 GEMM on the tensor cores, same interface and result
+// definition as block_gemm_tile (A, B float; kscale of type TS; kidx / kidx_b
+// index lists over k): C[m][n] = sum_k a(m,k) b(n,k).
+//
+// mma.sync m16n8k8 TF32 with FP32 accumulation, each operand split as
+// x = hi + lo (hi = x rounded to TF32, lo = x - hi rounded to TF32) and
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs): the dropped a_lo b_lo
+// is ~2^-22 of |a b|, so the products keep FP32-grade accuracy (the SCC's
+// FP32 phase converges its charges to 1e-5 through them).  The tensor cores'
+// accumulation does not round to nearest, so over K terms its error would
+// grow like K: the three MMAs of each k-step go into a zeroed register and
+// are added to the running sum by an ordinary round-to-nearest addition.
+// CTA tile 64 x 64, k-slices of 32 staged in shared memory (rows padded to 36
+// floats: the fragment reads of a warp hit 32 distinct banks); 8 warps as
+// 2 (m) x 4 (n), each 32 x 16 = two m16 x two n8 MMA tiles.  The next k-slice
+// is fetched into registers while the current one is multiplied.
+// smem: 2 * 64 * 36 floats (<= kGemmSmemElems doubles).  Ends with __syncthreads().
+
+constexpr int kTcBM = 64, kTcBN = 64, kTcBK = 32, kTcLD = kTcBK + 4;
+static_assert(2 * 64 * (32 + 4) * 4 <= kGemmSmemElems * 8, "tensor-core GEMM staging exceeds the GEMM smem region");
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <typename TS>
+__device__ __forceinline__ void block_gemm_tc(int M, int N, int K, const float* __restrict__ A, long long sam,
+                                           long long sak, const float* __restrict__ B, long long sbn,
+                                           long long sbk, float* __restrict__ C, long long ldc,
+                                           const int* __restrict__ kidx, const int* __restrict__ kidx_b,
+                                           const TS* __restrict__ kscale, float* smem) {
+  float* As = smem;                      // [64][36]
+  float* Bs = smem + kTcBM * kTcLD;      // [64][36]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int g = lane >> 2, tg = lane & 3;
+  const int wm = wid >> 2, wn = wid & 3;   // warp tile: rows wm*32 + [0,32), cols wn*16 + [0,16)
+  // staging map: 8 elements of each operand per thread along its contiguous
+  // dimension (k if the k stride is 1, else m / n)
+  const bool a_kc = (sak == 1), b_kc = (sbk == 1);
+  for (int m0 = 0; m0 < M; m0 += kTcBM) {
+    for (int n0 = 0; n0 < N; n0 += kTcBN) {
+      float acc[2][2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+      float ra[8], rb[8];
+      auto fetch = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int e = tid + r * kBlock;
+          int mm, kk;
+          if (a_kc) { kk = e % kTcBK; mm = e / kTcBK; } else { mm = e % kTcBM; kk = e / kTcBM; }
+          const int gm = m0 + mm, gk = k0 + kk;
+          float v = 0.f;
+          if (gm < M && gk < K) {
+            v = A[(long long)gm * sam + (long long)(kidx ? kidx[gk] : gk) * sak];
+            if (kscale) {
+              if constexpr (sizeof(TS) == 4) v *= float(kscale[gk]);
+              else v = float(double(v) * kscale[gk]);
+            }
+          }
+          ra[r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int e = tid + r * kBlock;
+          int nn, kk;
+          if (b_kc) { kk = e % kTcBK; nn = e / kTcBK; } else { nn = e % kTcBN; kk = e / kTcBN; }
+          const int gn = n0 + nn, gk = k0 + kk;
+          rb[r] = (gn < N && gk < K) ? B[(long long)gn * sbn + (long long)(kidx_b ? kidx_b[gk] : gk) * sbk] : 0.f;
+        }
+      };
+      fetch(0);
+      for (int k0 = 0; k0 < K; k0 += kTcBK) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int e = tid + r * kBlock;
+          int mm, kk;
+          if (a_kc) { kk = e % kTcBK; mm = e / kTcBK; } else { mm = e % kTcBM; kk = e / kTcBM; }
+          As[mm * kTcLD + kk] = ra[r];
+          int nn, kb;
+          if (b_kc) { kb = e % kTcBK; nn = e / kTcBK; } else { nn = e % kTcBN; kb = e / kTcBN; }
+          Bs[nn * kTcLD + kb] = rb[r];
+        }
+        __syncthreads();
+        if (k0 + kTcBK < K) fetch(k0 + kTcBK);   // in flight during the MMAs
+#pragma unroll
+        for (int ks = 0; ks < kTcBK; ks += 8) {
+          uint32_t ah[2][4], al[2][4], bh[2][2], bl[2][2];
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const float* ap = As + (wm * 32 + i * 16 + g) * kTcLD + ks + tg;
+            const float x[4] = {ap[0], ap[8 * kTcLD], ap[4], ap[8 * kTcLD + 4]};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              ah[i][c] = to_tf32(x[c]);
+              al[i][c] = to_tf32(x[c] - __uint_as_float(ah[i][c]));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const float* bp = Bs + (wn * 16 + j * 8 + g) * kTcLD + ks + tg;
+            const float x[2] = {bp[0], bp[4]};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              bh[j][c] = to_tf32(x[c]);
+              bl[j][c] = to_tf32(x[c] - __uint_as_float(bh[j][c]));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              float t[4] = {0.f, 0.f, 0.f, 0.f};
+              mma_tf32(t, al[i], bh[j]);
+              mma_tf32(t, ah[i], bl[j]);
+              mma_tf32(t, ah[i], bh[j]);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[i][j][c] = __fadd_rn(acc[i][j][c], t[c]);
+            }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int r0 = m0 + wm * 32 + i * 16 + g, c0 = n0 + wn * 16 + j * 8 + 2 * tg;
+          if (r0 < M) {
+            if (c0 < N) C[(long long)r0 * ldc + c0] = acc[i][j][0];
+            if (c0 + 1 < N) C[(long long)r0 * ldc + c0 + 1] = acc[i][j][1];
+          }
+          if (r0 + 8 < M) {
+            if (c0 < N) C[(long long)(r0 + 8) * ldc + c0] = acc[i][j][2];
+            if (c0 + 1 < N) C[(long long)(r0 + 8) * ldc + c0 + 1] = acc[i][j][3];
+          }
+        }
+    }
+  }
+  __syncthreads();
+}
+
 // micro-tile (4 or 5 per thread: tile edge 64 or 80) with the least padding
 // of a dimension d, the smaller on ties
 __device__ __forceinline__ int gemm_micro(int d) {
@@ -291,6 +447,15 @@ __device__ void block_gemm(int M, int N, int K, const T* __restrict__ A, long lo
                            const TB* __restrict__ B, long long sbn, long long sbk, T* __restrict__ C,
                            long long ldc, const int* __restrict__ kidx, const int* __restrict__ kidx_b,
                            const typename NoDeduce<TS>::type* __restrict__ kscale, T* smem) {
+  if constexpr (sizeof(T) == 4 && sizeof(TB) == 4) {
+    // tensor cores where the 64 x 64 tiles waste little (n = 116, 174, 232,
+    // 348: ~10%); the SIMT tiles (64 or 80 wide) fit the rest better
+    const float pad = float((M + 63) / 64 * 64) / float(M) * (float((N + 63) / 64 * 64) / float(N));
+    if (M >= 96 && N >= 96 && pad <= 1.25f) {
+      block_gemm_tc<TS>(M, N, K, A, sam, sak, B, sbn, sbk, C, ldc, kidx, kidx_b, kscale, smem);
+      return;
+    }
+  }
   const int tm = gemm_micro(M), tn = gemm_micro(N);
 #define FMO_GEMM_CASE(a, b)                                                                              \
   if (tm == a && tn == b) {                                                                              \
@@ -495,9 +660,9 @@ struct JacobiScratch {
   int* act;
 };
 
-template <typename T>
-__device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol, double tol,
-                            int max_sweeps, JacobiScratch<T> js, double* red) {
+template <typename T, int kUnroll>
+__device__ int block_jacobi_u(T* A, int lda, int n, T* CT, long long ldc, int ncol, double tol,
+                              int max_sweeps, JacobiScratch<T> js, double* red) {
   const int npad = n + (n & 1);
   const int half = npad / 2;
   const int tid = threadIdx.x;
@@ -551,45 +716,73 @@ __device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol
       ++rotations;
       // 2x2 block updates A <- J^T A J: one warp per active pair k, lanes over
       // the partner pairs k2 (a block of two active pairs is done once, by
-      // the warp of the smaller k)
+      // the warp of the smaller k).  Every block is read and written by one
+      // lane only, so each lane first loads kUnroll partner blocks and then
+      // updates them: the loads are in flight together (A in global memory,
+      // large n-mers: one load's latency is ~1 us).
       for (int i = wid; i < na; i += nw) {
         const int k = list[i];
         const int p = js.p[k], q = js.q[k];
         const T c = js.c[k], s = js.s[k];
-        for (int k2 = lane; k2 < half; k2 += 32) {
-          if (js.act[k2] && k2 < k) continue;
-          const int p2 = js.p[k2], q2 = js.q[k2];
-          const T c2 = js.c[k2], s2 = js.s[k2];
-          const T b00 = A[p * lda + p2], b01 = A[p * lda + q2];
-          const T b10 = A[q * lda + p2], b11 = A[q * lda + q2];
-          const T t00 = b00 * c2 - b01 * s2, t01 = b00 * s2 + b01 * c2;
-          const T t10 = b10 * c2 - b11 * s2, t11 = b10 * s2 + b11 * c2;
-          const T x00 = c * t00 - s * t10, x01 = c * t01 - s * t11;
-          const T x10 = s * t00 + c * t10, x11 = s * t01 + c * t11;
-          if (k == k2) {
-            A[p * lda + p] = x00;
-            A[q * lda + q] = x11;
-            A[p * lda + q] = T(0);
-            A[q * lda + p] = T(0);
-          } else {
-            A[p * lda + p2] = x00; A[p * lda + q2] = x01;
-            A[q * lda + p2] = x10; A[q * lda + q2] = x11;
-            A[p2 * lda + p] = x00; A[q2 * lda + p] = x01;
-            A[p2 * lda + q] = x10; A[q2 * lda + q] = x11;
+        for (int k2b = lane; k2b < half; k2b += 32 * kUnroll) {
+          int p2[kUnroll], q2[kUnroll];
+          bool ok[kUnroll];
+          T c2[kUnroll], s2[kUnroll], b00[kUnroll], b01[kUnroll], b10[kUnroll], b11[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int k2 = k2b + 32 * u;
+            ok[u] = k2 < half && !(js.act[k2] && k2 < k);
+            if (ok[u]) {
+              p2[u] = js.p[k2]; q2[u] = js.q[k2];
+              c2[u] = js.c[k2]; s2[u] = js.s[k2];
+              b00[u] = A[p * lda + p2[u]]; b01[u] = A[p * lda + q2[u]];
+              b10[u] = A[q * lda + p2[u]]; b11[u] = A[q * lda + q2[u]];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            if (!ok[u]) continue;
+            const T t00 = b00[u] * c2[u] - b01[u] * s2[u], t01 = b00[u] * s2[u] + b01[u] * c2[u];
+            const T t10 = b10[u] * c2[u] - b11[u] * s2[u], t11 = b10[u] * s2[u] + b11[u] * c2[u];
+            const T x00 = c * t00 - s * t10, x01 = c * t01 - s * t11;
+            const T x10 = s * t00 + c * t10, x11 = s * t01 + c * t11;
+            if (k == k2b + 32 * u) {
+              A[p * lda + p] = x00;
+              A[q * lda + q] = x11;
+              A[p * lda + q] = T(0);
+              A[q * lda + p] = T(0);
+            } else {
+              A[p * lda + p2[u]] = x00; A[p * lda + q2[u]] = x01;
+              A[q * lda + p2[u]] = x10; A[q * lda + q2[u]] = x11;
+              A[p2[u] * lda + p] = x00; A[q2[u] * lda + p] = x01;
+              A[p2[u] * lda + q] = x10; A[q2[u] * lda + q] = x11;
+            }
           }
         }
       }
-      // rotate the rows p, q of CT: one warp per active pair, lanes over columns
+      // rotate the rows p, q of CT: one warp per active pair, lanes over
+      // columns, kUnroll loads of each row in flight
       for (int i = wid; i < na; i += nw) {
         const int k = list[i];
         const int p = js.p[k], q = js.q[k];
         const T c = js.c[k], s = js.s[k];
         T* rp = CT + p * ldc;
         T* rq = CT + q * ldc;
-        for (int j = lane; j < ncol; j += 32) {
-          const T vp = rp[j], vq = rq[j];
-          rp[j] = c * vp - s * vq;
-          rq[j] = s * vp + c * vq;
+        for (int jb = lane; jb < ncol; jb += 32 * kUnroll) {
+          T vp[kUnroll], vq[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int j = jb + 32 * u;
+            if (j < ncol) { vp[u] = rp[j]; vq[u] = rq[j]; }
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int j = jb + 32 * u;
+            if (j < ncol) {
+              rp[j] = c * vp[u] - s * vq[u];
+              rq[j] = s * vp[u] + c * vq[u];
+            }
+          }
         }
       }
       __syncthreads();
@@ -597,6 +790,16 @@ __device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol
     if (rotations == 0) return sweep;
   }
   return -1;
+}
+
+// A in shared memory (every n-mer that fits): one partner block per lane at a
+// time (fewer live registers); A in global memory: four blocks in flight per
+// lane.
+template <typename T>
+__device__ int block_jacobi(T* A, int lda, int n, T* CT, long long ldc, int ncol, double tol, int max_sweeps,
+                            JacobiScratch<T> js, double* red) {
+  if (__isShared(A)) return block_jacobi_u<T, 1>(A, lda, n, CT, ldc, ncol, tol, max_sweeps, js, red);
+  return block_jacobi_u<T, 4>(A, lda, n, CT, ldc, ncol, tol, max_sweeps, js, red);
 }
 
 }  // namespace fmo

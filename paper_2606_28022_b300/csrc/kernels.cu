@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kBlock) lowdin_kernel(const Nmer* __restrict__
   T* A;
   if (a_in_smem) { A = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)npad * npad; }
   else A = Ag + nm.apad;  // global scratch, npad*npad per n-mer
-  T* gemm = reinterpret_cast<T*>(sp); sp += sizeof(T) * kGemmSmemElems;
+  T* gemm = reinterpret_cast<T*>(sp); sp += sizeof(double) * kGemmSmemElems;   // room for any GEMM variant
   double* red = reinterpret_cast<double*>(sp); sp += sizeof(double) * 32;
   double* scale = reinterpret_cast<double*>(sp); sp += sizeof(double) * npad;
   JacobiScratch<T> js;
@@ -2053,7 +2053,7 @@ static size_t lowdin_smem(int max_n, int elem_bytes, int a_in_smem) {
   const int npad = max_n + (max_n & 1);
   size_t b = 0;
   if (a_in_smem) b += (size_t)elem_bytes * npad * npad;
-  b += (size_t)elem_bytes * kGemmSmemElems + sizeof(double) * 32 + sizeof(double) * npad + 3 * sizeof(int) * npad;
+  b += sizeof(double) * kGemmSmemElems + sizeof(double) * 32 + sizeof(double) * npad + 3 * sizeof(int) * npad;
   b = (b + 15) & ~size_t(15);
   b += 2 * (size_t)elem_bytes * npad + 16;
   return b;
