@@ -101,6 +101,7 @@ typedef struct fmo_params {
 enum { FMO_PREC_FP64 = 0, FMO_PREC_MIXED = 1 };
 enum { FMO_LOOP_GLOBAL = 0, FMO_LOOP_NESTED = 1 };
 enum { FMO_NMER_FINISH_ENERGY = 0, FMO_NMER_FINISH_ITERATE = 1 };
+enum { FMO_ESP_AUTO = 0, FMO_ESP_PAIRWISE = 1 };
 
 typedef struct fmo_options {
   int32_t level;            /* 1 = FMO1, 2 = FMO2 (Eq. 12), 3 = FMO3 (Eq. 16) */
@@ -147,6 +148,13 @@ typedef struct fmo_options {
                                in FP64 after the FP32 phase (nmer_finish and
                                mixed_finish are ignored).  Precision FP64 runs
                                always allow the gradient. */
+  int32_t esp_mode;         /* the supersystem potential phi = gamma dq (Eq. 21)
+                               of every monomer-loop step: FMO_ESP_AUTO
+                               (default) keeps gamma of all shell pairs in
+                               device memory when it fits (<= 32 GB and <= 1/4
+                               of the free memory) and forms phi as a matrix-
+                               vector product; FMO_ESP_PAIRWISE evaluates gamma
+                               pair by pair every step (no n_sh^2 buffer). */
 } fmo_options;
 
 /* Counters of the last fmo_run. */
@@ -172,7 +180,8 @@ typedef struct fmo_stats {
   int64_t d2h_bytes;          /* device -> host bytes copied by the run */
   double ms_gradient;         /* last fmo_get_gradient (CUDA events) */
   int32_t zvector_iterations; /* GMRES iterations of its Z-vector solve */
-  int32_t pad_;
+  int32_t guess_restarts;     /* 1: the learned guess's monomer loop did not
+                                 converge and the run restarted from neutral */
   double zvector_residual;    /* final ||w - (1 - Gamma chi) z|| / ||w|| */
 } fmo_stats;
 

@@ -1438,6 +1438,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (o.nmer_finish != FMO_NMER_FINISH_ENERGY && o.nmer_finish != FMO_NMER_FINISH_ITERATE)
     return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
   if (o.want_gradient != 0 && o.want_gradient != 1) return fail(ctx, FMO_ERR_ARG, "want_gradient must be 0 or 1");
+  if (o.esp_mode != FMO_ESP_AUTO && o.esp_mode != FMO_ESP_PAIRWISE) return fail(ctx, FMO_ERR_ARG, "unknown esp_mode");
   if (ctx->n_cut > 0 && o.precision != FMO_PREC_FP64)
     return fail(ctx, FMO_ERR_UNSUPPORTED, "cut bonds (hybrid orbital projection) need precision FP64");
   cudaSetDevice(ctx->device);
@@ -1462,7 +1463,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     const size_t gbytes = sizeof(double) * (size_t)ctx->n_sh * (size_t)ctx->n_sh;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    ctx->gam_full_ok = gbytes <= kGammaFullMaxBytes && (gbytes <= ctx->d_gam_full.cap || gbytes <= free_b / 4);
+    ctx->gam_full_ok = o.esp_mode == FMO_ESP_AUTO && gbytes <= kGammaFullMaxBytes &&
+                       (gbytes <= ctx->d_gam_full.cap || gbytes <= free_b / 4);
     if (ctx->gam_full_ok) {
       CK(ctx->d_gam_full.ensure(gbytes));
       CK(launch_gamma_full(st, ctx->n_sh, ctx->d_xyz.as<double>(), ctx->d_sh_atom.as<int>(),
@@ -1572,7 +1574,9 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     for (auto& e : ev) cudaEventDestroy(e);
     fmo_options o2 = o;
     o2.guess = 0;
-    return fmo_run(ctx, &o2, cuda_stream);
+    const fmo_status rs = fmo_run(ctx, &o2, cuda_stream);
+    ctx->stats.guess_restarts = 1;
+    return rs;
   }
   // frozen ESP of the final monomer charges
   CK(compute_phi(ctx, st, 0));
@@ -1767,8 +1771,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   for (int s : st_dim) timeout |= (s == FMO_SCC_TIMEOUT);
   for (int s : st_tri) timeout |= (s == FMO_SCC_TIMEOUT);
   if (timeout) return fail(ctx, FMO_ERR_TIMEOUT, "deadline reached");
-  for (double v : ctx->totals) if (std::isinf(v)) return fail(ctx, FMO_ERR_NAN, "non-finite total");
-  if (o.level >= 2 && !std::isfinite(ctx->totals[1])) return fail(ctx, FMO_ERR_NAN, "non-finite FMO2 energy");
+  for (int k = 0; k < o.level; ++k)
+    if (!std::isfinite(ctx->totals[k])) return fail(ctx, FMO_ERR_NAN, "non-finite FMO total");
   if (failed > 0 || change >= o.outer_tol)
     return fail(ctx, FMO_ERR_NOT_CONVERGED, std::to_string(failed) + " n-mer solves did not converge");
   ctx->err.clear();

@@ -120,7 +120,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // at different iterations and deadlock at the next barrier.  A sum is
 // therefore reduced onto lane 0 and broadcast from there (an XOR butterfly
 // leaves each lane with a differently rounded total).  Max is exact, so its
-// butterfly gives identical values everywhere.
+// butterfly gives identical values everywhere; it propagates NaN.
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -128,10 +128,16 @@ __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return __shfl_sync(0xffffffffu, v, 0);
 }
+// max that propagates NaN (fmax would drop it: a NaN residual must not read
+// as converged)
+template <typename T>
+__device__ __forceinline__ T nan_max(T a, T b) {
+  return (a != a || b != b) ? (a != a ? a : b) : fmax(a, b);
+}
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 

@@ -864,7 +864,7 @@ __device__ double energy_of_output(const Nmer& nm, const SccArgs& ar, SccSmem& s
       v = warp_sum(v);
       if (lane == 0) {
         part += sm.sig[s] + 0.5 * sm.dqout[s] * v;
-        dmax = fmax(dmax, fabs(sm.dqout[s] - sm.dqin[s]));
+        dmax = nan_max(dmax, fabs(sm.dqout[s] - sm.dqin[s]));
       }
     }
   }
@@ -1409,6 +1409,14 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   }
   __syncthreads();
 
+  // non-finite start charges or potential (a NaN guess): no iterations, NaN
+  // results and status
+  bool bad_in = false;
+  {
+    int b = 0;
+    for (int s = threadIdx.x; s < nsh; s += blockDim.x) b |= !isfinite(sm.dqin[s]) || !isfinite(sm.esp[s]);
+    bad_in = __syncthreads_or(b);
+  }
   const int lda_d = npad;
   PrecPtrs<double> pd{ar.CTd + nm.mat, ar.W1d + nm.mat, ar.W2d + nm.mat,
                       ar.a_smem_d ? reinterpret_cast<double*>(sm.A) : ar.Agd + nm.apad,
@@ -1442,7 +1450,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   int status = FMO_SCC_MAX_ITER_CODE;
   int it = 0, it32 = 0, jac_fail = 0;
   double e_el = 0.0;
-  if (ar.single_step) {
+  if (ar.single_step && !bad_in) {
     // one iteration from the given charges in the given precision; the
     // caller mixes the charges of all monomers together
     phase = ar.step_phase;
@@ -1483,7 +1491,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   if (!ar.single_step && phase == 0 && ct_smem) load_ct_smem();
   long long t_it = clock64();
   if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0) ar.trace[1024] = double(t_it - t_start);
-  for (it = (ar.single_step ? ar.max_iter + 2 : 1); it <= ar.max_iter; ++it) {
+  for (it = (ar.single_step || bad_in ? ar.max_iter + 2 : 1); it <= ar.max_iter; ++it) {
     double diff = 0.0;
     if (phase == 0) {
       if (it32 > 0 && it32 % 4 == 0) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
@@ -1559,6 +1567,14 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   }
   if (ar.single_step) it = 1;
   else if (it > ar.max_iter) it = ar.max_iter;
+  if (bad_in) {
+    it = 0;
+    status = FMO_SCC_NAN_CODE;
+    e_el = __longlong_as_double(0x7ff8000000000000LL);
+    for (int s = threadIdx.x; s < nsh; s += blockDim.x) sm.dqout[s] = sm.dqin[s];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = e_el;
+    __syncthreads();
+  }
   if (jac_fail && status == FMO_SCC_CONVERGED_CODE) status = FMO_SCC_JACOBI_CODE;
   // keep a float copy of the final eigenvectors in global memory for a later
   // warm start
@@ -1835,7 +1851,7 @@ __global__ void __launch_bounds__(1024) global_mix_kernel(int n, double* __restr
   double* px = hist + (size_t)2 * kHist * n;
   double* pF = px + n;
   double dm = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dm = fmax(dm, fabs(xo[i] - x[i]));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dm = nan_max(dm, fabs(xo[i] - x[i]));
   dm = block_max(dm, red);
   double es = 0.0, ec = 0.0;
   for (int i = threadIdx.x; i < nf; i += blockDim.x) neumaier_add(es, ec, e[i]);
@@ -1926,7 +1942,7 @@ __global__ void maxdiff_kernel(int n, const double* __restrict__ a, const double
                                double* __restrict__ out) {
   __shared__ double red[32];
   double m = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(a[i] - b[i]));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = nan_max(m, fabs(a[i] - b[i]));
   m = block_max(m, red);
   if (threadIdx.x == 0) *out = m;
 }

@@ -58,7 +58,7 @@ class FmoOptions(C.Structure):
                 ("trimer_cut", C.c_double), ("scc_tol", C.c_double), ("e_tol", C.c_double),
                 ("outer_tol", C.c_double), ("mixed_switch_tol", C.c_double),
                 ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("nmer_finish", C.c_int32),
-                ("want_gradient", C.c_int32)]
+                ("want_gradient", C.c_int32), ("esp_mode", C.c_int32)]
 
 
 class FmoStats(C.Structure):
@@ -72,7 +72,8 @@ class FmoStats(C.Structure):
                 ("iters_fp32", C.c_int64 * 3), ("iters_fp64", C.c_int64 * 3),
                 ("flops_fp32", C.c_double * 3), ("flops_fp64", C.c_double * 3),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("ms_gradient", C.c_double),
-                ("zvector_iterations", C.c_int32), ("pad_", C.c_int32), ("zvector_residual", C.c_double)]
+                ("zvector_iterations", C.c_int32), ("guess_restarts", C.c_int32),
+                ("zvector_residual", C.c_double)]
 
     def as_dict(self):
         out = {}
@@ -188,6 +189,8 @@ def options(**kw) -> FmoOptions:
             v = {"global": 0, "nested": 1}[v]
         if k == "nmer_finish" and isinstance(v, str):
             v = {"energy": 0, "iterate": 1}[v]
+        if k == "esp_mode" and isinstance(v, str):
+            v = {"auto": 0, "pairwise": 1}[v]
         setattr(o, k, v)
     return o
 
