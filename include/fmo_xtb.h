@@ -274,6 +274,18 @@ fmo_status fmo_mlp_train(fmo_ctx *ctx, int32_t n_frames, const double *xyz_frame
                          int32_t epochs, int32_t batch_frames, double lr, uint64_t seed, double *loss_per_epoch);
 
 /*
+ * Loss and weight gradient of the current model on n_frames frames (same
+ * layouts as fmo_mlp_train), without an update and with the current feature
+ * mean and scale: *loss = the mean squared error of the two-pass prediction
+ * (the potential feature from the first pass, held fixed in the gradient),
+ * grad[FMO_MLP_N_TRAINED] (or NULL) its gradient in the flat weight layout
+ * (W1, b1, W2, b2, W3, b3).  The GPU backward kernels of the training step.
+ */
+#define FMO_MLP_N_TRAINED 26754
+fmo_status fmo_mlp_loss_grad(fmo_ctx *ctx, int32_t n_frames, const double *xyz_frames, const double *shell_dq,
+                             double *loss, float *grad);
+
+/*
  * Run the FMO calculation (Sec. 2.3): coordination numbers of the whole
  * system, monomer SCCs iterated to self-consistency in each other's ESP,
  * n-mer selection, SCC dimers (and trimers) in the frozen ESP, ES-DIM pairs,

@@ -49,11 +49,13 @@ struct Pass {
   DevBuf d_nm, d_order, S, H0, S32, H32, gam, CTd, W1d, W2d, Agd, CTf, W1f, W2f, Agf, esp, dq, eps, hist;
   DevBuf energy, e_el, e_rep, dEV, iters, iters32, status;
   DevBuf V;                               // hybrid orbital projectors (n x n per n-mer)
+  DevBuf hQd, hQf, hDd, hDf, hnq;         // their factors V = Q^T D Q (mixed precision)
   int max_healed_sh = 0, max_projected = 0;
   std::vector<int> h_iters, h_iters32;
   void release() {
     for (DevBuf* b : {&d_nm, &d_order, &S, &H0, &gam, &CTd, &W1d, &W2d, &Agd, &CTf, &W1f, &W2f, &Agf, &esp, &dq,
-                      &eps, &hist, &energy, &e_el, &e_rep, &dEV, &iters, &iters32, &status, &V})
+                      &eps, &hist, &energy, &e_el, &e_rep, &dEV, &iters, &iters32, &status, &V, &hQd, &hQf, &hDd,
+                      &hDf, &hnq})
       b->release();
   }
 };
@@ -329,6 +331,13 @@ cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3
   ENS(P.iters32, sizeof(int) * nn);
   ENS(P.status, sizeof(int) * nn);
   if (ctx->n_cut > 0) ENS(P.V, sizeof(double) * std::max<long long>(mat, 1));
+  if (ctx->n_cut > 0 && precision == FMO_PREC_MIXED) {
+    ENS(P.hQd, sizeof(double) * kHopCols * std::max<long long>(ao, 1));
+    ENS(P.hQf, sizeof(float) * kHopCols * std::max<long long>(ao, 1));
+    ENS(P.hDd, sizeof(double) * kHopCols * kHopCols * nn);
+    ENS(P.hDf, sizeof(float) * kHopCols * kHopCols * nn);
+    ENS(P.hnq, sizeof(int) * nn);
+  }
 #undef ENS
   if ((e = upload(P.d_nm, P.nm, st)) != cudaSuccess) return e;
   if ((e = upload(P.d_order, P.order, st)) != cudaSuccess) return e;
@@ -381,9 +390,14 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
     CK(launch_to_float(st, P.tot_mat, P.S.as<double>(), P.S32.as<float>()));
     CK(launch_to_float(st, P.tot_mat, P.H0.as<double>(), P.H32.as<float>()));
   }
-  if (ctx->n_cut > 0)
+  if (ctx->n_cut > 0) {
+    const bool fac = (precision == FMO_PREC_MIXED);   // mixed: the factors as well
     CK(launch_hop_projector(st, nn, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(), ctx->d_elem.as<int>(),
-                            ctx->d_el.as<DevElem>(), ctx->params.v_hop, P.S.as<double>(), P.V.as<double>()));
+                            ctx->d_el.as<DevElem>(), ctx->params.v_hop, P.S.as<double>(), P.V.as<double>(),
+                            fac ? P.hQd.as<double>() : nullptr, fac ? P.hQf.as<float>() : nullptr,
+                            fac ? P.hDd.as<double>() : nullptr, fac ? P.hDf.as<float>() : nullptr,
+                            fac ? P.hnq.as<int>() : nullptr));
+  }
   CK(launch_gamma(st, nn, P.max_nsh, P.d_nm.as<Nmer>(), ctx->ftab(), ctx->d_xyz.as<double>(),
                   ctx->d_elem.as<int>(), ctx->d_sh_atom.as<int>(), ctx->d_sh_inv_eta.as<double>(), ctx->g,
                   P.gam.as<double>()));
@@ -397,7 +411,9 @@ fmo_status setup_pass(fmo_ctx* ctx, Pass& P, int precision, const SmemPlan& sp, 
     if (use_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
     else CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
   }
-  if (warm_from && use_f) {   // warm start in mixed precision only
+  if (warm_from && use_f && ctx->n_cut == 0) {
+    // warm start in mixed precision only, and only where every n-mer's basis
+    // is its monomers' bases side by side (no healed ghost atoms)
     CK(launch_warm_start(st, nn, P.d_nm.as<Nmer>(), warm_from->d_nm.as<Nmer>(), warm_from->CTf.as<float>(),
                          P.CTf.as<float>()));
   } else {
@@ -427,6 +443,7 @@ void stage(cudaStream_t st, const char* what, int k = -1) {
 // a matrix-vector product over the stored gamma of all shell pairs when it is
 // held, else evaluated pair by pair (use_float: FP32 estimate).
 constexpr size_t kGammaFullMaxBytes = size_t(32) << 30;
+constexpr int kStall32 = 8;   // monomer-loop steps without a 10% gain before FP32 gives up
 
 cudaError_t compute_phi(fmo_ctx* ctx, cudaStream_t st, int use_float) {
   if (ctx->gam_full_ok)
@@ -451,6 +468,10 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.CTf = P.CTf.as<float>(); L.W1f = P.W1f.as<float>(); L.W2f = P.W2f.as<float>(); L.Agf = P.Agf.as<float>();
   L.phi = with_phi ? ctx->d_phi.as<double>() : nullptr;
   L.vhop = ctx->n_cut > 0 ? P.V.as<double>() : nullptr;
+  if (ctx->n_cut > 0 && o.precision == FMO_PREC_MIXED) {
+    L.hop_Qd = P.hQd.as<double>(); L.hop_Qf = P.hQf.as<float>();
+    L.hop_Dd = P.hDd.as<double>(); L.hop_Df = P.hDf.as<float>(); L.hop_nq = P.hnq.as<int>();
+  }
   if (o.precision == FMO_PREC_MIXED) { L.S32 = P.S32.as<float>(); L.H32 = P.H32.as<float>(); }
   L.dq_mono = ctx->d_dq_mono.as<double>();
   L.esp = P.esp.as<double>(); L.dq = P.dq.as<double>(); L.eps = P.eps.as<double>(); L.hist = P.hist.as<double>();
@@ -469,11 +490,13 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.jac_hint = jac_hint;
   // a gradient needs FP64-converged n-mer densities: then the FP32 phase of a
   // mixed-precision n-mer hands over to FP64 iterations run to convergence
-  const bool grad_nmer = o.want_gradient && pass_id >= 1;
+  // (cut bonds, too: an FP32 phase cannot resolve the 1e6 Eh projector to
+  // the accuracy of the FP64 energy finish)
+  const bool grad_nmer = (o.want_gradient || ctx->n_cut > 0) && pass_id >= 1;
   L.fp64_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED && !grad_nmer) ? std::max(0, o.mixed_finish) : 0;
   L.energy_finish = (pass_id >= 1 && o.precision == FMO_PREC_MIXED && o.nmer_finish == FMO_NMER_FINISH_ENERGY &&
                      !grad_nmer);
-  const bool warm_nmer = (pass_id >= 1 && o.precision == FMO_PREC_MIXED);
+  const bool warm_nmer = (pass_id >= 1 && o.precision == FMO_PREC_MIXED && ctx->n_cut == 0);
   L.cold_steps = warm_nmer ? 12 : 2;
   L.first_rot = warm_nmer ? 1 : 0;
   L.first_jac_tol = warm_nmer ? 1e-3 : 0.0;
@@ -1439,8 +1462,6 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
   if (o.want_gradient != 0 && o.want_gradient != 1) return fail(ctx, FMO_ERR_ARG, "want_gradient must be 0 or 1");
   if (o.esp_mode != FMO_ESP_AUTO && o.esp_mode != FMO_ESP_PAIRWISE) return fail(ctx, FMO_ERR_ARG, "unknown esp_mode");
-  if (ctx->n_cut > 0 && o.precision != FMO_PREC_FP64)
-    return fail(ctx, FMO_ERR_UNSUPPORTED, "cut bonds (hybrid orbital projection) need precision FP64");
   cudaSetDevice(ctx->device);
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
   std::memset(&ctx->stats, 0, sizeof(ctx->stats));
@@ -1502,8 +1523,9 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     CK(ctx->d_mix_hist.ensure(sizeof(double) * (2 * kHist + 2) * (size_t)ctx->n_sh));
     CK(ctx->d_mix_state.ensure(mix_state_bytes()));
     CK(cudaMemsetAsync(ctx->d_mix_state.p, 0, mix_state_bytes(), st));
-    int phase = (o.precision == FMO_PREC_MIXED) ? 0 : 1, reortho = 0, n32 = 0;
+    int phase = (o.precision == FMO_PREC_MIXED) ? 0 : 1, reortho = 0, n32 = 0, stall32 = 0;
     const int cap32 = std::max(8, o.max_outer / 2);
+    double min32 = 1e300;
     struct { double e_prev, diff, e1; int have_prev, hcount, hhead, converged, count; } hs{};
     bool graph_ok = (o.schedule == 0);
     for (outer = 1; outer <= o.max_outer; ++outer) {
@@ -1538,7 +1560,12 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       change = hs.converged ? 0.0 : hs.diff;
       if (!(hs.diff == hs.diff)) break;
       if (hs.converged) break;
-      if (phase == 0 && (hs.diff < o.mixed_switch_tol || ++n32 >= cap32)) {
+      // the FP32 phase ends when converged, at its cap, or when it stops
+      // improving (its rounding floor)
+      if (phase == 0) {
+        if (hs.diff < 0.9 * min32) { min32 = hs.diff; stall32 = 0; } else { ++stall32; }
+      }
+      if (phase == 0 && (hs.diff < o.mixed_switch_tol || ++n32 >= cap32 || stall32 >= kStall32)) {
         phase = 1;
         reortho = 1;
         // keep the Broyden history, but form no secant across the hand-over
@@ -1864,6 +1891,7 @@ fmo_status fmo_get_stats(fmo_ctx* ctx, fmo_stats* st) {
 }
 
 static_assert(kMlpWeights == FMO_MLP_N_WEIGHTS, "weight layout of the header");
+static_assert(kMlpTrained == FMO_MLP_N_TRAINED, "trained-weight count of the header");
 
 fmo_status fmo_mlp_init(fmo_ctx* ctx, uint64_t seed) {
   g_ctx = ctx;
@@ -1930,6 +1958,74 @@ fmo_status fmo_mlp_predict(fmo_ctx* ctx, double* shell_dq) {
   CK(d2h(shell_dq, out.p, sizeof(double) * ctx->n_sh, st));
   CK(sync_stream(st));
   out.release();
+  if (err) return fail(ctx, FMO_ERR_UNSUPPORTED, "more than 256 neighbours within 6 A of an atom");
+  return FMO_OK;
+}
+
+fmo_status fmo_mlp_loss_grad(fmo_ctx* ctx, int32_t n_frames, const double* xyz_frames, const double* shell_dq,
+                             double* loss, float* grad) {
+  g_ctx = ctx;
+  if (!ctx || !xyz_frames || !shell_dq || !loss) return FMO_ERR_ARG;
+  if (!ctx->have_system) return fail(ctx, FMO_ERR_STATE, "fmo_set_system first");
+  if (!ctx->mlp_ready) return fail(ctx, FMO_ERR_STATE, "initialise or set the model weights first");
+  if (n_frames < 1) return fail(ctx, FMO_ERR_ARG, "n_frames must be positive");
+  cudaSetDevice(ctx->device);
+  fmo_status fs = mlp_tables(ctx);
+  if (fs != FMO_OK) return fs;
+  cudaStream_t st = ctx->own_stream;
+  const int N = ctx->n_int, B = n_frames, nsh = ctx->n_sh;
+  const size_t rows = (size_t)N * B;
+  const int chunk = 256, n_chunks = int((rows + chunk - 1) / chunk);
+  DevBuf xyzb, tmp, Xb, y, q, gy, tb, x0, z1, h1, z2, h2, gz1, gz2, part, lpart, gbuf;
+  CK(xyzb.ensure(sizeof(double) * 3 * rows));
+  CK(tmp.ensure(sizeof(double) * 3 * (size_t)ctx->n_atoms));
+  CK(tb.ensure(sizeof(float) * rows * 2));
+  std::vector<float> tf(nsh);
+  for (int f = 0; f < B; ++f) {
+    CK(h2d(tmp.p, xyz_frames + (size_t)f * 3 * ctx->n_atoms, sizeof(double) * 3 * ctx->n_atoms, st));
+    CK(launch_gather_xyz(st, N, ctx->d_perm.as<int>(), tmp.as<double>(), xyzb.as<double>() + (size_t)f * 3 * N));
+    for (int k = 0; k < nsh; ++k) tf[k] = float(shell_dq[(size_t)f * nsh + k]);
+    CK(h2d(tb.as<float>() + (size_t)f * nsh, tf.data(), sizeof(float) * nsh, st));
+    CK(sync_stream(st));
+  }
+  CK(Xb.ensure(sizeof(float) * rows * kMlpStride));
+  CK(y.ensure(sizeof(float) * rows * 2));
+  CK(q.ensure(sizeof(float) * rows * 2));
+  CK(gy.ensure(sizeof(float) * rows * 2));
+  CK(x0.ensure(sizeof(float) * rows * kMlpStride));
+  for (DevBuf* b : {&z1, &h1, &z2, &h2, &gz1, &gz2}) CK(b->ensure(sizeof(float) * rows * kMlpHidden));
+  CK(part.ensure(sizeof(float) * (size_t)n_chunks * kMlpTrained));
+  CK(lpart.ensure(sizeof(double) * (size_t)B * ctx->n_frag));
+  CK(gbuf.ensure(sizeof(float) * kMlpTrained));
+  CK(cudaMemsetAsync(ctx->d_mlp_err.p, 0, sizeof(int), st));
+  CK(mlp_descriptors(st, B, N, xyzb.as<double>(), ctx->d_mlp_elem4.as<int>(), Xb.as<float>(), ctx->d_mlp_err.as<int>()));
+  const float* W = ctx->d_mlp_W.as<float>();
+  const __half* W16 = ctx->d_mlp_W16.as<__half>();
+  const MlpCache none{nullptr, nullptr, nullptr, nullptr, nullptr};
+  const MlpCache cache{x0.as<float>(), z1.as<float>(), h1.as<float>(), z2.as<float>(), h2.as<float>()};
+  // the two passes of the training loss (pass-0 potential held fixed)
+  CK(mlp_forward(st, int(rows), Xb.as<float>(), W16, W + kMlpOffMean, W + kMlpOffScale, y.as<float>(), none));
+  CK(mlp_project(st, B, ctx->n_frag, N, ctx->d_f_atom0.as<int>(), ctx->d_f_nat.as<int>(), ctx->d_mlp_fcharge.as<int>(),
+                 y.as<float>(), q.as<float>(), nullptr, 0.0, nullptr, nullptr));
+  CK(mlp_esp(st, B, N, nsh, xyzb.as<double>(), ctx->d_mlp_atom_frag.as<int>(), ctx->d_mlp_atom_ie.as<float>(),
+             ctx->d_sh_atom.as<int>(), ctx->d_mlp_sh_ie.as<float>(), q.as<float>(), Xb.as<float>()));
+  CK(mlp_forward(st, int(rows), Xb.as<float>(), W16, W + kMlpOffMean, W + kMlpOffScale, y.as<float>(), cache));
+  CK(mlp_project(st, B, ctx->n_frag, N, ctx->d_f_atom0.as<int>(), ctx->d_f_nat.as<int>(), ctx->d_mlp_fcharge.as<int>(),
+                 y.as<float>(), q.as<float>(), tb.as<float>(), 1.0 / double(rows * 2), gy.as<float>(),
+                 lpart.as<double>()));
+  CK(mlp_gradient(st, int(rows), gy.as<float>(), W16, cache, gz2.as<float>(), gz1.as<float>(), part.as<float>(), chunk,
+                  gbuf.as<float>()));
+  std::vector<double> lp((size_t)B * ctx->n_frag);
+  int err = 0;
+  CK(d2h(lp.data(), lpart.p, sizeof(double) * lp.size(), st));
+  if (grad) CK(d2h(grad, gbuf.p, sizeof(float) * kMlpTrained, st));
+  CK(d2h(&err, ctx->d_mlp_err.p, sizeof(int), st));
+  CK(sync_stream(st));
+  double ls = 0.0;
+  for (double v : lp) ls += v;
+  *loss = ls / double(rows * 2);
+  for (DevBuf* b : {&xyzb, &tmp, &Xb, &y, &q, &gy, &tb, &x0, &z1, &h1, &z2, &h2, &gz1, &gz2, &part, &lpart, &gbuf})
+    b->release();
   if (err) return fail(ctx, FMO_ERR_UNSUPPORTED, "more than 256 neighbours within 6 A of an atom");
   return FMO_OK;
 }

@@ -57,6 +57,7 @@ struct FragTab {
 
 constexpr int kMaxHealedShells = 32;   // ghost shells of bonds healed in one n-mer
 constexpr int kMaxProjected = 16;      // hybrid-orbital-projected atoms in one n-mer
+constexpr int kHopCols = 4 * kMaxProjected;   // s and p functions of the projected atoms
 
 __device__ __forceinline__ bool frag_in_nmer(int nfrag, const int* frags, int f) {
   for (int k = 0; k < nfrag; ++k)

@@ -251,9 +251,16 @@ __global__ void integrals_kernel(const Nmer* __restrict__ nmers, FragTab ft,
 // outside the n-mer, D = V (1_sp - h h^T) on a ghost, h = c_s s + c_p (b . p)
 // (c_s = 1/2, c_p = sqrt(3)/2), b the unit vector from the BDA to the BAA.
 // One block per n-mer; local AOs in the order of build_maps.
+// With Qd non-null also the factors V = Q^T D Q of the n-mer (idx = its
+// block index): Q rows = the S rows of the projected s/p functions
+// (kHopCols x n per n-mer at offset kHopCols * nm.aov, FP64 in Qd and FP32 in
+// Qf), D = the 4 x 4 blocks on the diagonal (kHopCols^2 per n-mer, FP64 in
+// Dd, FP32 in Df), nq[idx] = the number of rows used (4 per projected atom).
 __global__ void hop_projector_kernel(const Nmer* __restrict__ nmers, FragTab ft, const double* __restrict__ xyz,
                                      const int* __restrict__ elem, const DevElem* __restrict__ el, double v_hop,
-                                     const double* __restrict__ S, double* __restrict__ V) {
+                                     const double* __restrict__ S, double* __restrict__ V,
+                                     double* __restrict__ Qd, float* __restrict__ Qf, double* __restrict__ Dd,
+                                     float* __restrict__ Df, int* __restrict__ nq) {
   const Nmer nm = nmers[blockIdx.x];
   __shared__ int s_np;
   __shared__ int s_idx[kMaxProjected][4];
@@ -300,6 +307,22 @@ __global__ void hop_projector_kernel(const Nmer* __restrict__ nmers, FragTab ft,
   const int n = nm.n, np = s_np;
   const double* Sm = S + nm.mat;
   double* Vm = V + nm.mat;
+  if (Qd) {
+    const long long qo = (long long)kHopCols * nm.aov, dof = (long long)blockIdx.x * kHopCols * kHopCols;
+    for (int e = threadIdx.x; e < 4 * np * n; e += blockDim.x) {
+      const int r = e / n, j = e - r * n;
+      const double v = Sm[(long long)s_idx[r / 4][r % 4] * n + j];
+      Qd[qo + e] = v;
+      Qf[qo + e] = float(v);
+    }
+    for (int e = threadIdx.x; e < kHopCols * kHopCols; e += blockDim.x) {
+      const int r = e / kHopCols, c = e - r * kHopCols;
+      const double v = (r / 4 == c / 4 && r / 4 < np) ? s_D[r / 4][4 * (r % 4) + (c % 4)] : 0.0;
+      Dd[dof + e] = v;
+      Df[dof + e] = float(v);
+    }
+    if (threadIdx.x == 0) nq[blockIdx.x] = 4 * np;
+  }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e - i * n;
     double v = 0.0;
@@ -510,6 +533,13 @@ struct SccArgs {
   float* Agf;
   const double* phi;       // supersystem potential sum_lambda gamma dq_mono (or null)
   const double* vhop;      // per-n-mer hybrid orbital projector V^HOP (n x n, or null)
+  // its factors V = Q^T D Q (hop_projector_kernel; null: not used): mixed
+  // precision keeps the 1e6 Eh projector out of the low-precision products
+  const double* hop_Qd;
+  const float* hop_Qf;
+  const double* hop_Dd;
+  const float* hop_Df;
+  const int* hop_nq;
   const double* dq_mono;   // monomer charges, global shell order
   double* esp;             // out: the n-mer's embedding potential
   double* dq;              // in: guess (if !guess_from_mono), out: charges
@@ -984,7 +1014,9 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   // Fock matrix F = H0 + 1/2 S (sig_mu + sig_nu), into W1 (a warp per row)
   {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const double* Vm = ar.vhop ? ar.vhop + nm.mat : nullptr;   // hybrid orbital projectors, if any
+    // hybrid orbital projectors, if any (with their factors given they are
+    // added in the MO basis after the transform instead)
+    const double* Vm = (ar.vhop && !ar.hop_Qd) ? ar.vhop + nm.mat : nullptr;
     if constexpr (sizeof(T) == 4) {
       // FP32 iteration: built in FP32 from the FP32 copies of H0 and S (the
       // result is rounded to FP32 anyway; no FP64 work per element)
@@ -1035,6 +1067,37 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   } else {
     block_gemm<T>(n, n, n, pp.CT, n, 1, pp.W1, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
     block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, n, 1, pp.A, pp.lda, nullptr, nullptr, nullptr, gemm);
+  }
+  if (ar.hop_Qd) {
+    // A += (CT Q^T) D (CT Q^T)^T: the projector in the MO basis from its
+    // factors, Y = CT Q^T (n x nq, in W1), T = Y D (in W2).  FP32 iterations:
+    // FP32 products (the projected levels, ~1e6 Eh, sit far above the Fermi
+    // level, and the occupied rows have small Y); FP64 iterations: FP64
+    // products.  The Fock matrix above was built without the projector.
+    const int nb = ar.order[blockIdx.x];
+    const int nq = ar.hop_nq[nb];
+    if (nq > 0) {
+      const long long qo = (long long)kHopCols * nm.aov, dof = (long long)nb * kHopCols * kHopCols;
+      T* Y = pp.W1;
+      T* Tq = pp.W2;
+      if constexpr (sizeof(T) == 4) {
+        block_gemm<T>(n, nq, n, pp.CT, n, 1, ar.hop_Qf + qo, n, 1, Y, nq, nullptr, nullptr, nullptr, gemm);
+        block_gemm<T>(n, nq, nq, Y, nq, 1, ar.hop_Df + dof, 1, kHopCols, Tq, nq, nullptr, nullptr, nullptr, gemm);
+      } else {
+        block_gemm<T, double>(n, nq, n, pp.CT, n, 1, ar.hop_Qd + qo, n, 1, Y, nq, nullptr, nullptr, nullptr, gemm);
+        block_gemm<T, double>(n, nq, nq, Y, nq, 1, ar.hop_Dd + dof, 1, kHopCols, Tq, nq, nullptr, nullptr, nullptr,
+                              gemm);
+      }
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int i = wid; i < n; i += nw) {
+        for (int j = lane; j < n; j += 32) {
+          T acc = T(0);
+          for (int c = 0; c < nq; ++c) acc = fma(Tq[(long long)i * nq + c], Y[(long long)j * nq + c], acc);
+          pp.A[(long long)i * pp.lda + j] += acc;
+        }
+      }
+      __syncthreads();
+    }
   }
   mark(1);
   int nocc = 0;
@@ -1315,6 +1378,10 @@ __device__ __forceinline__ double jacobi_threshold(double last, double floor_tol
   return fmax(floor_tol, fmin(1e-4, 1e-3 * last));
 }
 
+// FP32 iterations without a 10% improvement of the best residual before the
+// FP32 phase gives up and hands over to FP64
+constexpr int kStall32 = 8;
+
 __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ar.jac_hint_dev) ar.jac_hint = *ar.jac_hint_dev;
@@ -1483,6 +1550,9 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   int n64 = 0;
   bool fp32_converged = false;
   bool energy_done = false;
+  bool full64 = false;
+  double min32 = 1e300;
+  int stall32 = 0;
   if (!ar.single_step && ar.cold_refine) {
     // the starting rows made S-orthonormal to the working precision
     if (phase == 0) reorthonormalise<float>(nm, ar, sm, pf, ar.cold_steps, 1e-6);
@@ -1514,7 +1584,14 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       ar.trace[1024 + it] = double(t1 - t_it);
       t_it = t1;
     }
-    if (phase == 1 && ar.precision == 1 && ar.fp64_finish > 0 && ++n64 >= ar.fp64_finish) {
+    // FP32 phase: converged, or no longer improving (FP32 rounding floor, e.g.
+    // the 1e6 Eh hybrid-orbital projector) or at its cap -> FP64
+    if (phase == 0) {
+      if (diff < 0.9 * min32) { min32 = diff; stall32 = 0; } else { ++stall32; }
+    }
+    const bool fp32_done = phase == 0 && diff < ar.switch_tol;
+    const bool fp32_give_up = phase == 0 && !fp32_done && (it32 >= ar.fp32_cap || stall32 >= kStall32);
+    if (phase == 1 && ar.precision == 1 && ar.fp64_finish > 0 && !full64 && ++n64 >= ar.fp64_finish) {
       // FP64 energy of the FP32-converged charges (variational for n-mers
       // in a fixed ESP); the loop ends here
       status = fp32_converged ? FMO_SCC_CONVERGED_CODE : FMO_SCC_MAX_ITER_CODE;
@@ -1524,7 +1601,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     // loop decisions are made block-uniform with barrier votes (thread 0's
     // timer read decides the deadline)
     if (__syncthreads_or(!isfinite(e_el) || !isfinite(diff))) { status = FMO_SCC_NAN_CODE; break; }
-    if (ar.energy_finish && __syncthreads_and(phase == 0 && (diff < ar.switch_tol || it32 >= ar.fp32_cap))) {
+    if (ar.energy_finish && __syncthreads_and(fp32_done)) {
       // n-mer in mixed precision: FP64 energy of the FP32-converged density
       const long long tf = clock64();
       if (ct_smem) {
@@ -1532,7 +1609,7 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
         __syncthreads();
       }
       e_el = fp64_energy_of_rows(nm, ar, sm, pd, ctf_g, pf.W1, pf.W2);
-      status = diff < ar.switch_tol ? FMO_SCC_CONVERGED_CODE : FMO_SCC_MAX_ITER_CODE;
+      status = FMO_SCC_CONVERGED_CODE;
       if (__syncthreads_or(!isfinite(e_el))) status = FMO_SCC_NAN_CODE;
       if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0) ar.trace[1535] = double(clock64() - tf);
       energy_done = true;
@@ -1550,7 +1627,9 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     }
     broyden_step(nsh, it, hist, sm, hcount, hhead, 0.4, 0.01, !fresh64);
     fresh64 = false;
-    if (__syncthreads_and(phase == 0 && (diff < ar.switch_tol || it32 >= ar.fp32_cap))) {
+    if (__syncthreads_and(fp32_done || fp32_give_up)) {
+      // an FP32 phase that gave up converges fully in FP64
+      full64 = fp32_give_up;
       for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) pd.CT[e] = double(pf.CT[e]);
       __syncthreads();
       if (ct_smem) {
@@ -2104,7 +2183,8 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.atom_sh0 = L.atom_sh0; ar.el = L.el; ar.g = L.g; ar.S = L.S; ar.H0 = L.H0; ar.gam = L.gam;
   ar.CTd = L.CTd; ar.W1d = L.W1d; ar.W2d = L.W2d; ar.Agd = L.Agd;
   ar.CTf = L.CTf; ar.W1f = L.W1f; ar.W2f = L.W2f; ar.Agf = L.Agf;
-  ar.phi = L.phi; ar.vhop = L.vhop; ar.dq_mono = L.dq_mono; ar.esp = L.esp; ar.dq = L.dq; ar.eps = L.eps; ar.hist = L.hist;
+  ar.phi = L.phi; ar.vhop = L.vhop; ar.dq_mono = L.dq_mono;
+  ar.hop_Qd = L.hop_Qd; ar.hop_Qf = L.hop_Qf; ar.hop_Dd = L.hop_Dd; ar.hop_Df = L.hop_Df; ar.hop_nq = L.hop_nq; ar.esp = L.esp; ar.dq = L.dq; ar.eps = L.eps; ar.hist = L.hist;
   ar.energy = L.energy; ar.e_el = L.e_el; ar.e_rep = L.e_rep; ar.dEV = L.dEV; ar.iters = L.iters; ar.iters32 = L.iters32;
   ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
@@ -2170,9 +2250,10 @@ cudaError_t launch_phi_gemv(cudaStream_t st, int n_sh, const double* gam, const 
 }
 
 cudaError_t launch_hop_projector(cudaStream_t st, int n_nmer, const Nmer* nmers, FragTab ft, const double* xyz,
-                                 const int* elem, const DevElem* el, double v_hop, const double* S, double* V) {
+                                 const int* elem, const DevElem* el, double v_hop, const double* S, double* V,
+                                 double* Qd, float* Qf, double* Dd, float* Df, int* nq) {
   if (n_nmer == 0) return cudaSuccess;
-  hop_projector_kernel<<<n_nmer, 256, 0, st>>>(nmers, ft, xyz, elem, el, v_hop, S, V);
+  hop_projector_kernel<<<n_nmer, 256, 0, st>>>(nmers, ft, xyz, elem, el, v_hop, S, V, Qd, Qf, Dd, Df, nq);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

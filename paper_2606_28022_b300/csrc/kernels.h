@@ -49,6 +49,11 @@ struct SccLaunch {
   float* Agf;
   const double* phi;
   const double* vhop;   // per-n-mer hybrid orbital projectors (null without cut bonds)
+  const double* hop_Qd; // their factors (hop_projector_kernel), or null
+  const float* hop_Qf;
+  const double* hop_Dd;
+  const float* hop_Df;
+  const int* hop_nq;
   const double* dq_mono;
   double* esp;
   double* dq;
@@ -111,8 +116,13 @@ cudaError_t launch_phi(cudaStream_t st, int n_sh, const double* xyz, const int* 
 cudaError_t launch_gamma_full(cudaStream_t st, int n_sh, const double* xyz, const int* sh_atom,
                               const double* sh_inv_eta, GParams g, double* gam);
 cudaError_t launch_phi_gemv(cudaStream_t st, int n_sh, const double* gam, const double* dq, double* phi);
+// V^HOP (n x n per n-mer) and, with Qd non-null, its factors V = Q^T D Q:
+// Qd/Qf kHopCols x n per n-mer at kHopCols * nm.aov, Dd/Df kHopCols^2 per
+// n-mer, nq[n-mer] rows used
 cudaError_t launch_hop_projector(cudaStream_t st, int n_nmer, const Nmer* nmers, FragTab ft, const double* xyz,
-                                 const int* elem, const DevElem* el, double v_hop, const double* S, double* V);
+                                 const int* elem, const DevElem* el, double v_hop, const double* S, double* V,
+                                 double* Qd = nullptr, float* Qf = nullptr, double* Dd = nullptr, float* Df = nullptr,
+                                 int* nq = nullptr);
 cudaError_t launch_loop_control(cudaStream_t st, unsigned long long handle, const void* mix_state, int* outer,
                                 int max_outer);
 cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);

@@ -393,6 +393,15 @@ __global__ void mlp_adam_kernel(int n_chunks, const float* __restrict__ partial,
   W16[w] = __float2half_rn(nw);
 }
 
+// Sum of the chunk partials in chunk order: the gradient of the batch loss.
+__global__ void mlp_grad_sum_kernel(int n_chunks, const float* __restrict__ partial, float* __restrict__ grad) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= kMlpTrained) return;
+  float g = 0.0f;
+  for (int c = 0; c < n_chunks; ++c) g += partial[(size_t)c * kMlpTrained + w];
+  grad[w] = g;
+}
+
 __global__ void mlp_to_half_kernel(int n, const float* __restrict__ W, __half* __restrict__ W16) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w < n) W16[w] = __float2half_rn(W[w]);
@@ -505,6 +514,19 @@ cudaError_t mlp_backward_step(cudaStream_t st, int n, const float* gy, const __h
   MLP_CHECK();
   const float bc1 = 1.0f - powf(0.9f, float(t)), bc2 = 1.0f - powf(0.999f, float(t));
   mlp_adam_kernel<<<(kMlpTrained + 255) / 256, 256, 0, st>>>(n_chunks, partial, W, m, v, W16out, lr, bc1, bc2);
+  MLP_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t mlp_gradient(cudaStream_t st, int n, const float* gy, const __half* W16, const MlpCache& cache,
+                         float* gz2, float* gz1, float* partial, int chunk, float* grad) {
+  const int blocks = std::min((n + 31) / 32, 148 * 8);
+  mlp_backprop_kernel<<<blocks, 128, 0, st>>>(n, gy, W16, cache, gz2, gz1);
+  MLP_CHECK();
+  const int n_chunks = (n + chunk - 1) / chunk;
+  mlp_wgrad_kernel<<<n_chunks, 256, 0, st>>>(n, chunk, gy, gz2, gz1, cache, partial);
+  MLP_CHECK();
+  mlp_grad_sum_kernel<<<(kMlpTrained + 255) / 256, 256, 0, st>>>(n_chunks, partial, grad);
   MLP_CHECK();
   return cudaSuccess;
 }

@@ -48,6 +48,10 @@ cudaError_t mlp_project(cudaStream_t st, int n_frames, int n_frag, int n_atoms, 
 cudaError_t mlp_backward_step(cudaStream_t st, int n, const float* gy, const __half* W16, const MlpCache& cache,
                               float* gz2, float* gz1, float* partial, int chunk, float* W, float* m, float* v,
                               __half* W16out, float lr, int t);
+// backward pass and the weight gradient of the batch loss (no update):
+// grad[kMlpTrained] in the flat weight layout
+cudaError_t mlp_gradient(cudaStream_t st, int n, const float* gy, const __half* W16, const MlpCache& cache,
+                         float* gz2, float* gz1, float* partial, int chunk, float* grad);
 cudaError_t mlp_to_half(cudaStream_t st, int n, const float* W, __half* W16);
 cudaError_t mlp_feature_stats(cudaStream_t st, long long n, const float* X, float* mean, float* scale);
 cudaError_t mlp_to_double(cudaStream_t st, int n, const float* q, double* out);

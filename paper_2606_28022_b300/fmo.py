@@ -27,8 +27,10 @@ SYMBOLS = ["fmo_options_default", "fmo_create", "fmo_set_system", "fmo_set_coord
            "fmo_set_coordinates_device", "fmo_set_guess", "fmo_run", "fmo_get_energy",
            "fmo_get_sizes", "fmo_get_monomers", "fmo_get_dimers", "fmo_get_trimers", "fmo_get_gradient",
            "fmo_get_stats", "fmo_last_error", "fmo_destroy", "fmo_mlp_init", "fmo_mlp_set_weights",
-           "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train", "fmo_scc_solve_noalloc", "fmo_fma_peak"]
+           "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train", "fmo_scc_solve_noalloc", "fmo_fma_peak",
+           "fmo_mlp_loss_grad"]
 MLP_N_WEIGHTS = 26908
+MLP_N_TRAINED = 26754
 
 
 class FmoElement(C.Structure):
@@ -119,6 +121,7 @@ def load_library(path: str | None = None):
     lib.fmo_mlp_get_weights.argtypes = [vp, fp, C.POINTER(i64)]
     lib.fmo_mlp_predict.argtypes = [vp, dp]
     lib.fmo_mlp_train.argtypes = [vp, i32, dp, dp, i32, i32, C.c_double, C.c_uint64, dp]
+    lib.fmo_mlp_loss_grad.argtypes = [vp, i32, dp, dp, dp, fp]
     lib.fmo_fma_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
     lib.fmo_scc_solve_noalloc.argtypes = [vp, i32, ip, vp, i32, vp, vp, vp, vp, vp, vp, C.c_char_p, i32]
     lib.fmo_last_error.argtypes = [vp]
@@ -365,6 +368,17 @@ class FMO:
         self._check(self.lib.fmo_mlp_train(self.h, len(x), _dp(x.reshape(-1)), _dp(q.reshape(-1)), epochs,
                                            batch_frames, lr, seed, _dp(loss)))
         return loss
+
+    def mlp_loss_grad(self, xyz_frames: np.ndarray, shell_dq: np.ndarray):
+        """(loss, gradient in the flat layout of the trained weights) of the
+        current model on the frames, no update (fmo_mlp_loss_grad)."""
+        x = np.ascontiguousarray(xyz_frames, dtype=np.float64)
+        q = np.ascontiguousarray(shell_dq, dtype=np.float64)
+        loss = C.c_double(0.0)
+        g = np.zeros(MLP_N_TRAINED, dtype=np.float32)
+        self._check(self.lib.fmo_mlp_loss_grad(self.h, len(x), _dp(x.reshape(-1)), _dp(q.reshape(-1)), C.byref(loss),
+                                               g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
 
     def stats(self) -> dict:
         s = FmoStats()

@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
 same seeded inputs.  Tolerances: 1e-8 Eh per fragment energy and 1e-7 Eh for
-FMO totals in the FP64 path, 1e-6 Eh for the totals of the mixed path."""
+FMO totals in the FP64 path; 1e-6 Eh for the totals and 1e-7 Eh per dimer and
+trimer interaction energy in the mixed path."""
 import numpy as np
 import pytest
 
@@ -14,6 +15,7 @@ pytestmark = pytest.mark.gpu
 E_FRAG = 1e-8
 E_TOT = 1e-7
 E_TOT_MIXED = 1e-6
+E_NMER_MIXED = 1e-7   # per dimer / trimer energy, mixed path
 DQ = 1e-7
 
 
@@ -111,6 +113,8 @@ def test_anthracene4_fmo2_mixed(gpu, params, anthracene4):
     e1, e2, _ = g.energies()
     assert abs(e2 - ref.e_fmo2) < E_TOT_MIXED
     assert abs(e1 - ref.e_fmo1) < E_TOT_MIXED
+    d = g.dimers()
+    assert np.max(np.abs(d.dE - ref.dE_dimer)) < E_NMER_MIXED             # every dimer on its own
 
 
 def test_water8_mixed(gpu, params, water64):
@@ -178,6 +182,11 @@ def test_pentacene4_fmo3_fp64_and_mixed(gpu, params, pentacene4):
     e1, e2, e3 = g.energies()
     assert abs(e3 - ref.e_fmo3) < E_TOT_MIXED
     assert abs(e2 - ref.e_fmo2) < E_TOT_MIXED
+    assert np.max(np.abs(g.dimers().dE - ref.dE_dimer)) < E_NMER_MIXED
+    t = g.trimers()
+    assert np.array_equal(t.ijk, ref.trimers)
+    assert np.max(np.abs(t.dE3 - ref.dE_trimer)) < E_NMER_MIXED
+    assert np.max(np.abs(t.corr - ref.corr_trimer)) < E_NMER_MIXED
 
 
 @pytest.fixture(scope="module")
@@ -200,11 +209,23 @@ def test_polyalanine_hop_fmo3_of_three_fragments_equals_full_scc(gpu, params):
     assert abs(g.energies()[2] - full.energy) < E_TOT
 
 
-def test_hop_needs_fp64(gpu, params):
-    from paper_2606_28022_b300 import fmo
-    gpu.set_system(G.polyalanine_helix(3))
-    with pytest.raises(fmo.FMOError):
-        gpu.run(fmo.options(precision="mixed"))
+def test_polyalanine_hop_fmo2_mixed(gpu, params, ala5):
+    # mixed precision with cut bonds: the 1e6 Eh projector stays out of the
+    # FP32 products (added in the MO basis from its factors)
+    ref = ofmo.fmo(ala5, params, ofmo.FMOOptions(all_dimers_scc=True))
+    g = run_gpu(gpu, ala5, all_dimers_scc=1, precision="mixed")
+    e1, e2, _ = g.energies()
+    assert abs(e2 - ref.e_fmo2) < E_TOT_MIXED
+    assert abs(e1 - ref.e_fmo1) < E_TOT_MIXED
+    assert np.max(np.abs(g.dimers().dE - ref.dE_dimer)) < E_NMER_MIXED
+    assert (g.monomers().status == 0).all()
+
+
+def test_polyalanine_hop_fmo3_three_fragments_mixed_equals_full_scc(gpu, params):
+    s = G.polyalanine_helix(3)
+    full = xtb.single_point(s, params)
+    g = run_gpu(gpu, s, level=3, all_dimers_scc=1, trimer_cut=1e9, precision="mixed")
+    assert abs(g.energies()[2] - full.energy) < E_TOT_MIXED
 
 
 def test_graph_driven_and_host_driven_monomer_loops_agree(gpu, params, water64):
