@@ -44,7 +44,8 @@ typedef enum {
   FMO_ERR_TIMEOUT = 5,       /* deadline passed; kernels stopped early */
   FMO_ERR_NAN = 6,           /* non-finite value in a result */
   FMO_ERR_STATE = 7,         /* call out of order (e.g. run before set_system) */
-  FMO_ERR_UNSUPPORTED = 8    /* feature or size not supported */
+  FMO_ERR_UNSUPPORTED = 8,   /* feature or size not supported */
+  FMO_ERR_EXCHANGE = 9       /* the exchange callback of a sharded run failed */
 } fmo_status;
 
 /* Per-n-mer status words written by the SCC kernel. */
@@ -155,7 +156,30 @@ typedef struct fmo_options {
                                of the free memory) and forms phi as a matrix-
                                vector product; FMO_ESP_PAIRWISE evaluates gamma
                                pair by pair every step (no n_sh^2 buffer). */
+  int32_t shard_rank;       /* sharded run over shard_world processes (one per
+                               GPU; Sec. 2.3 and Eqs. 12 and 16 make the
+                               monomer steps, dimers and trimers independent
+                               given the monomer charges): this process solves
+                               the n-mers that fmo_lpt_partition (cost n^3)
+                               gives shard_rank in each pass, and every monomer
+                               step, pass and result is summed over the ranks
+                               through the callback of fmo_set_exchange.
+                               Results are those of the unsharded run, bit for
+                               bit, on every rank. */
+  int32_t shard_world;      /* number of ranks; 0 or 1 = not sharded.  Sharded
+                               runs need the global monomer loop and
+                               want_gradient = 0, and run the monomer loop
+                               host-driven (schedule 1). */
 } fmo_options;
+
+/* Element-wise sum over the ranks of a sharded run: replace buf[0 .. n) by
+ * the sum of every rank's buf.  fmo_run calls it on every rank with the same
+ * n, in the same order (once per monomer-loop step and once after each
+ * pass); each entry is non-zero on the rank that owns it only, so the sum is
+ * exact.  Return 0 on success; anything else ends fmo_run with
+ * FMO_ERR_EXCHANGE.  A torch.distributed all_reduce (gloo, CPU tensor) is
+ * one such callback.  The paper has no counterpart (its runs use one GPU). */
+typedef int32_t (*fmo_exchange_fn)(void *user, double *buf, int64_t n);
 
 /* Counters of the last fmo_run. */
 typedef struct fmo_stats {
@@ -186,6 +210,19 @@ typedef struct fmo_stats {
 } fmo_stats;
 
 typedef struct fmo_ctx fmo_ctx;
+
+/* Install the exchange callback of sharded runs (fn = NULL removes it);
+ * user is passed back unchanged.  Errors: FMO_ERR_ARG (ctx NULL). */
+fmo_status fmo_set_exchange(fmo_ctx *ctx, fmo_exchange_fn fn, void *user);
+
+/* Longest-processing-time-first partition of n work units over world ranks
+ * (host only, needs no GPU): units in order of decreasing cost[i] (ties: lower
+ * i first) each go to the rank with the least assigned cost so far (ties:
+ * lower rank); owner[i] receives the rank.  The makespan is within 4/3 of the
+ * optimum (Graham, 1969).  fmo_run shards every pass with it (cost n^3 of the
+ * n-mer's basis size).  Errors: FMO_ERR_ARG (NULL with n > 0, n < 0,
+ * world < 1, a cost that is negative or not finite). */
+fmo_status fmo_lpt_partition(const double *cost, int64_t n, int32_t world, int32_t *owner);
 
 /* Fill *o with the defaults: level 2, FP64, ES-DIM on, cut 4.0 A, tolerances
  * 1e-10, max_iter 300, max_outer 200, switch 1e-5, one FP64 finishing

@@ -52,6 +52,7 @@ struct Pass {
   DevBuf hQd, hQf, hDd, hDf, hnq;         // their factors V = Q^T D Q (mixed precision)
   int max_healed_sh = 0, max_projected = 0;
   std::vector<int> h_iters, h_iters32;
+  std::vector<int> owner;                 // sharded runs: rank of every n-mer (empty: all here)
   void release() {
     for (DevBuf* b : {&d_nm, &d_order, &S, &H0, &gam, &CTd, &W1d, &W2d, &Agd, &CTf, &W1f, &W2f, &Agf, &esp, &dq,
                       &eps, &hist, &energy, &e_el, &e_rep, &dEV, &iters, &iters32, &status, &V, &hQd, &hQf, &hDd,
@@ -95,6 +96,10 @@ struct Staging {
 
 struct fmo_ctx {
   int device = 0;
+  // sharded runs: this rank, the number of ranks and the exchange callback
+  int shard_rank = 0, shard_world = 1;
+  fmo_exchange_fn ex_fn = nullptr;
+  void* ex_user = nullptr;
   cudaStream_t own_stream = nullptr;
   std::string err;
   fmo_params params;
@@ -249,6 +254,24 @@ int elem_nao(const DevElem& e) {
   return n;
 }
 
+// Longest-processing-time-first partition: units by decreasing cost (ties:
+// lower index), each to the least loaded rank (ties: lower rank).
+std::vector<int> lpt_owner(const std::vector<double>& cost, int world) {
+  const size_t n = cost.size();
+  std::vector<int> idx(n), owner(n, 0);
+  for (size_t i = 0; i < n; ++i) idx[i] = int(i);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> load(std::max(world, 1), 0.0);
+  for (int i : idx) {
+    int r = 0;
+    for (int q = 1; q < world; ++q)
+      if (load[q] < load[r]) r = q;
+    owner[i] = r;
+    load[r] += cost[i];
+  }
+  return owner;
+}
+
 // Lay out a pass of n-mers (tuples of fragments) and size its buffers.
 cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3>>& tuples,
                       const std::vector<int>& nf, bool monomer_layout, int precision, cudaStream_t st) {
@@ -339,9 +362,83 @@ cudaError_t plan_pass(fmo_ctx* ctx, Pass& P, const std::vector<std::array<int, 3
     ENS(P.hnq, sizeof(int) * nn);
   }
 #undef ENS
+  P.owner.clear();
+  if (ctx->shard_world > 1 && !P.nm.empty()) {
+    // this rank launches its own n-mers only (LPT partition by n^3), in the
+    // pass's largest-first order
+    std::vector<double> cost(P.nm.size());
+    for (size_t i = 0; i < P.nm.size(); ++i) cost[i] = double(P.nm[i].n) * P.nm[i].n * P.nm[i].n;
+    P.owner = lpt_owner(cost, ctx->shard_world);
+    std::vector<int> mine;
+    for (int i : P.order)
+      if (P.owner[i] == ctx->shard_rank) mine.push_back(i);
+    P.order.swap(mine);
+  }
   if ((e = upload(P.d_nm, P.nm, st)) != cudaSuccess) return e;
   if ((e = upload(P.d_order, P.order, st)) != cudaSuccess) return e;
   return cudaSuccess;
+}
+
+// Entries of a device array that a sharded run sums over its ranks: entry e
+// belongs to n-mer item_of(e); other ranks' entries are zeroed before the sum.
+struct ExPart {
+  void* dev;
+  int type;        // 0 double, 1 int, 2 float
+  long long n;
+  std::vector<int> item;   // n-mer of every entry
+};
+
+// ExPart for per-n-mer arrays (one entry per n-mer)
+ExPart ex_per_nmer(DevBuf& b, int type, size_t nn) {
+  ExPart x{b.p, type, (long long)nn, std::vector<int>(nn)};
+  for (size_t i = 0; i < nn; ++i) x.item[i] = int(i);
+  return x;
+}
+
+// Sum of the parts over the ranks, in place, through the exchange callback.
+fmo_status shard_exchange(fmo_ctx* ctx, const Pass& P, std::vector<ExPart>& parts, cudaStream_t st) {
+  long long total = 0;
+  for (auto& x : parts) total += x.n;
+  std::vector<double> buf(std::max<long long>(total, 1), 0.0);
+  std::vector<std::vector<char>> raw(parts.size());
+  const size_t esz[3] = {sizeof(double), sizeof(int), sizeof(float)};
+  for (size_t k = 0; k < parts.size(); ++k) {
+    raw[k].resize(std::max<size_t>(esz[parts[k].type] * parts[k].n, 1));
+    if (parts[k].n) CK(d2h(raw[k].data(), parts[k].dev, esz[parts[k].type] * parts[k].n, st));
+  }
+  CK(sync_stream(st));
+  long long o = 0;
+  for (size_t k = 0; k < parts.size(); ++k) {
+    const ExPart& x = parts[k];
+    for (long long e = 0; e < x.n; ++e, ++o) {
+      if (P.owner[x.item[e]] != ctx->shard_rank) continue;
+      if (x.type == 0) buf[o] = reinterpret_cast<const double*>(raw[k].data())[e];
+      else if (x.type == 1) buf[o] = double(reinterpret_cast<const int*>(raw[k].data())[e]);
+      else buf[o] = double(reinterpret_cast<const float*>(raw[k].data())[e]);
+    }
+  }
+  if (ctx->ex_fn(ctx->ex_user, buf.data(), total) != 0) return fail(ctx, FMO_ERR_EXCHANGE, "exchange callback failed");
+  o = 0;
+  for (size_t k = 0; k < parts.size(); ++k) {
+    const ExPart& x = parts[k];
+    for (long long e = 0; e < x.n; ++e, ++o) {
+      if (x.type == 0) reinterpret_cast<double*>(raw[k].data())[e] = buf[o];
+      else if (x.type == 1) reinterpret_cast<int*>(raw[k].data())[e] = int(buf[o]);
+      else reinterpret_cast<float*>(raw[k].data())[e] = float(buf[o]);
+    }
+    if (x.n) CK(h2d(x.dev, raw[k].data(), esz[x.type] * x.n, st));
+  }
+  CK(sync_stream(st));
+  return FMO_OK;
+}
+
+// The results of a dimer or trimer pass on every rank of a sharded run.
+fmo_status shard_exchange_pass(fmo_ctx* ctx, Pass& P, cudaStream_t st) {
+  const size_t nn = P.nm.size();
+  if (ctx->shard_world <= 1 || nn == 0) return FMO_OK;
+  std::vector<ExPart> parts{ex_per_nmer(P.energy, 0, nn), ex_per_nmer(P.dEV, 0, nn), ex_per_nmer(P.iters, 1, nn),
+                            ex_per_nmer(P.status, 1, nn)};
+  return shard_exchange(ctx, P, parts, st);
 }
 
 struct SmemPlan {
@@ -532,7 +629,7 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  CK(launch_scc(st, nn, L));
+  CK(launch_scc(st, int(P.order.size()), L));
   cudaEventRecord(e1, st);
   // iteration counts of this launch -> algorithmic flops of the pass
   P.h_iters.resize(nn);
@@ -572,7 +669,7 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
             sb < (int)P.order.size() ? P.nm[P.order[sb]].n : -1, double(slow >> 20) * 1e-6, njac);
   }
   ctx->stats.scc_launches[pass_id] += 1;
-  for (int i = 0; i < nn; ++i) {
+  for (int i : P.order) {
     const double n3 = 15.0 * double(P.nm[i].n) * P.nm[i].n * P.nm[i].n;
     const int i32 = P.h_iters32[i], i64 = P.h_iters[i] - P.h_iters32[i];
     ctx->stats.iters_fp32[pass_id] += i32;
@@ -1152,6 +1249,8 @@ void fmo_options_default(fmo_options* o) {
   o->mixed_switch_tol = 1e-5;
   o->mixed_finish = 1;
   o->deadline_s = 0.0;
+  o->shard_rank = 0;
+  o->shard_world = 1;
 }
 
 fmo_status fmo_create(fmo_ctx** out, const fmo_params* p, int device) {
@@ -1462,6 +1561,16 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
   if (o.want_gradient != 0 && o.want_gradient != 1) return fail(ctx, FMO_ERR_ARG, "want_gradient must be 0 or 1");
   if (o.esp_mode != FMO_ESP_AUTO && o.esp_mode != FMO_ESP_PAIRWISE) return fail(ctx, FMO_ERR_ARG, "unknown esp_mode");
+  const int world = o.shard_world <= 1 ? 1 : o.shard_world;
+  if (o.shard_world < 0 || o.shard_rank < 0 || o.shard_rank >= world)
+    return fail(ctx, FMO_ERR_ARG, "shard_rank must lie in [0, shard_world)");
+  if (world > 1) {
+    if (!ctx->ex_fn) return fail(ctx, FMO_ERR_STATE, "a sharded run needs fmo_set_exchange");
+    if (o.monomer_loop != FMO_LOOP_GLOBAL) return fail(ctx, FMO_ERR_UNSUPPORTED, "sharded runs use the global monomer loop");
+    if (o.want_gradient) return fail(ctx, FMO_ERR_UNSUPPORTED, "sharded runs keep no gradient data");
+  }
+  ctx->shard_rank = world > 1 ? o.shard_rank : 0;
+  ctx->shard_world = world;
   cudaSetDevice(ctx->device);
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
   std::memset(&ctx->stats, 0, sizeof(ctx->stats));
@@ -1527,7 +1636,16 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     const int cap32 = std::max(8, o.max_outer / 2);
     double min32 = 1e300;
     struct { double e_prev, diff, e1; int have_prev, hcount, hhead, converged, count; } hs{};
-    bool graph_ok = (o.schedule == 0);
+    bool graph_ok = (o.schedule == 0) && world == 1;
+    // sharded: the output charges and energies of every step from all ranks
+    std::vector<ExPart> step_parts;
+    if (world > 1) {
+      ExPart q{ctx->mono.dq.p, 0, (long long)ctx->n_sh, std::vector<int>(ctx->n_sh, 0)};
+      for (int f = 0; f < nf; ++f)
+        for (int k = 0; k < ctx->mono.nm[f].nsh; ++k) q.item[ctx->mono.nm[f].shv + k] = f;
+      step_parts.push_back(std::move(q));
+      step_parts.push_back(ex_per_nmer(ctx->mono.energy, 0, nf));
+    }
     for (outer = 1; outer <= o.max_outer; ++outer) {
       if (graph_ok && phase == 1 && reortho == 0 && outer > 1 && outer < o.max_outer) {
         // the remaining FP64 steps run device-driven inside one CUDA graph
@@ -1548,6 +1666,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       fs = run_scc(ctx, ctx->mono, o, sp_mono, true, 0, st, 1, phase, reortho, outer == 1 ? 1 : 0,
                    (phase == 0 && outer > 1 && outer % 4 == 0) ? 1 : 0, outer == 1 ? 1.0 : hs.diff);
       if (fs != FMO_OK) return fs;
+      if (world > 1 && (fs = shard_exchange(ctx, ctx->mono, step_parts, st)) != FMO_OK) return fs;
       reortho = 0;
       CK(launch_global_mix(st, ctx->n_sh, ctx->d_dq_mono.as<double>(), ctx->mono.dq.as<double>(), nf,
                            ctx->mono.energy.as<double>(), ctx->d_mix_hist.as<double>(), ctx->d_mix_state.p,
@@ -1575,6 +1694,20 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       }
     }
     ctx->stats.n_monomer_solves = nf;
+    if (world > 1) {
+      // every rank: all monomer results, and the final FP32 rows that start
+      // the mixed-precision dimers and trimers
+      std::vector<ExPart> parts{ex_per_nmer(ctx->mono.iters, 1, nf), ex_per_nmer(ctx->mono.status, 1, nf)};
+      if (o.precision == FMO_PREC_MIXED && ctx->n_cut == 0) {
+        ExPart c{ctx->mono.CTf.p, 2, ctx->mono.tot_mat, std::vector<int>(ctx->mono.tot_mat, 0)};
+        for (int f = 0; f < nf; ++f) {
+          const long long n2 = (long long)ctx->mono.nm[f].n * ctx->mono.nm[f].n;
+          for (long long e = 0; e < n2; ++e) c.item[ctx->mono.nm[f].mat + e] = f;
+        }
+        parts.push_back(std::move(c));
+      }
+      if ((fs = shard_exchange(ctx, ctx->mono, parts, st)) != FMO_OK) return fs;
+    }
   } else {
   for (outer = 1; outer <= o.max_outer; ++outer) {
     CK(compute_phi(ctx, st, 0));
@@ -1670,6 +1803,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     stage(st, "dimer setup");
     fs = run_scc(ctx, ctx->dim, o, sp_dim, true, 1, st);
     if (fs != FMO_OK) return fs;
+    if ((fs = shard_exchange_pass(ctx, ctx->dim, st)) != FMO_OK) return fs;
     stage(st, "dimer scc");
   }
   // ---- ES-DIM pairs (Eq. 15)
@@ -1696,6 +1830,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     if (fs != FMO_OK) return fs;
     fs = run_scc(ctx, ctx->tri, o, sp_tri, true, 2, st);
     if (fs != FMO_OK) return fs;
+    if ((fs = shard_exchange_pass(ctx, ctx->tri, st)) != FMO_OK) return fs;
   }
   std::vector<int> tri_flat;
   for (auto& t : tri_tu) { tri_flat.push_back(t[0]); tri_flat.push_back(t[1]); tri_flat.push_back(t[2]); }
@@ -1773,7 +1908,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   for (size_t t = 0; t < ntri; ++t) if (st_tri[t] != FMO_SCC_CONVERGED) ++failed;
   ctx->r_tri = tri_flat;
   ctx->r_pair_k.assign(pair_scc.begin(), pair_scc.begin() + std::max<long long>(npair, 0));
-  ctx->grad_ready = (o.precision == FMO_PREC_FP64) || o.want_gradient;
+  ctx->grad_ready = ((o.precision == FMO_PREC_FP64) || o.want_gradient) && world == 1;
   ctx->last_cuts_ok = true;
   for (auto& t : tri_tu) {
     const long long nf_ = nf;
@@ -1803,6 +1938,23 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   if (failed > 0 || change >= o.outer_tol)
     return fail(ctx, FMO_ERR_NOT_CONVERGED, std::to_string(failed) + " n-mer solves did not converge");
   ctx->err.clear();
+  return FMO_OK;
+}
+
+fmo_status fmo_set_exchange(fmo_ctx* ctx, fmo_exchange_fn fn, void* user) {
+  if (!ctx) return FMO_ERR_ARG;
+  ctx->ex_fn = fn;
+  ctx->ex_user = user;
+  return FMO_OK;
+}
+
+fmo_status fmo_lpt_partition(const double* cost, int64_t n, int32_t world, int32_t* owner) {
+  if (n < 0 || world < 1 || (n > 0 && (!cost || !owner))) return FMO_ERR_ARG;
+  std::vector<double> c(cost, cost + n);
+  for (double x : c)
+    if (!(x >= 0.0) || !std::isfinite(x)) return FMO_ERR_ARG;
+  const std::vector<int> o = lpt_owner(c, world);
+  for (int64_t i = 0; i < n; ++i) owner[i] = o[i];
   return FMO_OK;
 }
 

@@ -13,6 +13,7 @@
 
 #include "fmo_device.cuh"
 #include "kernels.h"
+#include "tridiag.cuh"
 
 namespace fmo {
 
@@ -577,6 +578,9 @@ struct SccArgs {
   unsigned long long budget_ns;
   int a_smem_d, a_smem_f;
   int max_n, max_nsh, max_nat;
+  // > 0: shared-memory floats for packed rows of the tridiagonal eigen-solver
+  // (FP32 iterations of n-mers whose matrix is in global memory)
+  int tri_cap;
 };
 
 // Shared-memory layout of the SCC kernel (sizes from the launch maxima).
@@ -604,6 +608,7 @@ struct SccSmem {
   int* jsact;
   void* jsc;
   void* jss;
+  float* tri;    // tridiagonal eigen-solver work (after the regular layout; null if none)
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -1155,12 +1160,30 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
     }
   }
   if (!rotated) {
-    JacobiScratch<T> js{sm.jsp, sm.jsq, reinterpret_cast<T*>(sm.jsc), reinterpret_cast<T*>(sm.jss), sm.jsact};
-    const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
-    if (sw < 0 && sizeof(T) == 8) *jac_fail = 1;
-    if (threadIdx.x == 0) sm.misc[3] = sw;   // sweeps (diagnostic trace)
+    bool solved = false;
+    if constexpr (sizeof(T) == 4) {
+      // large n-mer, matrix in global memory: Householder tridiagonalisation
+      // with bisection and twisted-factorisation eigenvectors (Jacobi if it
+      // reports a failure)
+      if (sm.tri && n >= kTriMinN && n <= 512 && !__isShared(pp.A)) {
+        TriWork tw{sm.tri, ar.tri_cap, reinterpret_cast<float*>(ar.W1d + nm.mat),
+                   reinterpret_cast<float*>(ar.W2d + nm.mat)};
+        // columns per lane: the smallest multiple of 32 lanes covering n
+        if (n <= 128) solved = tri_eigh<4>(pp.A, pp.lda, n, pp.CT, pp.W1, pp.W2, tw, gemm, sm.red, sm.eps);
+        else if (n <= 256) solved = tri_eigh<8>(pp.A, pp.lda, n, pp.CT, pp.W1, pp.W2, tw, gemm, sm.red, sm.eps);
+        else if (n <= 384) solved = tri_eigh<12>(pp.A, pp.lda, n, pp.CT, pp.W1, pp.W2, tw, gemm, sm.red, sm.eps);
+        else solved = tri_eigh<16>(pp.A, pp.lda, n, pp.CT, pp.W1, pp.W2, tw, gemm, sm.red, sm.eps);
+        if (solved && threadIdx.x == 0) sm.misc[3] = -2;   // trace: tridiagonal solve
+      }
+    }
+    if (!solved) {
+      JacobiScratch<T> js{sm.jsp, sm.jsq, reinterpret_cast<T*>(sm.jsc), reinterpret_cast<T*>(sm.jss), sm.jsact};
+      const int sw = block_jacobi<T>(pp.A, pp.lda, n, pp.CT, n, n, jac_tol, 40, js, sm.red);
+      if (sw < 0 && sizeof(T) == 8) *jac_fail = 1;
+      if (threadIdx.x == 0) sm.misc[3] = sw;   // sweeps (diagnostic trace)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
+    }
     if (ar.trace && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(ar.trace + kTraceJacobi), 1ULL);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sm.eps[i] = double(pp.A[(long long)i * pp.lda + i]);
     __syncthreads();
     mts = fermi_step<T>(n, nm.nel, ar.g.kT, sm, &nocc);
   }
@@ -1391,6 +1414,8 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   const int a_bytes = (ar.a_smem_d ? int(sizeof(double)) : (ar.a_smem_f ? int(sizeof(float)) : 0)) *
                       ((ar.max_n + (ar.max_n & 1)) * (ar.max_n + (ar.max_n & 1)));
   SccSmem sm = carve_scc_smem(smem_raw, ar.max_n, ar.max_nsh, ar.max_nat, a_bytes);
+  sm.tri = ar.tri_cap > 0 ? reinterpret_cast<float*>(smem_raw + scc_smem_bytes(ar.max_n, ar.max_nsh, ar.max_nat, a_bytes))
+                          : nullptr;
   const long long t_start = clock64();
   build_maps(nm, ar.ft, ar.elem, ar.atom_sh0, ar.el, sm.mp);
   // ghosts of cut bonds healed in this n-mer (hybrid orbital projection):
@@ -2196,7 +2221,25 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.max_n = L.max_n; ar.max_nsh = L.max_nsh; ar.max_nat = L.max_nat;
   const int npad = L.max_n + (L.max_n & 1);
   const int a_bytes = (L.a_smem_d ? 8 : (L.a_smem_f ? 4 : 0)) * npad * npad;
-  const size_t sb = scc_smem_bytes(L.max_n, L.max_nsh, L.max_nat, a_bytes);
+  size_t sb = scc_smem_bytes(L.max_n, L.max_nsh, L.max_nat, a_bytes);
+  // FP32 iterations with the matrix in global memory: the rest of the
+  // shared memory holds the tridiagonal eigen-solver's vectors and as many
+  // packed rows of its trailing matrix as fit
+  ar.tri_cap = 0;
+  if (L.precision == 1 && !L.a_smem_f && !L.a_smem_d && L.max_n >= kTriMinN && L.max_n <= 512) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, scc_kernel);
+    const long long room = (long long)optin - (long long)fa.sharedSizeBytes - (long long)sb - 1024;
+    const long long want = (long long)npad * (npad + 1) / 2;
+    const long long cap = std::min(want, room / 4 - tri_vec_floats(npad));
+    if (cap > 0) {
+      ar.tri_cap = int(cap);
+      sb += sizeof(float) * ((size_t)tri_vec_floats(npad) + (size_t)cap);
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(scc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
   if (e != cudaSuccess) return e;
   scc_kernel<<<n_nmer, kBlock, sb, st>>>(ar);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libfmo_xtb.so")
 
 FMO_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_CONVERGED",
-                5: "ERR_TIMEOUT", 6: "ERR_NAN", 7: "ERR_STATE", 8: "ERR_UNSUPPORTED"}
+                5: "ERR_TIMEOUT", 6: "ERR_NAN", 7: "ERR_STATE", 8: "ERR_UNSUPPORTED", 9: "ERR_EXCHANGE"}
 PREC_FP64, PREC_MIXED = 0, 1
 
 SYMBOLS = ["fmo_options_default", "fmo_create", "fmo_set_system", "fmo_set_coordinates",
@@ -28,7 +28,7 @@ SYMBOLS = ["fmo_options_default", "fmo_create", "fmo_set_system", "fmo_set_coord
            "fmo_get_sizes", "fmo_get_monomers", "fmo_get_dimers", "fmo_get_trimers", "fmo_get_gradient",
            "fmo_get_stats", "fmo_last_error", "fmo_destroy", "fmo_mlp_init", "fmo_mlp_set_weights",
            "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train", "fmo_scc_solve_noalloc", "fmo_fma_peak",
-           "fmo_mlp_loss_grad"]
+           "fmo_mlp_loss_grad", "fmo_set_exchange", "fmo_lpt_partition"]
 MLP_N_WEIGHTS = 26908
 MLP_N_TRAINED = 26754
 
@@ -60,7 +60,11 @@ class FmoOptions(C.Structure):
                 ("trimer_cut", C.c_double), ("scc_tol", C.c_double), ("e_tol", C.c_double),
                 ("outer_tol", C.c_double), ("mixed_switch_tol", C.c_double),
                 ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("nmer_finish", C.c_int32),
-                ("want_gradient", C.c_int32), ("esp_mode", C.c_int32)]
+                ("want_gradient", C.c_int32), ("esp_mode", C.c_int32), ("shard_rank", C.c_int32),
+                ("shard_world", C.c_int32)]
+
+# element-wise sum over the ranks of a sharded run (fmo_exchange_fn)
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_int64)
 
 
 class FmoStats(C.Structure):
@@ -123,6 +127,8 @@ def load_library(path: str | None = None):
     lib.fmo_mlp_train.argtypes = [vp, i32, dp, dp, i32, i32, C.c_double, C.c_uint64, dp]
     lib.fmo_mlp_loss_grad.argtypes = [vp, i32, dp, dp, dp, fp]
     lib.fmo_fma_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
+    lib.fmo_set_exchange.argtypes = [vp, EXCHANGE_FN, vp]
+    lib.fmo_lpt_partition.argtypes = [dp, i64, i32, ip]
     lib.fmo_scc_solve_noalloc.argtypes = [vp, i32, ip, vp, i32, vp, vp, vp, vp, vp, vp, C.c_char_p, i32]
     lib.fmo_last_error.argtypes = [vp]
     lib.fmo_last_error.restype = C.c_char_p
@@ -143,6 +149,16 @@ def fma_peak(precision: str = "fp32", device: int = 0) -> float:
     if st != FMO_OK:
         raise FMOError(st, "fmo_fma_peak failed")
     return t.value
+
+
+def lpt_partition(cost, world: int) -> np.ndarray:
+    """Rank of every work unit under the library's LPT partition (fmo_lpt_partition)."""
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    owner = np.zeros(len(c), dtype=np.int32)
+    st = load_library().fmo_lpt_partition(_dp(c), len(c), int(world), _ip(owner))
+    if st != FMO_OK:
+        raise FMOError(st, "fmo_lpt_partition failed")
+    return owner
 
 
 def params_to_c(params: Params) -> FmoParams:
@@ -248,6 +264,7 @@ class FMO:
         if st != FMO_OK:
             raise FMOError(st, "fmo_create failed")
         self.h = h
+        self._exchange = None
         self.n_atoms = 0
         self.n_frag = 0
 
@@ -283,6 +300,23 @@ class FMO:
 
     def set_coordinates_device(self, ptr: int, stream: int | None = None):
         self._check(self.lib.fmo_set_coordinates_device(self.h, C.c_void_p(ptr), C.c_void_p(stream or 0)))
+
+    def set_exchange(self, fn):
+        """Sharded runs: fn(buf) must replace the float64 array buf by its
+        element-wise sum over all ranks (e.g. shard.allreduce_exchange)."""
+        if fn is None:
+            self._exchange = None
+            self._check(self.lib.fmo_set_exchange(self.h, EXCHANGE_FN(), None))
+            return
+
+        def cb(user, ptr, n):
+            try:
+                fn(np.ctypeslib.as_array(ptr, shape=(int(n),)))
+                return 0
+            except Exception:   # noqa: BLE001 - reported to the library as a failed exchange
+                return 1
+        self._exchange = EXCHANGE_FN(cb)   # kept alive as long as the context
+        self._check(self.lib.fmo_set_exchange(self.h, self._exchange, None))
 
     def set_guess(self, shell_dq: np.ndarray):
         x = np.ascontiguousarray(shell_dq, dtype=np.float64)
