@@ -19,6 +19,11 @@ Every function follows one passage of the paper (Einsele & Mitric, FMO-xTB):
 Readings of passages the paper leaves open are marked READING and listed in
 the design notes.  Units: bohr, Hartree; charges in electrons
 (dq = population - reference occupation, READING C-6).
+PARITY UNPINNED: the modifiers of H0 in Eqs. 8-10 (the polynomial factor Pi,
+the electronegativity factor and the CN-dependent levels) have no independent
+pin: the extended-Hueckel test switches them off and the in-shell
+proportionality test cannot see them; the paper prints no parameter table or
+worked value to check them against.
 """
 from __future__ import annotations
 

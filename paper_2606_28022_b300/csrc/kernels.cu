@@ -1558,13 +1558,16 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
     if (phase == 0 && ct_smem) load_ct_smem();
     if (phase == 0 && ar.reortho32 && !ar.cold_refine) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
     double diff = 0.0;
+    // every step diagonalises to the working precision (no threshold loosened
+    // by the residual): the global mixer then iterates one fixed map.  A
+    // threshold that followed the residual changed the map from step to step
+    // and left the monomer loop of distorted frames oscillating.
     if (phase == 0) {
-      e_el = scc_iteration<float>(nm, ar, sm, pf, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_f), &jac_fail, &diff,
-                                  !ar.cold_refine);
+      e_el = scc_iteration<float>(nm, ar, sm, pf, ar.jacobi_tol_f, &jac_fail, &diff, !ar.cold_refine);
       it32 = 1;
     } else {
-      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(ar.jac_hint, ar.jacobi_tol_d), &jac_fail, &diff,
-                                   !ar.cold_refine, ar.precision == 1 ? ctf_g : nullptr, pf.W1, pf.W2);
+      e_el = scc_iteration<double>(nm, ar, sm, pd, ar.jacobi_tol_d, &jac_fail, &diff, !ar.cold_refine,
+                                   ar.precision == 1 ? ctf_g : nullptr, pf.W1, pf.W2);
     }
     it = 1;
     status = (phase == 1 && jac_fail) ? FMO_SCC_JACOBI_CODE
