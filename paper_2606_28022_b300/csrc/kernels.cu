@@ -1162,10 +1162,10 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   if (!rotated) {
     bool solved = false;
     if constexpr (sizeof(T) == 4) {
-      // large n-mer, matrix in global memory: Householder tridiagonalisation
+      // n-mers of 64 to 512 basis functions: Householder tridiagonalisation
       // with bisection and twisted-factorisation eigenvectors (Jacobi if it
       // reports a failure)
-      if (sm.tri && n >= kTriMinN && n <= 512 && !__isShared(pp.A)) {
+      if (sm.tri && n >= kTriMinN && n <= 512) {
         TriWork tw{sm.tri, ar.tri_cap, reinterpret_cast<float*>(ar.W1d + nm.mat),
                    reinterpret_cast<float*>(ar.W2d + nm.mat)};
         // columns per lane: the smallest multiple of 32 lanes covering n
@@ -1404,6 +1404,9 @@ __device__ __forceinline__ double jacobi_threshold(double last, double floor_tol
 // FP32 iterations without a 10% improvement of the best residual before the
 // FP32 phase gives up and hands over to FP64
 constexpr int kStall32 = 8;
+// iterations without a 10% improvement of the best residual before an n-mer
+// SCC switches to full-precision eigen-solves
+constexpr int kStallTight = 6;
 
 __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1581,6 +1584,16 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
   bool full64 = false;
   double min32 = 1e300;
   int stall32 = 0;
+  // Jacobi thresholds follow the residual (early iterations rotate only the
+  // large elements) until the FP64 iterations stall: kStallTight iterations
+  // without a 10% improvement of their best residual.  From then on every
+  // eigen-solve is to working precision and the Broyden history restarts, so
+  // the mixer iterates one fixed map (a map that changed from step to step
+  // left dimers of distorted geometries oscillating).  A stalled FP32 phase
+  // hands over to FP64 instead (kStall32).
+  bool tight = false;
+  double min_all = 1e300;
+  int stall_all = 0;
   if (!ar.single_step && ar.cold_refine) {
     // the starting rows made S-orthonormal to the working precision
     if (phase == 0) reorthonormalise<float>(nm, ar, sm, pf, ar.cold_steps, 1e-6);
@@ -1595,14 +1608,27 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       if (it32 > 0 && it32 % 4 == 0) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
       // a warm start only needs near-canonical rows before the rotation
       // updates take over: its first eigen-solve may be loose
-      const double thr = (it == 1 && ar.first_jac_tol > 0) ? ar.first_jac_tol : jacobi_threshold(last, ar.jacobi_tol_f);
+      const double thr = tight ? ar.jacobi_tol_f
+                               : ((it == 1 && ar.first_jac_tol > 0) ? ar.first_jac_tol
+                                                                    : jacobi_threshold(last, ar.jacobi_tol_f));
       e_el = scc_iteration<float>(nm, ar, sm, pf, thr, &jac_fail, &diff, it > 1 || !ar.cold_refine || ar.first_rot);
       ++it32;
     } else {
-      e_el = scc_iteration<double>(nm, ar, sm, pd, jacobi_threshold(last, ar.jacobi_tol_d), &jac_fail, &diff,
-                                   it > 1 || !ar.cold_refine, ar.precision == 1 ? ctf_g : nullptr, pf.W1, pf.W2);
+      e_el = scc_iteration<double>(nm, ar, sm, pd, tight ? ar.jacobi_tol_d : jacobi_threshold(last, ar.jacobi_tol_d),
+                                   &jac_fail, &diff, it > 1 || !ar.cold_refine, ar.precision == 1 ? ctf_g : nullptr,
+                                   pf.W1, pf.W2);
     }
     last = diff;
+    if (phase == 1 && !tight) {
+      if (diff < 0.9 * min_all) { min_all = diff; stall_all = 0; }
+      else if (++stall_all >= kStallTight) {
+        tight = true;
+        hcount = 0;
+        hhead = 0;
+        have_prev = false;
+        fresh64 = true;   // no secant pair across the switch
+      }
+    }
     if (ar.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 512) {
       // per iteration: residual (negative in FP32), Jacobi sweeps (-1 =
       // rotation step) and SM cycles
@@ -2225,11 +2251,11 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   const int npad = L.max_n + (L.max_n & 1);
   const int a_bytes = (L.a_smem_d ? 8 : (L.a_smem_f ? 4 : 0)) * npad * npad;
   size_t sb = scc_smem_bytes(L.max_n, L.max_nsh, L.max_nat, a_bytes);
-  // FP32 iterations with the matrix in global memory: the rest of the
-  // shared memory holds the tridiagonal eigen-solver's vectors and as many
-  // packed rows of its trailing matrix as fit
+  // FP32 iterations of n-mers (no FP64 matrix in shared memory): the rest of
+  // the shared memory holds the tridiagonal eigen-solver's vectors and as
+  // many packed rows of its trailing matrix as fit
   ar.tri_cap = 0;
-  if (L.precision == 1 && !L.a_smem_f && !L.a_smem_d && L.max_n >= kTriMinN && L.max_n <= 512) {
+  if (L.precision == 1 && !L.a_smem_d && L.max_n >= kTriMinN && L.max_n <= 512) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
