@@ -114,11 +114,14 @@ typedef struct fmo_options {
   int32_t guess;            /* 0 neutral charges, 1 learned model (fmo_mlp_*;
                                restarts from 0 if the monomer loop does not
                                converge), 2 user charges (fmo_set_guess) */
-  int32_t schedule;         /* 0 (default): after the first FP64 step the
-                               global monomer loop runs device-driven inside
-                               one CUDA graph (a conditional while node ends it
-                               on convergence); 1: one host round trip per
-                               step.  Results are identical. */
+  int32_t schedule;         /* 0 (default): the global monomer loop runs
+                               device-driven in CUDA graphs with conditional
+                               while nodes: the FP32 steps after the first (a
+                               device-side loop control ends them at the
+                               FP32 -> FP64 hand-over), then the FP64 steps
+                               after the hand-over step (ended on
+                               convergence); 1: one host round trip per step.
+                               Results are identical. */
   int32_t monomer_loop;     /* FMO_LOOP_GLOBAL (default): one SCC iteration of
                                every monomer per outer step, then one Broyden
                                step on all monomer charges together;

@@ -99,6 +99,7 @@ struct fmo_ctx {
   // sharded runs: this rank, the number of ranks and the exchange callback
   int shard_rank = 0, shard_world = 1;
   fmo_exchange_fn ex_fn = nullptr;
+  DevBuf d_p32;                           // FP32-phase bookkeeping of the graph-driven monomer loop
   void* ex_user = nullptr;
   cudaStream_t own_stream = nullptr;
   std::string err;
@@ -553,7 +554,8 @@ cudaError_t compute_phi(fmo_ctx* ctx, cudaStream_t st, int use_float) {
 
 fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& sp, bool with_phi,
                    int pass_id, cudaStream_t st, int single_step = 0, int step_phase = 1, int reortho = 0,
-                   int cold = 1, int reortho32 = 0, double jac_hint = 1.0, bool capture = false) {
+                   int cold = 1, int reortho32 = 0, double jac_hint = 1.0, bool capture = false,
+                   const int* step_dev = nullptr) {
   const int nn = int(P.nm.size());
   if (nn == 0) return FMO_OK;
   SccLaunch L{};
@@ -584,6 +586,7 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.reortho = reortho;
   L.cold_refine = cold;
   L.reortho32 = reortho32;
+  L.step_dev = step_dev;
   L.jac_hint = jac_hint;
   // a gradient needs FP64-converged n-mer densities: then the FP32 phase of a
   // mixed-precision n-mer hands over to FP64 iterations run to convergence
@@ -705,7 +708,7 @@ double now_ms(cudaEvent_t a, cudaEvent_t b) {
 // condition on convergence, a NaN residual or the step limit.  No host round
 // trip per step.  `done` steps have run; on return *outer is the last step.
 cudaError_t run_monomer_graph(fmo_ctx* ctx, const fmo_options& o, const SmemPlan& sp, cudaStream_t st, int done,
-                              int* outer) {
+                              int* outer, int phase = 1, Phase32State* p32 = nullptr, int cap32 = 0) {
   const int nf = ctx->n_frag;
   int* d_outer = reinterpret_cast<int*>(ctx->d_scalar.p);
   cudaError_t e = h2d(d_outer, &done, sizeof(int), st);
@@ -735,14 +738,20 @@ cudaError_t run_monomer_graph(fmo_ctx* ctx, const fmo_options& o, const SmemPlan
   GK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   GK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   {
-    cudaError_t ce = compute_phi(ctx, cs, 0);
-    fmo_status fs = (ce == cudaSuccess) ? run_scc(ctx, ctx->mono, o, sp, true, 0, cs, 1, 1, 0, 0, 0, 1.0, true)
+    // one step: the FP32 phase works with an FP32 estimate of the potential
+    // and orthonormalises every fourth step (decided from the device step count)
+    cudaError_t ce = compute_phi(ctx, cs, phase == 0 ? 1 : 0);
+    fmo_status fs = (ce == cudaSuccess) ? run_scc(ctx, ctx->mono, o, sp, true, 0, cs, 1, phase, 0, 0, 0, 1.0, true,
+                                                  phase == 0 ? d_outer : nullptr)
                                         : FMO_ERR_CUDA;
     if (ce == cudaSuccess && fs == FMO_OK)
       ce = launch_global_mix(cs, ctx->n_sh, ctx->d_dq_mono.as<double>(), ctx->mono.dq.as<double>(), nf,
                              ctx->mono.energy.as<double>(), ctx->d_mix_hist.as<double>(), ctx->d_mix_state.p,
-                             o.outer_tol, o.e_tol, 1);
-    if (ce == cudaSuccess && fs == FMO_OK) ce = launch_loop_control(cs, h, ctx->d_mix_state.p, d_outer, o.max_outer);
+                             o.outer_tol, o.e_tol, phase == 1);
+    if (ce == cudaSuccess && fs == FMO_OK)
+      ce = (phase == 0) ? launch_loop_control32(cs, h, ctx->d_mix_state.p, p32, d_outer, o.max_outer,
+                                                o.mixed_switch_tol, cap32, kStall32)
+                        : launch_loop_control(cs, h, ctx->d_mix_state.p, d_outer, o.max_outer);
     cudaGraph_t captured = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
     if (ce == cudaSuccess && fs != FMO_OK) ce = cudaErrorUnknown;
@@ -759,8 +768,13 @@ cudaError_t run_monomer_graph(fmo_ctx* ctx, const fmo_options& o, const SmemPlan
   const int steps = *outer - done;
   for (const Nmer& m : ctx->mono.nm) {
     const double n3 = 15.0 * double(m.n) * m.n * m.n;
-    ctx->stats.iters_fp64[0] += steps;
-    ctx->stats.flops_fp64[0] += n3 * steps;
+    if (phase == 0) {
+      ctx->stats.iters_fp32[0] += steps;
+      ctx->stats.flops_fp32[0] += n3 * steps;
+    } else {
+      ctx->stats.iters_fp64[0] += steps;
+      ctx->stats.flops_fp64[0] += n3 * steps;
+    }
   }
   ctx->stats.scc_launches[0] += steps;
   cleanup();
@@ -1289,7 +1303,7 @@ void fmo_destroy(fmo_ctx* ctx) {
                     &ctx->d_f_sh0, &ctx->d_f_nsh, &ctx->d_f_ao0, &ctx->d_f_nao, &ctx->d_trace, &ctx->d_gam_full, &ctx->d_mlp_W, &ctx->d_mlp_W16, &ctx->d_mlp_m, &ctx->d_mlp_v,
                     &ctx->d_mlp_elem4, &ctx->d_mlp_atom_frag, &ctx->d_mlp_atom_ie, &ctx->d_mlp_sh_ie,
                     &ctx->d_mlp_fcharge, &ctx->d_mlp_err, &ctx->d_mlp_X, &ctx->d_mlp_y, &ctx->d_mlp_q, &ctx->d_ghost_frag, &ctx->d_ghost_src, &ctx->d_bda_baa_frag, &ctx->d_hop_baa, &ctx->d_dq_mono, &ctx->d_phi, &ctx->d_phi_part,
-                    &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_pair_scc, &ctx->d_dE_pair,
+                    &ctx->d_bounds, &ctx->d_rmin, &ctx->d_scalar, &ctx->d_t0, &ctx->d_mix_hist, &ctx->d_mix_state, &ctx->d_p32, &ctx->d_pair_scc, &ctx->d_dE_pair,
                     &ctx->d_esdim_pairs, &ctx->d_esdim_idx, &ctx->d_tri_frag, &ctx->d_dE3, &ctx->d_corr,
                     &ctx->d_totals, &ctx->d_grad_work, &ctx->d_grad, &ctx->d_gt, &ctx->d_gslots_a,
                     &ctx->d_gslots_s, &ctx->d_gpair, &ctx->d_gfrag_ptr, &ctx->d_gent_a, &ctx->d_gent_s,
@@ -1647,6 +1661,34 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
       step_parts.push_back(ex_per_nmer(ctx->mono.energy, 0, nf));
     }
     for (outer = 1; outer <= o.max_outer; ++outer) {
+      if (graph_ok && phase == 0 && outer > 1 && outer < o.max_outer) {
+        // the FP32 steps after the first run device-driven inside one CUDA
+        // graph, which ends on convergence or at the FP32 phase's hand-over
+        int last = outer - 1;
+        Phase32State p{min32, stall32, n32, 0};
+        CK(ctx->d_p32.ensure(sizeof(Phase32State)));
+        CK(h2d(ctx->d_p32.p, &p, sizeof(p), st));
+        if (run_monomer_graph(ctx, o, sp_mono, st, outer - 1, &last, 0, ctx->d_p32.as<Phase32State>(), cap32) ==
+            cudaSuccess) {
+          CK(d2h(&hs, ctx->d_mix_state.p, sizeof(hs), st));
+          CK(d2h(&p, ctx->d_p32.p, sizeof(p), st));
+          CK(sync_stream(st));
+          outer = last;
+          min32 = p.min32; stall32 = p.stall32; n32 = p.n32;
+          change = hs.converged ? 0.0 : hs.diff;
+          if (!(hs.diff == hs.diff) || hs.converged) break;
+          if (p.hand_over) {
+            phase = 1;
+            reortho = 1;
+            CK(cudaMemsetAsync((char*)ctx->d_mix_state.p + 3 * sizeof(double), 0, sizeof(int), st));
+            CK(cudaMemsetAsync((char*)ctx->d_mix_state.p + 3 * sizeof(double) + 4 * sizeof(int), 0, sizeof(int),
+                               st));
+          }
+          continue;
+        }
+        graph_ok = false;                 // graphs unavailable: host-driven steps
+        cudaGetLastError();
+      }
       if (graph_ok && phase == 1 && reortho == 0 && outer > 1 && outer < o.max_outer) {
         // the remaining FP64 steps run device-driven inside one CUDA graph
         int last = outer - 1;

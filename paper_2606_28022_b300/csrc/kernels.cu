@@ -562,6 +562,7 @@ struct SccArgs {
   int reortho;       // single step: carry the FP32 vectors over to FP64 first
   int cold_refine;   // the vectors are the Loewdin start: restore S-orthonormality in FP64 first
   int reortho32;     // single step: one FP32 Newton-Schulz step before the iteration
+  const int* step_dev;   // if set: reortho32 from the device step count (graph-launched FP32 steps)
   double jac_hint;   // SCC residual before this launch (sets the first Jacobi threshold)
   const double* jac_hint_dev;   // if set: read jac_hint from the device (graph-launched steps)
   const float* S32;  // mixed precision: S and H0 rounded to FP32 (the FP32 iterations read these)
@@ -1559,7 +1560,10 @@ __global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
       reorthonormalise<float>(nm, ar, sm, pf, 2, 1e-6);
     }
     if (phase == 0 && ct_smem) load_ct_smem();
-    if (phase == 0 && ar.reortho32 && !ar.cold_refine) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
+    // every fourth FP32 step (1-based, after the first) restores orthonormality
+    const int step = ar.step_dev ? *ar.step_dev + 1 : 0;
+    const bool r32 = ar.step_dev ? (step > 1 && step % 4 == 0) : (ar.reortho32 != 0);
+    if (phase == 0 && r32 && !ar.cold_refine) reorthonormalise<float>(nm, ar, sm, pf, 1, 0.0);
     double diff = 0.0;
     // every step diagonalises to the working precision (no threshold loosened
     // by the residual): the global mixer then iterates one fixed map.  A
@@ -2243,7 +2247,7 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   ar.status = L.status; ar.guess_from_mono = L.guess_from_mono; ar.precision = L.precision;
   ar.max_iter = L.max_iter; ar.fp32_cap = L.fp32_cap;
   ar.single_step = L.single_step; ar.step_phase = L.step_phase; ar.reortho = L.reortho;
-  ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.jac_hint = L.jac_hint; ar.jac_hint_dev = L.jac_hint_dev; ar.S32 = L.S32; ar.H32 = L.H32; ar.trace = L.trace;
+  ar.cold_refine = L.cold_refine; ar.reortho32 = L.reortho32; ar.step_dev = L.step_dev; ar.jac_hint = L.jac_hint; ar.jac_hint_dev = L.jac_hint_dev; ar.S32 = L.S32; ar.H32 = L.H32; ar.trace = L.trace;
   ar.fp64_finish = L.fp64_finish; ar.energy_finish = L.energy_finish; ar.first_jac_tol = L.first_jac_tol; ar.cold_steps = L.cold_steps; ar.first_rot = L.first_rot; ar.tol = L.tol; ar.etol = L.etol;
   ar.switch_tol = L.switch_tol; ar.jacobi_tol_d = L.jacobi_tol_d; ar.jacobi_tol_f = L.jacobi_tol_f;
   ar.t0 = L.t0; ar.budget_ns = L.budget_ns; ar.a_smem_d = L.a_smem_d; ar.a_smem_f = L.a_smem_f;
@@ -2338,6 +2342,33 @@ __global__ void loop_control_kernel(cudaGraphConditionalHandle handle, const Mix
   const int o = ++*outer;
   const bool more = !st->converged && st->diff == st->diff && o < max_outer;
   cudaGraphSetConditional(handle, more ? 1u : 0u);
+}
+
+// The FP32 steps' bookkeeping of the host-driven loop, in the same order: stop
+// on convergence or NaN; otherwise track the best residual and end the FP32
+// phase at the switch tolerance, the step cap or kStall32 steps without a
+// 10% improvement; continue while none of these and steps remain.
+__global__ void loop_control32_kernel(cudaGraphConditionalHandle handle, const MixState* st, Phase32State* p,
+                                      int* outer, int max_outer, double switch_tol, int cap32, int stall_limit) {
+  const int o = ++*outer;
+  const double d = st->diff;
+  const bool stop = st->converged || !(d == d);
+  bool hand = false;
+  if (!stop) {
+    if (d < 0.9 * p->min32) { p->min32 = d; p->stall32 = 0; } else { ++p->stall32; }
+    hand = d < switch_tol || ++p->n32 >= cap32 || p->stall32 >= stall_limit;
+  }
+  p->hand_over = hand ? 1 : 0;
+  cudaGraphSetConditional(handle, (!stop && !hand && o < max_outer) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_control32(cudaStream_t st, unsigned long long handle, const void* mix_state,
+                                  Phase32State* p32, int* outer, int max_outer, double switch_tol, int cap32,
+                                  int stall_limit) {
+  loop_control32_kernel<<<1, 1, 0, st>>>((cudaGraphConditionalHandle)handle, (const MixState*)mix_state, p32, outer,
+                                         max_outer, switch_tol, cap32, stall_limit);
+  LAUNCH_CHECK();
+  return cudaSuccess;
 }
 
 cudaError_t launch_loop_control(cudaStream_t st, unsigned long long handle, const void* mix_state, int* outer,

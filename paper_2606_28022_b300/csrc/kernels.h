@@ -75,6 +75,7 @@ struct SccLaunch {
   int reortho;
   int cold_refine;
   int reortho32;
+  const int* step_dev;   // graph-launched FP32 steps: steps done before this one (sets reortho32 on the device)
   double jac_hint;
   const double* jac_hint_dev;
   const float* S32;   // mixed precision: FP32 copies of S and H0 (launch_to_float)
@@ -123,6 +124,17 @@ cudaError_t launch_hop_projector(cudaStream_t st, int n_nmer, const Nmer* nmers,
                                  const int* elem, const DevElem* el, double v_hop, const double* S, double* V,
                                  double* Qd = nullptr, float* Qf = nullptr, double* Dd = nullptr, float* Df = nullptr,
                                  int* nq = nullptr);
+// FP32 steps of the global monomer loop inside a CUDA graph: the same stall
+// and hand-over bookkeeping as the host-driven loop, on the device
+struct Phase32State {
+  double min32;   // best residual of the FP32 steps
+  int stall32;    // steps since its last 10% improvement
+  int n32;        // FP32 steps taken
+  int hand_over;  // 1: the FP32 phase ended (converged to the switch tolerance, cap, or stall)
+};
+cudaError_t launch_loop_control32(cudaStream_t st, unsigned long long handle, const void* mix_state,
+                                  Phase32State* p32, int* outer, int max_outer, double switch_tol, int cap32,
+                                  int stall_limit);
 cudaError_t launch_loop_control(cudaStream_t st, unsigned long long handle, const void* mix_state, int* outer,
                                 int max_outer);
 cudaError_t launch_frag_bounds(cudaStream_t st, int n_frag, FragTab ft, const double* xyz, double* bounds);
