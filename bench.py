@@ -41,6 +41,9 @@ sys.path.insert(0, ROOT)
 METRIC = "FMO2/3 energy wall time & fragment-SCC/s vs plain FP64 GPU at |dE|<=1e-6 Eh"
 UNIT = "fragment-SCC/s"
 WORKLOADS = {
+    "water64": dict(level=2, opts=dict(all_dimers_scc=1),
+                    desc="water64-FMO2: 64 rigid waters (O-H 0.957 A, 104.5 deg), seeded centres uniform in a "
+                         "1.0 g/cm3 sphere with O-O >= 2.6 A, random orientations; all 2016 dimers with full SCC"),
     "pentacene660": dict(level=3, desc="pentacene660-FMO3: 660 C22H14 (23,760 atoms), seeded triclinic herringbone "
                                        "a=6.27 b=7.78 c=14.53 A (76.5/87.7/84.7 deg), 0.05 A jitter; SCC dimer iff "
                                        "closest atom < 4.0 A, else ES-DIM; SCC trimer iff all three pairs < 4.0 A"),
@@ -85,6 +88,8 @@ def workload(rank: int, name: str = "pentacene660", n_mol: int | None = None):
     from paper_2606_28022_b300.inputs import geometry as G
     if name == "pentacene660":
         system, info = G.pentacene_cluster(660, seed=4)
+    elif name == "water64":
+        system, info = G.water_cluster(64, 1), {}
     else:
         system, info = G.anthracene_cluster(128, seed=2)
     if n_mol is not None and n_mol < system.n_frag:
@@ -248,7 +253,8 @@ def run_reference(args, rank, world):
     from paper_2606_28022_b300.inputs.params import ANGSTROM
     wl = WORKLOADS[args.workload]
     system, _ = workload(0, args.workload, args.n_mol)
-    dimers, trimers = nmer_lists(system, wl["level"], 4.0 * ANGSTROM)
+    cut = float("inf") if wl.get("opts", {}).get("all_dimers_scc") else 4.0 * ANGSTROM
+    dimers, trimers = nmer_lists(system, wl["level"], cut)
     workers = cpu_workers()
     per_step = max(8, 2 * workers)
     for k in range(args.warmup):
@@ -324,7 +330,7 @@ def main():
     g.set_system(system)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
-    opts = fmo.options(level=wl["level"], precision=args.precision)
+    opts = fmo.options(level=wl["level"], precision=args.precision, **wl.get("opts", {}))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
     e_key = wl["level"] - 1
 
@@ -384,7 +390,7 @@ def main():
     # plain FP64 GPU form of the same workload (the metric's comparison)
     fp64 = None
     if rank == 0 and args.precision == "mixed" and args.fp64_repeats > 0:
-        o64 = fmo.options(level=wl["level"], precision="fp64")
+        o64 = fmo.options(level=wl["level"], precision="fp64", **wl.get("opts", {}))
         ms64 = []
         for _ in range(args.fp64_repeats):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -408,7 +414,7 @@ def main():
     # then fmo_get_gradient), once
     grad = None
     if rank == 0 and not args.no_gradient:
-        og = fmo.options(level=wl["level"], precision=args.precision, want_gradient=1)
+        og = fmo.options(level=wl["level"], precision=args.precision, want_gradient=1, **wl.get("opts", {}))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         g.run(og, stream=sptr)
