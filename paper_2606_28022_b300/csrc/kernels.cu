@@ -1409,7 +1409,12 @@ constexpr int kStall32 = 8;
 // SCC switches to full-precision eigen-solves
 constexpr int kStallTight = 6;
 
-__global__ void __launch_bounds__(kBlock) scc_kernel(SccArgs ar) {
+// kMinBlocks = 2: at most 128 registers per thread, so that two CTAs share an
+// SM (more warps to hide latency) when the pass's matrices live in global
+// memory; kMinBlocks = 1: all 255 registers (n-mers whose matrices fill the
+// shared memory run one CTA per SM anyway).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) scc_kernel(SccArgs ar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ar.jac_hint_dev) ar.jac_hint = *ar.jac_hint_dev;
   const int idx = ar.order[blockIdx.x];
@@ -2257,15 +2262,22 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   size_t sb = scc_smem_bytes(L.max_n, L.max_nsh, L.max_nat, a_bytes);
   // FP32 iterations of n-mers (no FP64 matrix in shared memory): the rest of
   // the shared memory holds the tridiagonal eigen-solver's vectors and as
-  // many packed rows of its trailing matrix as fit
+  // many packed rows of its trailing matrix as fit.  With the eigen-solve
+  // matrix in global memory two CTAs share an SM (each gets half of the SM's
+  // shared memory).
   ar.tri_cap = 0;
+  const bool two = (L.precision == 1 && a_bytes == 0 && L.max_n >= kTriMinN);
   if (L.precision == 1 && !L.a_smem_d && L.max_n >= kTriMinN && L.max_n <= 512) {
-    int dev = 0, optin = 0;
+    int dev = 0, optin = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, scc_kernel);
-    const long long room = (long long)optin - (long long)fa.sharedSizeBytes - (long long)sb - 1024;
+    if (two) cudaFuncGetAttributes(&fa, scc_kernel<2>);
+    else cudaFuncGetAttributes(&fa, scc_kernel<1>);
+    // per CTA: dynamic + static + 1 KB reserved by the runtime
+    const long long budget = two ? std::min<long long>(optin, per_sm / 2 - 1024) : optin;
+    const long long room = budget - (long long)fa.sharedSizeBytes - (long long)sb - 1024;
     const long long want = (long long)npad * (npad + 1) / 2;
     const long long cap = std::min(want, room / 4 - tri_vec_floats(npad));
     if (cap > 0) {
@@ -2273,9 +2285,15 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
       sb += sizeof(float) * ((size_t)tri_vec_floats(npad) + (size_t)cap);
     }
   }
-  cudaError_t e = cudaFuncSetAttribute(scc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  if (e != cudaSuccess) return e;
-  scc_kernel<<<n_nmer, kBlock, sb, st>>>(ar);
+  if (two) {
+    cudaError_t e = cudaFuncSetAttribute(scc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    if (e != cudaSuccess) return e;
+    scc_kernel<2><<<n_nmer, kBlock, sb, st>>>(ar);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(scc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    if (e != cudaSuccess) return e;
+    scc_kernel<1><<<n_nmer, kBlock, sb, st>>>(ar);
+  }
   LAUNCH_CHECK();
   return cudaSuccess;
 }
