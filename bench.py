@@ -465,7 +465,7 @@ def main():
         dl = [tuple(x) for x in dims.ij[dims.scc]]
         tl = [tuple(x) for x in tris.ijk]
         workers = cpu_workers()
-        rate, dt, counts, workers = cpu_oracle_sample(system, s0["n_monomer_solves"], dl, tl, max(8, 3 * workers),
+        rate, dt, counts, workers = cpu_oracle_sample(system, s0["n_monomer_solves"], dl, tl, max(8, 15 * workers),
                                                       workers=workers)
         cpu = {"value": rate, "unit": UNIT, "cores": workers, "kind": "oracle",
                "sample": f"{sum(counts.values())} oracle n-mer SCC solves of this workload {counts} in the workload's "

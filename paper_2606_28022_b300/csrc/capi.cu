@@ -453,13 +453,19 @@ bool pass_fits(const Pass& P) {
          P.max_projected <= kMaxProjected;
 }
 
-SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision) {
+// fp32_only: mixed-precision dimers or trimers that iterate in FP32 only (they
+// end with the FP64 energy of their FP32 density); with 64 or more basis
+// functions their matrices stay in global memory, so that two CTAs share an
+// SM and the FP32 eigen-solves use the tridiagonal solver.
+SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision, bool fp32_only = false) {
   const int npad = P.max_n + (P.max_n & 1);
   SmemPlan sp{0, 0, 0};
   const size_t lim = (size_t)ctx->smem_optin;
   const size_t with_d = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 8 * npad * npad);
   const size_t with_f = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 4 * npad * npad);
-  if (with_d <= lim) { sp.a_d = 1; sp.a_f = (precision == FMO_PREC_MIXED); }
+  if (fp32_only && precision == FMO_PREC_MIXED && P.max_n >= 64) {
+    // global memory (sp stays {0, 0})
+  } else if (with_d <= lim) { sp.a_d = 1; sp.a_f = (precision == FMO_PREC_MIXED); }
   else if (precision == FMO_PREC_MIXED && with_f <= lim) { sp.a_f = 1; }
   sp.bytes = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, (sp.a_d ? 8 : (sp.a_f ? 4 : 0)) * npad * npad);
   return sp;
@@ -1836,7 +1842,10 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   ctx->stats.n_trimer_scc = (long long)tri_tu.size();
   // ---- SCC dimers in the frozen ESP
   CK(plan_pass(ctx, ctx->dim, dim_tu, dim_nf, false, o.precision, st));
-  const SmemPlan sp_dim = plan_smem(ctx, ctx->dim, o.precision);
+  // dimers and trimers that iterate in FP32 only: no cut bonds, no gradient,
+  // the FP64 energy finish
+  const bool nmer_fp32_only = ctx->n_cut == 0 && !o.want_gradient && o.nmer_finish == FMO_NMER_FINISH_ENERGY;
+  const SmemPlan sp_dim = plan_smem(ctx, ctx->dim, o.precision, nmer_fp32_only);
   if (sp_dim.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->dim))
     return fail(ctx, FMO_ERR_UNSUPPORTED, "dimer too large");
   if (!dim_tu.empty()) {
@@ -1864,7 +1873,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   stage(st, "esdim", int(es_pairs.size()));
   // ---- SCC trimers
   CK(plan_pass(ctx, ctx->tri, tri_tu, tri_nf, false, o.precision, st));
-  const SmemPlan sp_tri = plan_smem(ctx, ctx->tri, o.precision);
+  const SmemPlan sp_tri = plan_smem(ctx, ctx->tri, o.precision, nmer_fp32_only);
   if (sp_tri.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->tri))
     return fail(ctx, FMO_ERR_UNSUPPORTED, "trimer too large");
   if (!tri_tu.empty()) {
