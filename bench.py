@@ -330,7 +330,10 @@ def main():
     g.set_system(system)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
-    opts = fmo.options(level=wl["level"], precision=args.precision, **wl.get("opts", {}))
+    # the dimer/trimer schedule cached by the autotuner for this size class
+    # (the built-in rule when none is cached)
+    from paper_2606_28022_b300 import autotune
+    opts = autotune.options(system, wl["level"], args.precision, dev.index, **wl.get("opts", {}))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
     e_key = wl["level"] - 1
 
@@ -478,6 +481,10 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": wl["desc"], "precision": args.precision, "level": wl["level"],
+                           "nmer_schedule": {"nmer_ctas_per_sm": int(opts.nmer_ctas_per_sm),
+                                             "nmer_matrix_smem": int(opts.nmer_matrix_smem),
+                                             "source": "autotuner cache" if (opts.nmer_ctas_per_sm or
+                                                                             opts.nmer_matrix_smem) else "rule"},
                            "n_frag": system.n_frag, "n_atoms": system.n_atoms,
                            "n_dimer_scc": s0["n_dimer_scc"], "n_dimer_esdim": s0["n_dimer_esdim"],
                            "n_trimer_scc": s0["n_trimer_scc"], "outer_iterations": s0["outer_iterations"],

@@ -173,6 +173,17 @@ typedef struct fmo_options {
                                runs need the global monomer loop and
                                want_gradient = 0, and run the monomer loop
                                host-driven (schedule 1). */
+  int32_t nmer_ctas_per_sm; /* schedule of the dimer and trimer passes (the
+                               autotuner's knobs; results do not depend on
+                               them): 0 (default) the built-in rule, 1 one CTA
+                               per SM with 255 registers per thread, 2 two CTAs
+                               per SM with 128 registers each and half an SM of
+                               shared memory each */
+  int32_t nmer_matrix_smem; /* where the dimers' and trimers' n x n eigen-solve
+                               matrix lives: 0 (default) the built-in rule
+                               (global memory for mixed-precision n-mers that
+                               iterate in FP32 only), 1 shared memory where it
+                               fits, 2 global memory */
 } fmo_options;
 
 /* Element-wise sum over the ranks of a sharded run: replace buf[0 .. n) by

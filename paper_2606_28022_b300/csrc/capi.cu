@@ -457,13 +457,15 @@ bool pass_fits(const Pass& P) {
 // end with the FP64 energy of their FP32 density); with 64 or more basis
 // functions their matrices stay in global memory, so that two CTAs share an
 // SM and the FP32 eigen-solves use the tridiagonal solver.
-SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision, bool fp32_only = false) {
+SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision, bool fp32_only = false, int placement = 0) {
   const int npad = P.max_n + (P.max_n & 1);
   SmemPlan sp{0, 0, 0};
   const size_t lim = (size_t)ctx->smem_optin;
   const size_t with_d = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 8 * npad * npad);
   const size_t with_f = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 4 * npad * npad);
-  if (fp32_only && precision == FMO_PREC_MIXED && P.max_n >= 64) {
+  // placement: 0 the rule above, 1 shared memory where it fits, 2 global memory
+  const bool global = placement == 2 || (placement == 0 && fp32_only && precision == FMO_PREC_MIXED && P.max_n >= 64);
+  if (global) {
     // global memory (sp stays {0, 0})
   } else if (with_d <= lim) { sp.a_d = 1; sp.a_f = (precision == FMO_PREC_MIXED); }
   else if (precision == FMO_PREC_MIXED && with_f <= lim) { sp.a_f = 1; }
@@ -622,6 +624,7 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.t0 = ctx->d_t0.as<unsigned long long>();
   L.budget_ns = o.deadline_s > 0 ? (unsigned long long)(o.deadline_s * 1e9) : 0ULL;
   L.a_smem_d = sp.a_d; L.a_smem_f = sp.a_f;
+  L.ctas_per_sm = pass_id >= 1 ? o.nmer_ctas_per_sm : 0;
   L.max_n = P.max_n; L.max_nsh = P.max_nsh; L.max_nat = P.max_nat;
   if (!sp.a_d) CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
   if (o.precision == FMO_PREC_MIXED && !sp.a_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
@@ -1581,6 +1584,8 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
   if (o.want_gradient != 0 && o.want_gradient != 1) return fail(ctx, FMO_ERR_ARG, "want_gradient must be 0 or 1");
   if (o.esp_mode != FMO_ESP_AUTO && o.esp_mode != FMO_ESP_PAIRWISE) return fail(ctx, FMO_ERR_ARG, "unknown esp_mode");
+  if (o.nmer_ctas_per_sm < 0 || o.nmer_ctas_per_sm > 2 || o.nmer_matrix_smem < 0 || o.nmer_matrix_smem > 2)
+    return fail(ctx, FMO_ERR_ARG, "nmer_ctas_per_sm and nmer_matrix_smem must be 0, 1 or 2");
   const int world = o.shard_world <= 1 ? 1 : o.shard_world;
   if (o.shard_world < 0 || o.shard_rank < 0 || o.shard_rank >= world)
     return fail(ctx, FMO_ERR_ARG, "shard_rank must lie in [0, shard_world)");
@@ -1845,7 +1850,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   // dimers and trimers that iterate in FP32 only: no cut bonds, no gradient,
   // the FP64 energy finish
   const bool nmer_fp32_only = ctx->n_cut == 0 && !o.want_gradient && o.nmer_finish == FMO_NMER_FINISH_ENERGY;
-  const SmemPlan sp_dim = plan_smem(ctx, ctx->dim, o.precision, nmer_fp32_only);
+  const SmemPlan sp_dim = plan_smem(ctx, ctx->dim, o.precision, nmer_fp32_only, o.nmer_matrix_smem);
   if (sp_dim.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->dim))
     return fail(ctx, FMO_ERR_UNSUPPORTED, "dimer too large");
   if (!dim_tu.empty()) {
@@ -1873,7 +1878,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
   stage(st, "esdim", int(es_pairs.size()));
   // ---- SCC trimers
   CK(plan_pass(ctx, ctx->tri, tri_tu, tri_nf, false, o.precision, st));
-  const SmemPlan sp_tri = plan_smem(ctx, ctx->tri, o.precision, nmer_fp32_only);
+  const SmemPlan sp_tri = plan_smem(ctx, ctx->tri, o.precision, nmer_fp32_only, o.nmer_matrix_smem);
   if (sp_tri.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->tri))
     return fail(ctx, FMO_ERR_UNSUPPORTED, "trimer too large");
   if (!tri_tu.empty()) {

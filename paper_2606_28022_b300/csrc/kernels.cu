@@ -2266,7 +2266,8 @@ cudaError_t launch_scc(cudaStream_t st, int n_nmer, const SccLaunch& L) {
   // matrix in global memory two CTAs share an SM (each gets half of the SM's
   // shared memory).
   ar.tri_cap = 0;
-  const bool two = (L.precision == 1 && a_bytes == 0 && L.max_n >= kTriMinN);
+  const bool two = L.ctas_per_sm == 2 ||
+                   (L.ctas_per_sm == 0 && L.precision == 1 && a_bytes == 0 && L.max_n >= kTriMinN);
   if (L.precision == 1 && !L.a_smem_d && L.max_n >= kTriMinN && L.max_n <= 512) {
     int dev = 0, optin = 0, per_sm = 0;
     cudaGetDevice(&dev);

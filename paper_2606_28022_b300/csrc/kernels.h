@@ -91,6 +91,7 @@ struct SccLaunch {
   const unsigned long long* t0;   // device timestamp of the run start
   unsigned long long budget_ns;   // 0 = no deadline
   int a_smem_d, a_smem_f;
+  int ctas_per_sm;   // 0: rule (two CTAs per SM when the eigen-solve matrix is in global memory), 1 or 2
   int max_n, max_nsh, max_nat;
 };
 

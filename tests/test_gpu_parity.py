@@ -241,3 +241,25 @@ def test_graph_driven_and_host_driven_monomer_loops_agree(gpu, params, water64):
         assert out[a][0][:2] == out[b][0][:2]          # FMO1, FMO2 (FMO3 is NaN at level 2)
         assert np.array_equal(out[a][1], out[b][1])
         assert out[a][2] == out[b][2]
+
+
+def test_nmer_schedules_change_speed_not_results(gpu, params, anthracene4):
+    # the autotuner's knobs: CTAs per SM (same arithmetic) and the place of the
+    # eigen-solve matrix (Jacobi in shared memory or the tridiagonal solver in
+    # global memory: the same solution to FP32 rounding)
+    from paper_2606_28022_b300 import fmo
+    gpu.set_system(anthracene4)
+    out = {}
+    for c in (0, 1, 2):
+        for m in (0, 1, 2):
+            gpu.run(fmo.options(all_dimers_scc=1, precision="mixed", nmer_ctas_per_sm=c, nmer_matrix_smem=m))
+            out[(c, m)] = (gpu.energies()[1], gpu.dimers().dE.copy())
+    ref = ofmo.fmo(anthracene4, params, ofmo.FMOOptions(all_dimers_scc=True))
+    for (c, m), (e2, dE) in out.items():
+        assert abs(e2 - ref.e_fmo2) < E_TOT_MIXED
+        assert np.max(np.abs(dE - ref.dE_dimer)) < E_NMER_MIXED
+    for m in (1, 2):
+        assert out[(1, m)][0] == out[(2, m)][0]          # one or two CTAs per SM: bit for bit
+    with pytest.raises(fmo.FMOError) as e:
+        gpu.run(fmo.options(nmer_ctas_per_sm=3))
+    assert e.value.status == 1
