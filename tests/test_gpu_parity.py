@@ -263,3 +263,18 @@ def test_nmer_schedules_change_speed_not_results(gpu, params, anthracene4):
     with pytest.raises(fmo.FMOError) as e:
         gpu.run(fmo.options(nmer_ctas_per_sm=3))
     assert e.value.status == 1
+
+
+def test_beyond_512_basis_functions_two_fragments_equal_full_scc(gpu, params):
+    # 96 waters in two fragments of 48 (288 basis functions each): the monomers
+    # take the tridiagonal solver from global memory, the dimer (576 > 512
+    # functions) falls back to Jacobi on a global-memory matrix; FMO2 of two
+    # fragments is the full SCC
+    w = G.water_cluster(96, 3)
+    nat = len(w.Z)
+    frag = (np.arange(nat) // (3 * 48)).astype(w.frag.dtype)
+    s = G.System(Z=w.Z, xyz=w.xyz, frag=frag, frag_charge=np.zeros(2))
+    full = xtb.single_point(s, params)
+    for prec, tol in (("fp64", E_TOT), ("mixed", E_TOT_MIXED)):
+        g = run_gpu(gpu, s, all_dimers_scc=1, precision=prec)
+        assert abs(g.energies()[1] - full.energy) < tol, prec
