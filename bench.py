@@ -481,10 +481,9 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": wl["desc"], "precision": args.precision, "level": wl["level"],
-                           "nmer_schedule": {"nmer_ctas_per_sm": int(opts.nmer_ctas_per_sm),
-                                             "nmer_matrix_smem": int(opts.nmer_matrix_smem),
-                                             "source": "autotuner cache" if (opts.nmer_ctas_per_sm or
-                                                                             opts.nmer_matrix_smem) else "rule"},
+                           "schedule": {**{f: int(getattr(opts, f)) for f in autotune.FIELDS},
+                                        "source": "autotuner cache" if any(getattr(opts, f) for f in
+                                                                           autotune.FIELDS) else "rule"},
                            "n_frag": system.n_frag, "n_atoms": system.n_atoms,
                            "n_dimer_scc": s0["n_dimer_scc"], "n_dimer_esdim": s0["n_dimer_esdim"],
                            "n_trimer_scc": s0["n_trimer_scc"], "outer_iterations": s0["outer_iterations"],

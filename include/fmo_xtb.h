@@ -184,6 +184,13 @@ typedef struct fmo_options {
                                (global memory for mixed-precision n-mers that
                                iterate in FP32 only), 1 shared memory where it
                                fits, 2 global memory */
+  int32_t monomer_ctas_per_sm;  /* the same two knobs for the monomer pass: 0
+                               (default) the built-in rule, 1 or 2 CTAs per SM */
+  int32_t monomer_matrix_smem;  /* 0 (default) the rule (shared memory where it
+                               fits), 1 shared memory where it fits, 2 global
+                               memory, 3 mixed precision: only the FP32 matrix
+                               in shared memory (small enough for two CTAs per
+                               SM) */
 } fmo_options;
 
 /* Element-wise sum over the ranks of a sharded run: replace buf[0 .. n) by

@@ -1,14 +1,17 @@
-"""Schedule autotuner of the dimer and trimer passes.
+"""Schedule autotuner of the SCC passes (monomers, dimers, trimers).
 
-Two knobs of fmo_options change how fast the dimer and trimer passes run, not
-what they compute: nmer_ctas_per_sm (one CTA per SM with 255 registers per
-thread, or two with 128 registers and half an SM of shared memory each) and
-nmer_matrix_smem (the n x n eigen-solve matrix of every n-mer in shared memory
-where it fits, or in global memory).  tune() times every combination on the
-device for one system (the passes' own CUDA-event stage times, best of
-`repeats` runs), keeps the fastest in a JSON cache keyed by the workload's
-size class, and reports it beside the built-in rule; options() returns
-fmo_options with the cached choice, or the rule (0, 0) when nothing is cached.
+Knobs of fmo_options that change how fast the passes run, not what they
+compute: nmer_ctas_per_sm / monomer_ctas_per_sm (one CTA per SM with 255
+registers per thread, or two with 128 registers and half an SM of shared
+memory each) and nmer_matrix_smem / monomer_matrix_smem (the n x n
+eigen-solve matrix of every n-mer in shared memory where it fits, in global
+memory, or for monomers only its FP32 copy in shared memory).  tune() times
+every combination of the dimer/trimer knobs on the device for one system (the
+passes' own CUDA-event stage times, best of `repeats` runs), then the monomer
+knobs with that choice, keeps the fastest in a JSON cache keyed by the
+workload's size class, and reports it beside the built-in rule; options()
+returns fmo_options with the cached choice, or the rule when nothing is
+cached.
 
     python -m paper_2606_28022_b300.autotune --workload pentacene660 --precision mixed
 """
@@ -24,6 +27,8 @@ import numpy as np
 from . import fmo
 
 KNOBS = [(c, m) for c in (1, 2) for m in (1, 2)]
+MONO_KNOBS = [(1, 1), (2, 1), (2, 2), (2, 3)]
+FIELDS = ("nmer_ctas_per_sm", "nmer_matrix_smem", "monomer_ctas_per_sm", "monomer_matrix_smem")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "schedules.json")
 
 
@@ -54,32 +59,44 @@ def options(system, level: int, precision: str, device: int = 0, path: str = DEF
     when the cache has no entry for its size class)."""
     name = device_name if device_name is not None else _device_name(device)
     e = load(path).get(size_class(system, level, precision, name))
-    knobs = {} if e is None else {"nmer_ctas_per_sm": int(e["nmer_ctas_per_sm"]),
-                                   "nmer_matrix_smem": int(e["nmer_matrix_smem"])}
+    knobs = {} if e is None else {f: int(e[f]) for f in FIELDS if f in e}
     return fmo.options(level=level, precision=precision, **knobs, **kw)
 
 
 def tune(g: "fmo.FMO", system, level: int, precision: str, device: int = 0, repeats: int = 2,
          path: str = DEFAULT_CACHE, **kw) -> dict:
-    """Time the built-in rule and every knob combination on `system`; cache and
-    return the fastest combination with all timings (ms of the dimer and
-    trimer stages, best of `repeats`)."""
+    """Time the built-in rule and every knob combination on `system` (the
+    dimer and trimer stages for their knobs, then the monomer stage for its
+    knobs, best of `repeats` each); cache and return the fastest choice with
+    all timings."""
     g.set_system(system)
-    rows = []
-    for c, m in [(0, 0)] + KNOBS:
-        o = fmo.options(level=level, precision=precision, nmer_ctas_per_sm=c, nmer_matrix_smem=m, **kw)
-        best = math.inf
-        energies = None
+
+    def timed(knobs, stage):
+        o = fmo.options(level=level, precision=precision, **knobs, **kw)
+        best, energies = math.inf, None
         for _ in range(repeats):
             g.run(o, allow_unconverged=True)
             st = g.stats()
-            best = min(best, st["ms_dimer"] + st["ms_trimer"])
+            best = min(best, sum(st[x] for x in stage))
             energies = g.energies()
-        rows.append({"nmer_ctas_per_sm": c, "nmer_matrix_smem": m, "ms": best, "energies": list(energies)})
+        return best, list(energies)
+
+    rows = []
+    for c, m in [(0, 0)] + KNOBS:
+        t, e = timed({"nmer_ctas_per_sm": c, "nmer_matrix_smem": m}, ("ms_dimer", "ms_trimer"))
+        rows.append({"nmer_ctas_per_sm": c, "nmer_matrix_smem": m, "ms": t, "energies": e})
     choice = min(rows[1:], key=lambda r: r["ms"])
+    nk = {"nmer_ctas_per_sm": choice["nmer_ctas_per_sm"], "nmer_matrix_smem": choice["nmer_matrix_smem"]}
+    mrows = []
+    for c, m in [(0, 0)] + MONO_KNOBS:
+        t, e = timed({**nk, "monomer_ctas_per_sm": c, "monomer_matrix_smem": m}, ("ms_monomer",))
+        mrows.append({"monomer_ctas_per_sm": c, "monomer_matrix_smem": m, "ms": t, "energies": e})
+    mchoice = min(mrows[1:], key=lambda r: r["ms"])
     key = size_class(system, level, precision, _device_name(device))
-    entry = {"nmer_ctas_per_sm": choice["nmer_ctas_per_sm"], "nmer_matrix_smem": choice["nmer_matrix_smem"],
-             "ms": choice["ms"], "rule_ms": rows[0]["ms"], "timings": rows}
+    entry = {**nk, "ms": choice["ms"], "rule_ms": rows[0]["ms"], "timings": rows,
+             "monomer_ctas_per_sm": mchoice["monomer_ctas_per_sm"],
+             "monomer_matrix_smem": mchoice["monomer_matrix_smem"], "monomer_ms": mchoice["ms"],
+             "monomer_rule_ms": mrows[0]["ms"], "monomer_timings": mrows}
     cache = load(path)
     cache[key] = entry
     tmp = path + ".tmp"

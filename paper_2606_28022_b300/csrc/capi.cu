@@ -463,10 +463,13 @@ SmemPlan plan_smem(fmo_ctx* ctx, const Pass& P, int precision, bool fp32_only = 
   const size_t lim = (size_t)ctx->smem_optin;
   const size_t with_d = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 8 * npad * npad);
   const size_t with_f = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, 4 * npad * npad);
-  // placement: 0 the rule above, 1 shared memory where it fits, 2 global memory
+  // placement: 0 the rule above, 1 shared memory where it fits, 2 global
+  // memory, 3 (mixed precision) only the FP32 matrix in shared memory
   const bool global = placement == 2 || (placement == 0 && fp32_only && precision == FMO_PREC_MIXED && P.max_n >= 64);
   if (global) {
     // global memory (sp stays {0, 0})
+  } else if (placement == 3 && precision == FMO_PREC_MIXED) {
+    if (with_f <= lim) sp.a_f = 1;
   } else if (with_d <= lim) { sp.a_d = 1; sp.a_f = (precision == FMO_PREC_MIXED); }
   else if (precision == FMO_PREC_MIXED && with_f <= lim) { sp.a_f = 1; }
   sp.bytes = scc_smem_size(P.max_n, P.max_nsh, P.max_nat, (sp.a_d ? 8 : (sp.a_f ? 4 : 0)) * npad * npad);
@@ -624,7 +627,7 @@ fmo_status run_scc(fmo_ctx* ctx, Pass& P, const fmo_options& o, const SmemPlan& 
   L.t0 = ctx->d_t0.as<unsigned long long>();
   L.budget_ns = o.deadline_s > 0 ? (unsigned long long)(o.deadline_s * 1e9) : 0ULL;
   L.a_smem_d = sp.a_d; L.a_smem_f = sp.a_f;
-  L.ctas_per_sm = pass_id >= 1 ? o.nmer_ctas_per_sm : 0;
+  L.ctas_per_sm = pass_id >= 1 ? o.nmer_ctas_per_sm : o.monomer_ctas_per_sm;
   L.max_n = P.max_n; L.max_nsh = P.max_nsh; L.max_nat = P.max_nat;
   if (!sp.a_d) CK(P.Agd.ensure(sizeof(double) * P.tot_apad));
   if (o.precision == FMO_PREC_MIXED && !sp.a_f) CK(P.Agf.ensure(sizeof(float) * P.tot_apad));
@@ -1584,8 +1587,10 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     return fail(ctx, FMO_ERR_ARG, "unknown n-mer finish");
   if (o.want_gradient != 0 && o.want_gradient != 1) return fail(ctx, FMO_ERR_ARG, "want_gradient must be 0 or 1");
   if (o.esp_mode != FMO_ESP_AUTO && o.esp_mode != FMO_ESP_PAIRWISE) return fail(ctx, FMO_ERR_ARG, "unknown esp_mode");
-  if (o.nmer_ctas_per_sm < 0 || o.nmer_ctas_per_sm > 2 || o.nmer_matrix_smem < 0 || o.nmer_matrix_smem > 2)
-    return fail(ctx, FMO_ERR_ARG, "nmer_ctas_per_sm and nmer_matrix_smem must be 0, 1 or 2");
+  if (o.nmer_ctas_per_sm < 0 || o.nmer_ctas_per_sm > 2 || o.nmer_matrix_smem < 0 || o.nmer_matrix_smem > 2 ||
+      o.monomer_ctas_per_sm < 0 || o.monomer_ctas_per_sm > 2 || o.monomer_matrix_smem < 0 ||
+      o.monomer_matrix_smem > 3)
+    return fail(ctx, FMO_ERR_ARG, "schedule knobs out of range");
   const int world = o.shard_world <= 1 ? 1 : o.shard_world;
   if (o.shard_world < 0 || o.shard_rank < 0 || o.shard_rank >= world)
     return fail(ctx, FMO_ERR_ARG, "shard_rank must lie in [0, shard_world)");
@@ -1633,7 +1638,7 @@ fmo_status fmo_run(fmo_ctx* ctx, const fmo_options* opt, void* cuda_stream) {
     for (int f = 0; f < nf; ++f) tu[f] = {f, -1, -1};
     CK(plan_pass(ctx, ctx->mono, tu, nfr, true, o.precision, st));
   }
-  const SmemPlan sp_mono = plan_smem(ctx, ctx->mono, o.precision);
+  const SmemPlan sp_mono = plan_smem(ctx, ctx->mono, o.precision, false, o.monomer_matrix_smem);
   if (sp_mono.bytes > (size_t)ctx->smem_optin || !pass_fits(ctx->mono))
     return fail(ctx, FMO_ERR_UNSUPPORTED, "monomer too large");
   fmo_status fs = setup_pass(ctx, ctx->mono, o.precision, sp_mono, st);

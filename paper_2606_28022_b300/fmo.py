@@ -61,7 +61,8 @@ class FmoOptions(C.Structure):
                 ("outer_tol", C.c_double), ("mixed_switch_tol", C.c_double),
                 ("deadline_s", C.c_double), ("mixed_finish", C.c_int32), ("nmer_finish", C.c_int32),
                 ("want_gradient", C.c_int32), ("esp_mode", C.c_int32), ("shard_rank", C.c_int32),
-                ("shard_world", C.c_int32), ("nmer_ctas_per_sm", C.c_int32), ("nmer_matrix_smem", C.c_int32)]
+                ("shard_world", C.c_int32), ("nmer_ctas_per_sm", C.c_int32), ("nmer_matrix_smem", C.c_int32),
+                ("monomer_ctas_per_sm", C.c_int32), ("monomer_matrix_smem", C.c_int32)]
 
 # element-wise sum over the ranks of a sharded run (fmo_exchange_fn)
 EXCHANGE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_int64)
