@@ -1243,6 +1243,107 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
   return e_out;
 }
 
+constexpr bool kCholStart = true;   // Cholesky pass in the warm start of large n-mers
+
+// Dot products of the two passes below: sum_{k < len} x[k sx] (y0[k sy], y1[k sy])
+// with x shared by the block's threads (a broadcast) and y0/y1 per thread.
+// The operands live in L2 (an n-mer's matrices do not fit in L1 beside the
+// kernel's shared memory), so 16 terms are loaded before any is added: one
+// L2 round trip per 16 terms.
+__device__ __forceinline__ void chol_dot2(int len, const float* x, long long sx, const float* y0, const float* y1,
+                                          long long sy, float& r0, float& r1) {
+  constexpr int kU = 16;
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+  int k = 0;
+  for (; k + kU <= len; k += kU) {
+    float xv[kU], v0[kU], v1[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      xv[u] = x[(long long)(k + u) * sx];
+      v0[u] = y0[(long long)(k + u) * sy];
+      v1[u] = y1[(long long)(k + u) * sy];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u += 2) {
+      a0 = fmaf(xv[u], v0[u], a0);
+      a1 = fmaf(xv[u + 1], v0[u + 1], a1);
+      b0 = fmaf(xv[u], v1[u], b0);
+      b1 = fmaf(xv[u + 1], v1[u + 1], b1);
+    }
+  }
+  for (; k < len; ++k) {
+    const float xv = x[(long long)k * sx];
+    a0 = fmaf(xv, y0[(long long)k * sy], a0);
+    b0 = fmaf(xv, y1[(long long)k * sy], b0);
+  }
+  r0 = a0 + a1;
+  r1 = b0 + b1;
+}
+
+// Cholesky orthonormalisation of rows far from S-orthonormal (the warm start
+// of an n-mer from its monomers' rows).  With M = CT S CT^T = U^T U (U upper
+// triangular), the rows U^-T CT are S-orthonormal: a Gram-Schmidt pass over
+// the rows in order, which keeps the first fragment's rows and makes every
+// later row orthogonal to the rows before it.  These rows span the same space
+// as the Loewdin rows M^-1/2 CT and differ from them by an orthogonal
+// transformation, so they serve n-mers whose first iteration diagonalises
+// exactly.  It replaces the Newton-Schulz steps that bring |M - I| from order
+// 0.1 to 1e-2 (about ten n^3 products) by O(n^3 / 3) scalar work that needs no
+// tensor-core tiles.
+//   E: n x n, row-major, M - I on entry; its upper triangle becomes U.
+//   Lt: n x n scratch (U^T, row-major).
+// Returns false, with CT untouched, if a pivot is not positive (M not
+// numerically positive definite); the caller then keeps Newton-Schulz.
+__device__ __noinline__ bool chol_orthonormalise(int n, float* CT, float* E, float* Lt) {
+  __shared__ float s_piv;
+  __shared__ int s_bad;
+  // n <= 2 * kBlock: every thread owns up to two rows i (two columns c below),
+  // taken in one loop so that their loads overlap
+  for (int j = 0; j < n; ++j) {
+    // left-looking column j: d_i = M_ji - sum_{k<j} U_kj U_ki for i >= j
+    const int i0 = j + threadIdx.x, i1 = i0 + blockDim.x;
+    const bool h0 = i0 < n, h1 = i1 < n;
+    float s0 = 0.f, s1 = 0.f;
+    if (h0) chol_dot2(j, E + j, n, E + i0, E + (h1 ? i1 : i0), n, s0, s1);
+    const float d0 = h0 ? (i0 == j ? 1.f : 0.f) + E[(long long)j * n + i0] - s0 : 0.f;
+    const float d1 = h1 ? E[(long long)j * n + i1] - s1 : 0.f;
+    if (threadIdx.x == 0) {
+      s_bad = !(d0 > 1e-6f);
+      s_piv = s_bad ? 1.f : sqrtf(d0);
+    }
+    __syncthreads();
+    if (s_bad) return false;          // CT not yet touched; E is rebuilt by the caller
+    const float inv = 1.f / s_piv;
+    if (h0) E[(long long)j * n + i0] = (i0 == j) ? s_piv : d0 * inv;
+    if (h1) E[(long long)j * n + i1] = d1 * inv;
+    __syncthreads();
+  }
+  // Lt = U^T (row i of Lt: column i of U, lower triangle)
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int i = int(e / n), k = int(e - (long long)i * n);
+    if (k <= i) Lt[e] = E[(long long)k * n + i];
+  }
+  __syncthreads();
+  // CT <- U^-T CT by forward substitution, columns c0 and c1 of CT per thread
+  const int c0 = threadIdx.x, c1 = c0 + blockDim.x;
+  if (c0 < n) {
+    const bool h1 = c1 < n;
+    float* y0 = CT + c0;
+    float* y1 = CT + (h1 ? c1 : c0);
+    for (int i = 0; i < n; ++i) {
+      const float* li = Lt + (long long)i * n;
+      float s0, s1;
+      chol_dot2(i, li, 1, y0, y1, n, s0, s1);
+      const float r0 = (y0[(long long)i * n] - s0) / li[i];
+      const float r1 = (y1[(long long)i * n] - s1) / li[i];
+      y0[(long long)i * n] = r0;
+      if (h1) y1[(long long)i * n] = r1;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // CT <- (M^{-1/2}) CT with M = CT S CT^T, by Newton-Schulz steps
 // CT <- 1.5 CT - 0.5 M CT (each squares the error of M - I), until
 // max |M - I| < tol or max_steps: restores the S-orthonormality of the
@@ -1254,6 +1355,7 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
   const int n = nm.n;
   T* gemm = reinterpret_cast<T*>(sm.gemm);
   const double* Sm = ar.S + nm.mat;
+  bool chol_tried = !kCholStart;
   for (int step = 0; step < max_steps; ++step) {
     if constexpr (sizeof(T) == 4)   // S rounded to FP32 either way; the FP32 copy skips the conversions
       block_gemm<T>(n, n, n, pp.CT, n, 1, ar.S32 + nm.mat, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
@@ -1267,6 +1369,16 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
       // GEMMs instead of ~|E|^2 for 3 (A is free scratch here)
       const double err = max_dev_from_identity(pp.W1, n, n, sm.red, pp.W1);   // W1 <- E
       if (err < tol) break;
+      // n-mers whose first iteration is a tridiagonal solve: one Cholesky pass
+      // instead of the third-order steps (once; Newton-Schulz polishes after)
+      if (err > 1e-2 && !chol_tried && sm.tri && n >= kTriMinN && n <= 2 * kBlock) {
+        chol_tried = true;
+        if (chol_orthonormalise(n, pp.CT, pp.W1, pp.W2)) continue;
+        // not positive definite: E was partly overwritten, rebuild it
+        block_gemm<T>(n, n, n, pp.CT, n, 1, ar.S32 + nm.mat, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
+        block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, 1, n, pp.W1, n, nullptr, nullptr, nullptr, gemm);
+        max_dev_from_identity(pp.W1, n, n, sm.red, pp.W1);
+      }
       if (err > 1e-2) {
         block_gemm<T>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, nullptr, gemm);     // Y = E CT
         block_gemm<T>(n, n, n, pp.W1, n, 1, pp.W2, 1, n, pp.A, pp.lda, nullptr, nullptr, nullptr, gemm); // E Y
