@@ -55,7 +55,8 @@ WORKLOADS = {
 # an ncu capture, with the hash of the kernel sources it was taken on; used
 # only while those sources are unchanged
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = ["paper_2606_28022_b300/csrc/kernels.cu", "paper_2606_28022_b300/csrc/fmo_device.cuh"]
+KERNEL_SOURCES = ["paper_2606_28022_b300/csrc/kernels.cu", "paper_2606_28022_b300/csrc/fmo_device.cuh",
+                  "paper_2606_28022_b300/csrc/tridiag.cuh"]
 
 
 def kernel_source_hash() -> str:

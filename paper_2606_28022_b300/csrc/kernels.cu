@@ -1245,36 +1245,34 @@ __device__ double scc_iteration(const Nmer& nm, const SccArgs& ar, SccSmem& sm, 
 
 constexpr bool kCholStart = true;   // Cholesky pass in the warm start of large n-mers
 
-// Dot products of the two passes below: sum_{k < len} x[k sx] (y0[k sy], y1[k sy])
-// with x shared by the block's threads (a broadcast) and y0/y1 per thread.
-// The operands live in L2 (an n-mer's matrices do not fit in L1 beside the
-// kernel's shared memory), so 16 terms are loaded before any is added: one
-// L2 round trip per 16 terms.
-__device__ __forceinline__ void chol_dot2(int len, const float* x, long long sx, const float* y0, const float* y1,
-                                          long long sy, float& r0, float& r1) {
-  constexpr int kU = 16;
+// Dot products of the two passes below: sum_{k < len} x[k] (y0[k sy], y1[k sy])
+// with x in shared memory (staged once for the block: every thread uses the
+// same x) and y0/y1 per thread in global memory.  Those live in L2 (an
+// n-mer's matrices do not fit in L1 beside the kernel's shared memory), so 32
+// terms of each are loaded before any is added: one L2 round trip per 32.
+__device__ __forceinline__ void chol_dot2(int len, const float* x, const float* y0, const float* y1, long long sy,
+                                          float& r0, float& r1) {
+  constexpr int kU = 32;
   float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
   int k = 0;
   for (; k + kU <= len; k += kU) {
-    float xv[kU], v0[kU], v1[kU];
+    float v0[kU], v1[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      xv[u] = x[(long long)(k + u) * sx];
       v0[u] = y0[(long long)(k + u) * sy];
       v1[u] = y1[(long long)(k + u) * sy];
     }
 #pragma unroll
     for (int u = 0; u < kU; u += 2) {
-      a0 = fmaf(xv[u], v0[u], a0);
-      a1 = fmaf(xv[u + 1], v0[u + 1], a1);
-      b0 = fmaf(xv[u], v1[u], b0);
-      b1 = fmaf(xv[u + 1], v1[u + 1], b1);
+      a0 = fmaf(x[k + u], v0[u], a0);
+      a1 = fmaf(x[k + u + 1], v0[u + 1], a1);
+      b0 = fmaf(x[k + u], v1[u], b0);
+      b1 = fmaf(x[k + u + 1], v1[u + 1], b1);
     }
   }
   for (; k < len; ++k) {
-    const float xv = x[(long long)k * sx];
-    a0 = fmaf(xv, y0[(long long)k * sy], a0);
-    b0 = fmaf(xv, y1[(long long)k * sy], b0);
+    a0 = fmaf(x[k], y0[(long long)k * sy], a0);
+    b0 = fmaf(x[k], y1[(long long)k * sy], b0);
   }
   r0 = a0 + a1;
   r1 = b0 + b1;
@@ -1291,20 +1289,22 @@ __device__ __forceinline__ void chol_dot2(int len, const float* x, long long sx,
 // 0.1 to 1e-2 (about ten n^3 products) by O(n^3 / 3) scalar work that needs no
 // tensor-core tiles.
 //   E: n x n, row-major, M - I on entry; its upper triangle becomes U.
-//   Lt: n x n scratch (U^T, row-major).
+//   Lt: n x n scratch (U^T, row-major); xs: n floats of shared memory.
 // Returns false, with CT untouched, if a pivot is not positive (M not
 // numerically positive definite); the caller then keeps Newton-Schulz.
-__device__ __noinline__ bool chol_orthonormalise(int n, float* CT, float* E, float* Lt) {
+__device__ __noinline__ bool chol_orthonormalise(int n, float* CT, float* E, float* Lt, float* xs) {
   __shared__ float s_piv;
   __shared__ int s_bad;
   // n <= 2 * kBlock: every thread owns up to two rows i (two columns c below),
   // taken in one loop so that their loads overlap
   for (int j = 0; j < n; ++j) {
     // left-looking column j: d_i = M_ji - sum_{k<j} U_kj U_ki for i >= j
+    for (int k = threadIdx.x; k < j; k += blockDim.x) xs[k] = E[(long long)k * n + j];
+    __syncthreads();
     const int i0 = j + threadIdx.x, i1 = i0 + blockDim.x;
     const bool h0 = i0 < n, h1 = i1 < n;
     float s0 = 0.f, s1 = 0.f;
-    if (h0) chol_dot2(j, E + j, n, E + i0, E + (h1 ? i1 : i0), n, s0, s1);
+    if (h0) chol_dot2(j, xs, E + i0, E + (h1 ? i1 : i0), n, s0, s1);
     const float d0 = h0 ? (i0 == j ? 1.f : 0.f) + E[(long long)j * n + i0] - s0 : 0.f;
     const float d1 = h1 ? E[(long long)j * n + i1] - s1 : 0.f;
     if (threadIdx.x == 0) {
@@ -1325,22 +1325,25 @@ __device__ __noinline__ bool chol_orthonormalise(int n, float* CT, float* E, flo
   }
   __syncthreads();
   // CT <- U^-T CT by forward substitution, columns c0 and c1 of CT per thread
+  // (every thread takes part in staging row i of Lt)
   const int c0 = threadIdx.x, c1 = c0 + blockDim.x;
-  if (c0 < n) {
-    const bool h1 = c1 < n;
-    float* y0 = CT + c0;
-    float* y1 = CT + (h1 ? c1 : c0);
-    for (int i = 0; i < n; ++i) {
-      const float* li = Lt + (long long)i * n;
+  const bool h0 = c0 < n, h1 = c1 < n;
+  float* y0 = CT + (h0 ? c0 : 0);
+  float* y1 = CT + (h1 ? c1 : (h0 ? c0 : 0));
+  for (int i = 0; i < n; ++i) {
+    for (int k = threadIdx.x; k <= i; k += blockDim.x) xs[k] = Lt[(long long)i * n + k];
+    __syncthreads();
+    if (h0) {
       float s0, s1;
-      chol_dot2(i, li, 1, y0, y1, n, s0, s1);
-      const float r0 = (y0[(long long)i * n] - s0) / li[i];
-      const float r1 = (y1[(long long)i * n] - s1) / li[i];
+      chol_dot2(i, xs, y0, y1, n, s0, s1);
+      const float inv = 1.f / xs[i];
+      const float r0 = (y0[(long long)i * n] - s0) * inv;
+      const float r1 = (y1[(long long)i * n] - s1) * inv;
       y0[(long long)i * n] = r0;
       if (h1) y1[(long long)i * n] = r1;
     }
+    __syncthreads();
   }
-  __syncthreads();
   return true;
 }
 
@@ -1373,7 +1376,7 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
       // instead of the third-order steps (once; Newton-Schulz polishes after)
       if (err > 1e-2 && !chol_tried && sm.tri && n >= kTriMinN && n <= 2 * kBlock) {
         chol_tried = true;
-        if (chol_orthonormalise(n, pp.CT, pp.W1, pp.W2)) continue;
+        if (chol_orthonormalise(n, pp.CT, pp.W1, pp.W2, reinterpret_cast<float*>(gemm))) continue;
         // not positive definite: E was partly overwritten, rebuild it
         block_gemm<T>(n, n, n, pp.CT, n, 1, ar.S32 + nm.mat, n, 1, pp.W2, n, nullptr, nullptr, nullptr, gemm);
         block_gemm<T>(n, n, n, pp.W2, n, 1, pp.CT, 1, n, pp.W1, n, nullptr, nullptr, nullptr, gemm);
@@ -1390,6 +1393,11 @@ __device__ void reorthonormalise(const Nmer& nm, const SccArgs& ar, SccSmem& sm,
         block_gemm<T>(n, n, n, pp.W1, n, 1, pp.CT, 1, n, pp.W2, n, nullptr, nullptr, nullptr, gemm);     // E CT
         for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
           pp.CT[e] = pp.CT[e] - T(0.5) * pp.W2[e];
+        __syncthreads();
+        // from |E| < 3e-4 this step leaves (3/4)|E|^2 < 1e-7 plus FP32
+        // rounding, below any tolerance used here: no product to confirm it
+        if (err < 3e-4 && tol >= 1e-6) break;
+        continue;
       }
       __syncthreads();
       continue;
