@@ -449,6 +449,34 @@ fmo_status fmo_scc_solve_noalloc(const fmo_params *p, int32_t n_atoms, const int
                                  int32_t *status_dev, void *cuda_stream, char *err, int32_t err_len);
 
 /*
+ * Occupied-subspace projectors of a batch of symmetric matrices by
+ * second-order spectral-projection purification (SP2), the matrix-product
+ * alternative to the diagonalisation in each SCC iteration (Introduction:
+ * diagonalisation is the cubic step; Methodology, GFN1-xTB SCC).  For every
+ * b < batch:
+ *   D_b = sum_{i < n_occ[b]} c_i c_i^T,  F_b c_i = e_i c_i,  e ascending,
+ * the zero-temperature density with occupation one (a closed-shell density
+ * is 2 D_b); unique when e_{n_occ-1} < e_{n_occ}.
+ *   F_dev      device, batch x n x n doubles, row-major, symmetric (read only)
+ *   n_occ_dev  device, batch int32 occupied-orbital counts, 0..n
+ *   n          1..FMO_SP2_MAX_N;  batch >= 0 (0: nothing is launched)
+ *   max_iter   >= 1, purification steps per matrix (50 suffice for a
+ *              spectrum-to-gap ratio up to ~1e6)
+ *   D_dev      device, batch x n x n doubles, output
+ *   work_dev   device, batch x n x n doubles of caller-owned scratch
+ *   iters_dev  device, batch int32 output: steps taken, -1 not converged
+ *              within max_iter (or no gap at n_occ), -2 n_occ out of range
+ *   cuda_stream  stream the kernel is enqueued on (NULL: default stream);
+ *              the call returns without waiting.
+ * FP64 throughout; one CTA per matrix.  Allocates nothing.  Errors:
+ * FMO_ERR_ARG (sizes, NULL pointers), FMO_ERR_CUDA (launch failure).
+ */
+#define FMO_SP2_MAX_N 2048
+fmo_status fmo_sp2_projector(const double *F_dev, const int32_t *n_occ_dev, int32_t n,
+                             int32_t batch, int32_t max_iter, double *D_dev, double *work_dev,
+                             int32_t *iters_dev, void *cuda_stream);
+
+/*
  * Measured FMA throughput of CUDA device `device` in TFLOP/s (2 flops per
  * FMA): precision FMO_PREC_MIXED measures FP32, FMO_PREC_FP64 FP64.  A
  * diagnostic for the roofline of the SCC kernel; the paper has no

@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfmo_xtb.so")
-SOURCES = ["capi.cu", "kernels.cu", "noalloc.cu", "mlp.cu", "fmo_gradient.cu", "peaks.cu"]
+SOURCES = ["capi.cu", "kernels.cu", "noalloc.cu", "mlp.cu", "fmo_gradient.cu", "peaks.cu", "purify.cu"]
 HEADERS = ["fmo_device.cuh", "kernels.h", "mlp.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]

@@ -1,0 +1,155 @@
+// Density-matrix purification: the occupied-subspace projector of a batch of
+// orthogonalised Fock matrices from matrix products alone, in place of the
+// diagonalisation that makes each SCC iteration cubic (Introduction; the
+// GFN1-xTB SCC step of the Methodology).  Second-order spectral projection
+// (SP2, Niklasson, Phys. Rev. B 66, 155115 (2002)):
+//   X0 = (e_max I - F) / (e_max - e_min)      (Gershgorin bounds, spectrum in [0,1],
+//                                              lowest orbital energies near 1)
+//   X <- X^2        if |tr(X^2) - n_occ| < |2 tr(X) - tr(X^2) - n_occ|
+//   X <- 2X - X^2   otherwise
+// until the idempotency error tr(X) - tr(X^2) stops falling (parameter-free
+// stop: no decrease over two steps once it is below 1e-6).
+//
+// One CTA per matrix; X lives in the output buffer and X^2 in the caller's
+// work buffer (both n x n row-major, L2-resident for n-mer sizes); FP64
+// products through 32 x 32 shared-memory tiles.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "../../include/fmo_xtb.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTile = 32;
+
+__device__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < kThreads / 32; ++i) s += red[i];   // same order in every thread
+  return s;
+}
+
+__device__ double block_min(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = red[0];
+  for (int i = 1; i < kThreads / 32; ++i) s = fmin(s, red[i]);
+  return s;
+}
+
+// Y = X X for one n x n matrix; every thread of the CTA takes part.
+__device__ void square(const double *X, double *Y, int n, double (*As)[kTile + 1],
+                       double (*Bs)[kTile + 1]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // ty in 0..7
+  const int nt = (n + kTile - 1) / kTile;
+  for (int t = 0; t < nt * nt; ++t) {
+    const int i0 = (t / nt) * kTile, j0 = (t % nt) * kTile;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k0 = 0; k0 < n; k0 += kTile) {
+      for (int r = ty; r < kTile; r += kThreads / 32) {
+        const int ia = i0 + r, ka = k0 + tx, kb = k0 + r, jb = j0 + tx;
+        As[r][tx] = (ia < n && ka < n) ? X[(size_t)ia * n + ka] : 0.0;
+        Bs[r][tx] = (kb < n && jb < n) ? X[(size_t)kb * n + jb] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < kTile; ++kk) {
+        const double b = Bs[kk][tx];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][kk], b, acc[q]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + ty + 8 * q, j = j0 + tx;
+      if (i < n && j < n) Y[(size_t)i * n + j] = acc[q];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) sp2_kernel(const double *__restrict__ F,
+                                                       const int32_t *__restrict__ n_occ, int n,
+                                                       int max_iter, double *D, double *W,
+                                                       int32_t *iters) {
+  __shared__ double As[kTile][kTile + 1];
+  __shared__ double Bs[kTile][kTile + 1];
+  __shared__ double red[kThreads / 32];
+  const size_t nn = (size_t)n * n;
+  const double *f = F + blockIdx.x * nn;
+  double *X = D + blockIdx.x * nn;
+  double *Y = W + blockIdx.x * nn;
+  const int occ = n_occ[blockIdx.x];
+  if (occ < 0 || occ > n) {
+    if (threadIdx.x == 0) iters[blockIdx.x] = -2;
+    return;
+  }
+
+  // Gershgorin interval [lo, hi] holding the spectrum of F
+  double lo = CUDART_INF, nhi = CUDART_INF;
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    double r = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (j != i) r += fabs(f[(size_t)i * n + j]);
+    lo = fmin(lo, f[(size_t)i * n + i] - r);
+    nhi = fmin(nhi, -(f[(size_t)i * n + i] + r));
+  }
+  lo = block_min(lo, red);
+  const double hi = -block_min(nhi, red);
+  const double scale = hi > lo ? 1.0 / (hi - lo) : 0.0;
+  for (size_t idx = threadIdx.x; idx < nn; idx += kThreads) {
+    const size_t i = idx / n, j = idx % n;
+    X[idx] = ((i == j ? hi : 0.0) - f[idx]) * scale;
+  }
+  __syncthreads();
+
+  double e1 = CUDART_INF, e2 = CUDART_INF;
+  int done = -1;
+  for (int it = 1; it <= max_iter; ++it) {
+    square(X, Y, n, As, Bs);
+    __syncthreads();
+    double tx = 0.0, ty = 0.0;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+      tx += X[(size_t)i * n + i];
+      ty += Y[(size_t)i * n + i];
+    }
+    tx = block_sum(tx, red);
+    ty = block_sum(ty, red);
+    const double e = fabs(tx - ty);
+    const bool sq = fabs(ty - occ) < fabs(2.0 * tx - ty - occ);
+    for (size_t idx = threadIdx.x; idx < nn; idx += kThreads)
+      X[idx] = sq ? Y[idx] : 2.0 * X[idx] - Y[idx];
+    __syncthreads();
+    if (e < 1e-6 && e >= e2) {
+      // a gapless F (e.g. a multiple of I) can stall at a non-projector
+      // whose trace is not n_occ: reported as not converged
+      const double tr_new = sq ? ty : 2.0 * tx - ty;
+      done = fabs(tr_new - occ) < 0.5 ? it : -1;
+      break;
+    }
+    e2 = e1;
+    e1 = e;
+  }
+  if (threadIdx.x == 0) iters[blockIdx.x] = done;
+}
+
+}  // namespace
+
+extern "C" fmo_status fmo_sp2_projector(const double *F_dev, const int32_t *n_occ_dev, int32_t n,
+                                        int32_t batch, int32_t max_iter, double *D_dev,
+                                        double *work_dev, int32_t *iters_dev, void *cuda_stream) {
+  if (n < 1 || n > FMO_SP2_MAX_N || batch < 0 || max_iter < 1) return FMO_ERR_ARG;
+  if (batch == 0) return FMO_OK;
+  if (!F_dev || !n_occ_dev || !D_dev || !work_dev || !iters_dev) return FMO_ERR_ARG;
+  sp2_kernel<<<batch, kThreads, 0, (cudaStream_t)cuda_stream>>>(F_dev, n_occ_dev, n, max_iter,
+                                                                D_dev, work_dev, iters_dev);
+  return cudaGetLastError() == cudaSuccess ? FMO_OK : FMO_ERR_CUDA;
+}

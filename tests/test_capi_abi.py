@@ -20,7 +20,7 @@ def lib():
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"\b(fmo_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(fmo_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -70,3 +70,14 @@ def test_no_cpu_fallback_without_a_gpu(lib, params):
     with pytest.raises(fmo.FMOError) as e:
         fmo.FMO(params)
     assert e.value.status == 2                                  # FMO_ERR_CUDA
+
+
+def test_sp2_projector_argument_errors_need_no_gpu(lib):
+    # sizes are checked before any CUDA call; batch 0 launches nothing
+    f = lib.fmo_sp2_projector
+    assert f(None, None, 0, 1, 10, None, None, None, None) == 1          # n < 1
+    assert f(None, None, 2049, 1, 10, None, None, None, None) == 1       # n > FMO_SP2_MAX_N
+    assert f(None, None, 8, -1, 10, None, None, None, None) == 1         # batch < 0
+    assert f(None, None, 8, 1, 0, None, None, None, None) == 1           # max_iter < 1
+    assert f(None, None, 8, 1, 10, None, None, None, None) == 1          # NULL pointers
+    assert f(None, None, 8, 0, 10, None, None, None, None) == 0          # empty batch
