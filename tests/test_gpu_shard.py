@@ -61,7 +61,7 @@ def _rank(rank, world, port, out):
 
 
 def test_two_ranks_on_one_gpu_equal_the_unsharded_run():
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()   # no fork of a process that holds a CUDA context
     mp.spawn(_rank, args=(2, _free_port(), out), nprocs=2, join=True)
     ref = out[0]
     for name, _, _ in _systems():
