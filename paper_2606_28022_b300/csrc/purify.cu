@@ -45,13 +45,18 @@ __device__ double block_min(double v, double *red) {
   return s;
 }
 
-// Y = X X for one n x n matrix; every thread of the CTA takes part.
+// Y = X X for one symmetric n x n matrix; every thread of the CTA takes part.
+// Y is symmetric too: only the tiles on and above the diagonal are computed,
+// each off-diagonal one also stored transposed (through shared memory, so
+// both stores are row-contiguous).
 __device__ void square(const double *X, double *Y, int n, double (*As)[kTile + 1],
                        double (*Bs)[kTile + 1]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // ty in 0..7
   const int nt = (n + kTile - 1) / kTile;
   for (int t = 0; t < nt * nt; ++t) {
-    const int i0 = (t / nt) * kTile, j0 = (t % nt) * kTile;
+    const int ti = t / nt, tj = t % nt;
+    if (tj < ti) continue;                 // uniform over the CTA
+    const int i0 = ti * kTile, j0 = tj * kTile;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k0 = 0; k0 < n; k0 += kTile) {
       for (int r = ty; r < kTile; r += kThreads / 32) {
@@ -72,6 +77,19 @@ __device__ void square(const double *X, double *Y, int n, double (*As)[kTile + 1
     for (int q = 0; q < 4; ++q) {
       const int i = i0 + ty + 8 * q, j = j0 + tx;
       if (i < n && j < n) Y[(size_t)i * n + j] = acc[q];
+    }
+    if (tj > ti) {
+      // the k-loop ended on a barrier, so As is free
+#pragma unroll
+      for (int q = 0; q < 4; ++q) As[ty + 8 * q][tx] = acc[q];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = ty + 8 * q;          // row of the transposed tile
+        const int i = j0 + r, j = i0 + tx;
+        if (i < n && j < n) Y[(size_t)i * n + j] = As[tx][r];
+      }
+      __syncthreads();
     }
   }
 }
