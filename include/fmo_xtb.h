@@ -478,6 +478,19 @@ fmo_status fmo_sp2_projector(const double *F_dev, const int32_t *n_occ_dev, int3
                              int32_t *iters_dev, void *cuda_stream);
 
 /*
+ * The same projectors in FP32 (float buffers, FP32 products; traces and the
+ * step choice in FP64), the precision of the loose iterations of a
+ * mixed-precision SCC (Methodology, GFN1-xTB SCC; the FP32 phase before the
+ * FP64 finish).  Arguments, layout, ownership and errors as for
+ * fmo_sp2_projector.  The stop test is opened once the idempotency error is
+ * below 1e-2; the result is idempotent to ~n * 1e-7 and equals the FP64
+ * projector to ~1e-5 for well-conditioned gaps.
+ */
+fmo_status fmo_sp2_projector_f32(const float *F_dev, const int32_t *n_occ_dev, int32_t n,
+                                 int32_t batch, int32_t max_iter, float *D_dev, float *work_dev,
+                                 int32_t *iters_dev, void *cuda_stream);
+
+/*
  * Measured FMA throughput of CUDA device `device` in TFLOP/s (2 flops per
  * FMA): precision FMO_PREC_MIXED measures FP32, FMO_PREC_FP64 FP64.  A
  * diagnostic for the roofline of the SCC kernel; the paper has no

@@ -8,11 +8,12 @@
 //   X <- X^2        if |tr(X^2) - n_occ| < |2 tr(X) - tr(X^2) - n_occ|
 //   X <- 2X - X^2   otherwise
 // until the idempotency error tr(X) - tr(X^2) stops falling (parameter-free
-// stop: no decrease over two steps once it is below 1e-6).
+// stop: no decrease over two steps once it is below a gate, 1e-6 in FP64).
 //
 // One CTA per matrix; X lives in the output buffer and X^2 in the caller's
-// work buffer (both n x n row-major, L2-resident for n-mer sizes); FP64
-// products through 32 x 32 shared-memory tiles.
+// work buffer (both n x n row-major, L2-resident for n-mer sizes); products
+// through 32 x 32 shared-memory tiles in FP64 or, for the loose iterations of
+// a mixed-precision SCC, in FP32.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -49,25 +50,25 @@ __device__ double block_min(double v, double *red) {
 // Y is symmetric too: only the tiles on and above the diagonal are computed,
 // each off-diagonal one also stored transposed (through shared memory, so
 // both stores are row-contiguous).
-__device__ void square(const double *X, double *Y, int n, double (*As)[kTile + 1],
-                       double (*Bs)[kTile + 1]) {
+template <typename T>
+__device__ void square(const T *X, T *Y, int n, T (*As)[kTile + 1], T (*Bs)[kTile + 1]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // ty in 0..7
   const int nt = (n + kTile - 1) / kTile;
   for (int t = 0; t < nt * nt; ++t) {
     const int ti = t / nt, tj = t % nt;
     if (tj < ti) continue;                 // uniform over the CTA
     const int i0 = ti * kTile, j0 = tj * kTile;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int k0 = 0; k0 < n; k0 += kTile) {
       for (int r = ty; r < kTile; r += kThreads / 32) {
         const int ia = i0 + r, ka = k0 + tx, kb = k0 + r, jb = j0 + tx;
-        As[r][tx] = (ia < n && ka < n) ? X[(size_t)ia * n + ka] : 0.0;
-        Bs[r][tx] = (kb < n && jb < n) ? X[(size_t)kb * n + jb] : 0.0;
+        As[r][tx] = (ia < n && ka < n) ? X[(size_t)ia * n + ka] : T(0);
+        Bs[r][tx] = (kb < n && jb < n) ? X[(size_t)kb * n + jb] : T(0);
       }
       __syncthreads();
 #pragma unroll 8
       for (int kk = 0; kk < kTile; ++kk) {
-        const double b = Bs[kk][tx];
+        const T b = Bs[kk][tx];
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][kk], b, acc[q]);
       }
@@ -94,17 +95,25 @@ __device__ void square(const double *X, double *Y, int n, double (*As)[kTile + 1
   }
 }
 
-__global__ void __launch_bounds__(kThreads) sp2_kernel(const double *__restrict__ F,
+// Stop gate on the idempotency error: FP64 reaches ~1e-13; FP32 stalls near
+// n * 1e-7, so its parameter-free stop is opened at 1e-2 (all eigenvalues of X
+// within ~1e-2 of 0 or 1, where the error falls quadratically until rounding).
+template <typename T> struct Sp2Gate;
+template <> struct Sp2Gate<double> { static constexpr double value = 1e-6; };
+template <> struct Sp2Gate<float> { static constexpr double value = 1e-2; };
+
+// Traces and the branch decision are taken in FP64 in both precisions.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) sp2_kernel(const T *__restrict__ F,
                                                        const int32_t *__restrict__ n_occ, int n,
-                                                       int max_iter, double *D, double *W,
-                                                       int32_t *iters) {
-  __shared__ double As[kTile][kTile + 1];
-  __shared__ double Bs[kTile][kTile + 1];
+                                                       int max_iter, T *D, T *W, int32_t *iters) {
+  __shared__ T As[kTile][kTile + 1];
+  __shared__ T Bs[kTile][kTile + 1];
   __shared__ double red[kThreads / 32];
   const size_t nn = (size_t)n * n;
-  const double *f = F + blockIdx.x * nn;
-  double *X = D + blockIdx.x * nn;
-  double *Y = W + blockIdx.x * nn;
+  const T *f = F + blockIdx.x * nn;
+  T *X = D + blockIdx.x * nn;
+  T *Y = W + blockIdx.x * nn;
   const int occ = n_occ[blockIdx.x];
   if (occ < 0 || occ > n) {
     if (threadIdx.x == 0) iters[blockIdx.x] = -2;
@@ -125,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) sp2_kernel(const double *__restrict_
   const double scale = hi > lo ? 1.0 / (hi - lo) : 0.0;
   for (size_t idx = threadIdx.x; idx < nn; idx += kThreads) {
     const size_t i = idx / n, j = idx % n;
-    X[idx] = ((i == j ? hi : 0.0) - f[idx]) * scale;
+    X[idx] = (T)(((i == j ? hi : 0.0) - (double)f[idx]) * scale);
   }
   __syncthreads();
 
@@ -136,17 +145,17 @@ __global__ void __launch_bounds__(kThreads) sp2_kernel(const double *__restrict_
     __syncthreads();
     double tx = 0.0, ty = 0.0;
     for (int i = threadIdx.x; i < n; i += kThreads) {
-      tx += X[(size_t)i * n + i];
-      ty += Y[(size_t)i * n + i];
+      tx += (double)X[(size_t)i * n + i];
+      ty += (double)Y[(size_t)i * n + i];
     }
     tx = block_sum(tx, red);
     ty = block_sum(ty, red);
     const double e = fabs(tx - ty);
     const bool sq = fabs(ty - occ) < fabs(2.0 * tx - ty - occ);
     for (size_t idx = threadIdx.x; idx < nn; idx += kThreads)
-      X[idx] = sq ? Y[idx] : 2.0 * X[idx] - Y[idx];
+      X[idx] = sq ? Y[idx] : T(2) * X[idx] - Y[idx];
     __syncthreads();
-    if (e < 1e-6 && e >= e2) {
+    if (e < Sp2Gate<T>::value && e >= e2) {
       // a gapless F (e.g. a multiple of I) can stall at a non-projector
       // whose trace is not n_occ: reported as not converged
       const double tr_new = sq ? ty : 2.0 * tx - ty;
@@ -167,7 +176,19 @@ extern "C" fmo_status fmo_sp2_projector(const double *F_dev, const int32_t *n_oc
   if (n < 1 || n > FMO_SP2_MAX_N || batch < 0 || max_iter < 1) return FMO_ERR_ARG;
   if (batch == 0) return FMO_OK;
   if (!F_dev || !n_occ_dev || !D_dev || !work_dev || !iters_dev) return FMO_ERR_ARG;
-  sp2_kernel<<<batch, kThreads, 0, (cudaStream_t)cuda_stream>>>(F_dev, n_occ_dev, n, max_iter,
-                                                                D_dev, work_dev, iters_dev);
+  sp2_kernel<double><<<batch, kThreads, 0, (cudaStream_t)cuda_stream>>>(
+      F_dev, n_occ_dev, n, max_iter, D_dev, work_dev, iters_dev);
+  return cudaGetLastError() == cudaSuccess ? FMO_OK : FMO_ERR_CUDA;
+}
+
+extern "C" fmo_status fmo_sp2_projector_f32(const float *F_dev, const int32_t *n_occ_dev,
+                                            int32_t n, int32_t batch, int32_t max_iter,
+                                            float *D_dev, float *work_dev, int32_t *iters_dev,
+                                            void *cuda_stream) {
+  if (n < 1 || n > FMO_SP2_MAX_N || batch < 0 || max_iter < 1) return FMO_ERR_ARG;
+  if (batch == 0) return FMO_OK;
+  if (!F_dev || !n_occ_dev || !D_dev || !work_dev || !iters_dev) return FMO_ERR_ARG;
+  sp2_kernel<float><<<batch, kThreads, 0, (cudaStream_t)cuda_stream>>>(
+      F_dev, n_occ_dev, n, max_iter, D_dev, work_dev, iters_dev);
   return cudaGetLastError() == cudaSuccess ? FMO_OK : FMO_ERR_CUDA;
 }

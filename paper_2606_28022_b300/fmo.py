@@ -28,7 +28,8 @@ SYMBOLS = ["fmo_options_default", "fmo_create", "fmo_set_system", "fmo_set_coord
            "fmo_get_sizes", "fmo_get_monomers", "fmo_get_dimers", "fmo_get_trimers", "fmo_get_gradient",
            "fmo_get_stats", "fmo_last_error", "fmo_destroy", "fmo_mlp_init", "fmo_mlp_set_weights",
            "fmo_mlp_get_weights", "fmo_mlp_predict", "fmo_mlp_train", "fmo_scc_solve_noalloc", "fmo_fma_peak",
-           "fmo_mlp_loss_grad", "fmo_set_exchange", "fmo_lpt_partition", "fmo_sp2_projector"]
+           "fmo_mlp_loss_grad", "fmo_set_exchange", "fmo_lpt_partition", "fmo_sp2_projector",
+           "fmo_sp2_projector_f32"]
 MLP_N_WEIGHTS = 26908
 MLP_N_TRAINED = 26754
 
@@ -132,6 +133,7 @@ def load_library(path: str | None = None):
     lib.fmo_lpt_partition.argtypes = [dp, i64, i32, ip]
     lib.fmo_scc_solve_noalloc.argtypes = [vp, i32, ip, vp, i32, vp, vp, vp, vp, vp, vp, C.c_char_p, i32]
     lib.fmo_sp2_projector.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp]
+    lib.fmo_sp2_projector_f32.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp]
     lib.fmo_last_error.argtypes = [vp]
     lib.fmo_last_error.restype = C.c_char_p
     lib.fmo_destroy.argtypes = [vp]
@@ -154,12 +156,14 @@ def fma_peak(precision: str = "fp32", device: int = 0) -> float:
 
 
 def sp2_projector(F_ptr: int, n_occ_ptr: int, n: int, batch: int, max_iter: int, D_ptr: int,
-                  work_ptr: int, iters_ptr: int, stream: int | None = None) -> None:
+                  work_ptr: int, iters_ptr: int, stream: int | None = None, fp32: bool = False) -> None:
     """Occupied-subspace projectors of a batch of symmetric n x n matrices by
-    SP2 purification (fmo_sp2_projector); every pointer is a device address."""
-    st = load_library().fmo_sp2_projector(C.c_void_p(F_ptr), C.c_void_p(n_occ_ptr), int(n), int(batch),
-                                          int(max_iter), C.c_void_p(D_ptr), C.c_void_p(work_ptr),
-                                          C.c_void_p(iters_ptr), C.c_void_p(stream or 0))
+    SP2 purification (fmo_sp2_projector, or fmo_sp2_projector_f32 on float
+    buffers with fp32=True); every pointer is a device address."""
+    lib = load_library()
+    fn = lib.fmo_sp2_projector_f32 if fp32 else lib.fmo_sp2_projector
+    st = fn(C.c_void_p(F_ptr), C.c_void_p(n_occ_ptr), int(n), int(batch), int(max_iter),
+            C.c_void_p(D_ptr), C.c_void_p(work_ptr), C.c_void_p(iters_ptr), C.c_void_p(stream or 0))
     if st != FMO_OK:
         raise FMOError(st, "fmo_sp2_projector failed")
 

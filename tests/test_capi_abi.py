@@ -81,3 +81,7 @@ def test_sp2_projector_argument_errors_need_no_gpu(lib):
     assert f(None, None, 8, 1, 0, None, None, None, None) == 1           # max_iter < 1
     assert f(None, None, 8, 1, 10, None, None, None, None) == 1          # NULL pointers
     assert f(None, None, 8, 0, 10, None, None, None, None) == 0          # empty batch
+    g = lib.fmo_sp2_projector_f32
+    assert g(None, None, 0, 1, 10, None, None, None, None) == 1
+    assert g(None, None, 8, 1, 10, None, None, None, None) == 1
+    assert g(None, None, 8, 0, 10, None, None, None, None) == 0
